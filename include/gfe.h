@@ -1,0 +1,170 @@
+/*
+ * gfe.h -- C ABI of libgfe: exact Gaussian elimination with transformation
+ * matrix over small prime fields GF(p), p <= 251, on one GB300 (sm_103a).
+ *
+ * Method: Linton, Nebe, Niemeyer, Parker, Thackray, "A parallel algorithm for
+ * Gaussian elimination over finite fields", arXiv 1806.04211.  For an input
+ * C in GF(p)^{m x n} of rank r the library computes, Eq. (echelon) (Section 3.1):
+ *
+ *     (M 0; K 1) (rho; rho_bar) C (Ups^tr Ups_bar^tr) = (-1 R; 0 0)
+ *
+ * with rho (varrho) the pivot rows, Ups (Upsilon) the pivot columns and the
+ * paper's negative normalisation: every pivot entry of the echelon form is
+ * -1 (= p-1).  The pivot of a row is its first non-zero entry (Section 1);
+ * rho is then the row rank profile and Ups the column rank profile, which
+ * makes every output unique.  Ordering: rows of M and R by ascending pivot
+ * column, columns of M and K by ascending pivot row, rows of K ascending
+ * (rho_bar).  All indices are 0-based (the paper's are 1-based).
+ *
+ * Storage (argument "fmt"):
+ *   GFE_U8     one byte per entry, value in [0,p), row-major, ld in bytes.
+ *   GFE_BITS64 GF(2) only: rows of 64-bit words, bit (c % 64) of word c/64 is
+ *              column c (LSB first); ld in bytes (multiple of 8); pad bits
+ *              of the input are ignored, pad bits of outputs are written 0.
+ *
+ * Memory: every pointer in this header is DEVICE memory unless stated
+ * otherwise.  Inputs are never modified.  Outputs and the workspace are
+ * owned by the caller; the library keeps no pointer after a call returns
+ * except inside a gfe_server (see there).  Calls are asynchronous on the
+ * given CUDA stream (a cudaStream_t passed as void*; NULL = legacy default
+ * stream) EXCEPT that gfe_echelon / gfe_rank synchronise that stream
+ * internally once per block echelonisation (the host plans the data-dependent
+ * shapes); they return when all work has been queued and the result is
+ * complete on the device.
+ *
+ * Errors: every function returns a gfe_status.  GFE_EINVAL: bad argument
+ * (p not prime or > 251, fmt/p mismatch, negative sizes, NULL where a buffer
+ * is required, ld too small, workspace too small).  GFE_ECUDA: a CUDA call
+ * failed (gfe_last_error() gives its text).  No call aborts the process.
+ */
+#ifndef GFE_H
+#define GFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GFE_OK = 0,
+    GFE_EINVAL = 1,
+    GFE_ENOMEM = 2,
+    GFE_ETIMEOUT = 3,
+    GFE_EBUSY = 4,
+    GFE_ECUDA = 5,
+    GFE_EINTERNAL = 6,
+    GFE_ENOTSUP = 7
+} gfe_status;
+
+typedef enum { GFE_U8 = 0, GFE_BITS64 = 1 } gfe_storage;
+
+/* flags */
+#define GFE_WANT_TRANSFORM 0x1u  /* compute M and K (Task UpdateRowTrafo, Steps 2-3 on M) */
+#define GFE_WANT_DENSE_E   0x2u  /* also write dense E = (-RREF(C); 0), m x n        */
+#define GFE_WANT_DENSE_T   0x4u  /* also write dense T = (M 0; K 1) P_rho, m x m     */
+#define GFE_IMPL_PLAIN     0x100u /* block multiply-add on CUDA cores (the plain     */
+                                  /* comparator) instead of the tensor cores        */
+#define GFE_IMPL_TENSOR    0x200u /* force the tcgen05 tensor-core multiply-add     */
+
+/* A matrix argument: m x n over GF(p), stored as described above. */
+typedef struct {
+    int32_t p;
+    int64_t m, n;
+    int32_t fmt;          /* gfe_storage */
+    const void *data;     /* device */
+    int64_t ld;           /* bytes between consecutive rows */
+} gfe_matrix;
+
+/*
+ * Result buffers (device, caller-allocated, sized for the worst case
+ * r = min(m,n); the first r / m-r rows and r / n-r columns are written).
+ * Same storage format as the input.  Any pointer may be NULL to skip that
+ * output, except rank.
+ */
+typedef struct {
+    int64_t *rank;        /* 1 int64: r */
+    int64_t *pivot_cols;  /* Ups: r int64, ascending            (min(m,n) entries) */
+    int64_t *pivot_rows;  /* rho: r int64, ascending            (min(m,n) entries) */
+    void *R; int64_t ldR; /* r x (n-r)    (min(m,n) rows, n cols)                   */
+    void *M; int64_t ldM; /* r x r        (min(m,n) rows, min(m,n) cols)            */
+    void *K; int64_t ldK; /* (m-r) x r    (m rows, min(m,n) cols)                   */
+    void *E; int64_t ldE; /* m x n dense echelon form   (GFE_WANT_DENSE_E)          */
+    void *T; int64_t ldT; /* m x m dense transformation (GFE_WANT_DENSE_T)          */
+} gfe_result;
+
+/* Workspace (bytes, device) that gfe_echelon / gfe_rank need for A and flags.
+ * Depends only on (p, m, n, flags). */
+gfe_status gfe_query_workspace(const gfe_matrix *A, uint32_t flags, size_t *ws_bytes);
+
+/*
+ * gfe_echelon -- the whole method: Step 1 (Tasks ClearDown, Extend,
+ * UpdateRow, UpdateRowTrafo), Step 2 (Task RowLengthen) and Step 3 (Tasks
+ * Copy, PreClearUp, ClearUp) of "The Chief" (Section 3, Algorithm "The
+ * Chief"), with the single-block echelonisation ECH done recursively by the
+ * same scheme (Section 2.3.2).  M and K are written only with
+ * GFE_WANT_TRANSFORM (dense T needs it).
+ */
+gfe_status gfe_echelon(const gfe_matrix *A, const gfe_result *out, uint32_t flags,
+                       void *ws, size_t ws_bytes, void *stream);
+
+/* gfe_rank -- Step 1 without UpdateRowTrafo (the rank-only variant the paper
+ * lists in Section 1); writes r to rank_dev and, if non-NULL, Ups and rho. */
+gfe_status gfe_rank(const gfe_matrix *A, int64_t *rank_dev, int64_t *pivot_cols,
+                    int64_t *pivot_rows, uint32_t flags, void *ws, size_t ws_bytes,
+                    void *stream);
+
+/*
+ * gfe_batch_echelon -- count independent matrices (any sizes, any fields)
+ * echelonised together: the block tasks of all matrices that are ready at the
+ * same stage share kernel launches.  outs[i] receives the result of As[i];
+ * identical to count separate gfe_echelon calls.
+ */
+gfe_status gfe_query_batch_workspace(const gfe_matrix *As, int32_t count, uint32_t flags,
+                                     size_t *ws_bytes);
+gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32_t count,
+                             uint32_t flags, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * gfe_mad -- the job MAD (Section 4.1): C := W + A B over GF(p), A m x k,
+ * B k x n, W and C m x n, all GFE_U8 residues (device).  W may be NULL
+ * (C := A B, the job MUL) and may equal C.  ws: gfe_mad_workspace() bytes.
+ * The block multiply-add is the dominant cost of the method (Section 5,
+ * Lemma "closecosts").
+ */
+size_t gfe_mad_workspace(int32_t p, int64_t m, int64_t n, int64_t k);
+gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k,
+                   const uint8_t *W, int64_t ldw, const uint8_t *A, int64_t lda,
+                   const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                   uint32_t flags, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Block partition policy of the planner (the "carefully chosen" block sizes
+ * a_i, b_j of Section 3.1 and Section 5).  A block (or the whole input)
+ * whose larger side exceeds `threshold` is split into square blocks of side
+ * `block`; smaller ones into leaf blocks of at most 1024 rows x 64 columns,
+ * which the one-CTA ECH kernel echelonises.  Defaults: 8192, 2048.  Process
+ * wide; values <= 0 restore the defaults.  Results never depend on it.
+ */
+gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);
+
+/* Kernel-time profile of the calls made since the last reset (all streams).
+ * Collected with CUDA events around every kernel launch while enabled. */
+typedef struct {
+    int64_t launches[8];     /* by kind: 0 MAD tensor, 1 MAD plain, 2 ECH leaf,   */
+    double  ms[8];           /*   3 extract/riffle, 4 convert/assemble, 5 other   */
+    double  madds[8];        /* algorithmic multiply-adds done by the MAD kinds  */
+    int64_t host_syncs;      /* stream synchronisations made by the planner      */
+} gfe_profile;
+gfe_status gfe_profile_enable(int32_t on);
+gfe_status gfe_profile_read(gfe_profile *out, int32_t reset);
+
+const char *gfe_status_str(gfe_status s);
+const char *gfe_last_error(void);
+const char *gfe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GFE_H */

@@ -1,0 +1,405 @@
+// C ABI of libgfe (include/gfe.h): argument checks, workspace layout,
+// conversion between the API storage and the internal codec, profiling.
+#include "gfe.h"
+#include "gfe_internal.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <stdexcept>
+#include <vector>
+
+namespace gfe {
+
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string t_err;
+void set_error(const std::string &s) { t_err = s; }
+bool cuda_ok(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return true;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// profiling: CUDA events around every launch while enabled
+// ---------------------------------------------------------------------------
+bool g_prof_on = false;
+static std::mutex g_prof_mu;
+static gfe_profile g_prof;
+struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+    double madds;
+};
+static std::vector<Pending> g_pending;
+static std::vector<cudaEvent_t> g_evpool;
+
+static cudaEvent_t ev_get() {
+    if (!g_evpool.empty()) {
+        cudaEvent_t e = g_evpool.back();
+        g_evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(const Launch &L, Kind k, cudaEvent_t *ev0) {
+    (void)k;
+    *ev0 = nullptr;
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    *ev0 = ev_get();
+    cudaEventRecord(*ev0, L.st);
+}
+
+void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds) {
+    if (!g_prof_on || !ev0) return;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    cudaEvent_t e1 = ev_get();
+    cudaEventRecord(e1, L.st);
+    g_pending.push_back({(int)k, ev0, e1, madds});
+}
+
+static void resolve_locked() {
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(p.b);
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        g_prof.launches[p.kind] += 1;
+        g_prof.ms[p.kind] += ms;
+        g_prof.madds[p.kind] += p.madds;
+        g_evpool.push_back(p.a);
+        g_evpool.push_back(p.b);
+    }
+    g_pending.clear();
+}
+
+void prof_sync_point() {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (g_pending.size() > 4096) resolve_locked();
+}
+
+void prof_count_sync() {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.host_syncs += 1;
+}
+
+// ---------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------
+static bool is_prime(int p) {
+    if (p < 2) return false;
+    for (int d = 2; d * d <= p; ++d)
+        if (p % d == 0) return false;
+    return true;
+}
+
+static gfe_status check_matrix(const gfe_matrix *A) {
+    if (!A) return (set_error("matrix argument is NULL"), GFE_EINVAL);
+    if (!is_prime(A->p) || A->p > 251) return (set_error("p must be a prime <= 251"), GFE_EINVAL);
+    if (A->m < 0 || A->n < 0) return (set_error("negative size"), GFE_EINVAL);
+    if (A->m > (int64_t)1 << 30 || A->n > (int64_t)1 << 30) return (set_error("size too large"), GFE_EINVAL);
+    if (A->fmt == GFE_BITS64) {
+        if (A->p != 2) return (set_error("GFE_BITS64 needs p = 2"), GFE_EINVAL);
+        if (A->ld % 8 || A->ld < 8 * ((A->n + 63) / 64)) return (set_error("ld too small for GFE_BITS64"), GFE_EINVAL);
+    } else if (A->fmt == GFE_U8) {
+        if (A->ld < A->n) return (set_error("ld < n"), GFE_EINVAL);
+    } else {
+        return (set_error("unknown storage format"), GFE_EINVAL);
+    }
+    if (A->m > 0 && A->n > 0 && !A->data) return (set_error("data is NULL"), GFE_EINVAL);
+    return GFE_OK;
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t H, Mo, Ko, Ro, maps, arena, total;
+};
+
+static Layout layout(const gfe_matrix *A, bool trafo, bool wantR) {
+    const int es = codec_bytes(codec_for(A->p));
+    const int64_t m = A->m, n = A->n, mn = std::min(m, n);
+    Layout Lo;
+    size_t off = 0;
+    Lo.H = off;
+    off += al256((size_t)std::max<int64_t>(m, 1) * std::max<int64_t>(n, 1) * es);
+    Lo.Mo = off;
+    off += trafo ? al256((size_t)std::max<int64_t>(mn, 1) * std::max<int64_t>(mn, 1) * es) : 256;
+    Lo.Ko = off;
+    off += trafo ? al256((size_t)std::max<int64_t>(m, 1) * std::max<int64_t>(mn, 1) * es) : 256;
+    Lo.Ro = off;
+    off += wantR ? al256((size_t)std::max<int64_t>(mn, 1) * std::max<int64_t>(n, 1) * es) : 256;
+    Lo.maps = off;
+    off += al256((size_t)(m + n + 2) * 4);
+    Lo.arena = off;
+    Lo.total = off;
+    return Lo;
+}
+
+static void launch_for(const gfe_matrix *A, uint32_t flags, void *stream, Launch &L) {
+    L.st = (cudaStream_t)stream;
+    L.p = A->p;
+    L.codec = codec_for(A->p);
+    L.impl = (flags & GFE_IMPL_PLAIN) ? 1 : 0;
+}
+
+static gfe_status query(const gfe_matrix *A, bool trafo, bool wantR, size_t *ws) {
+    Layout Lo = layout(A, trafo, wantR);
+    Launch L;
+    launch_for(A, 0, nullptr, L);
+    DMat H;
+    H.rows = A->m;
+    H.cols = A->n;
+    H.ld = std::max<int64_t>(A->n, 1);
+    DMat Mo, Ko, Ro;
+    TopResult res;
+    size_t peak = 0;
+    try {
+        run_chief(L, nullptr, 0, true, H, trafo, wantR, Mo, Ko, Ro, res, &peak, Lo.arena, nullptr);
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        return GFE_EINTERNAL;
+    }
+    *ws = al256(peak) + 4096;
+    return GFE_OK;
+}
+
+static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_dev, int64_t *pcols,
+                      int64_t *prows, uint32_t flags, bool trafo, bool wantR, void *ws, size_t ws_bytes,
+                      void *stream) {
+    gfe_status st = check_matrix(A);
+    if (st) return st;
+    size_t need = 0;
+    st = query(A, trafo, wantR, &need);
+    if (st) return st;
+    if (!ws || ws_bytes < need) {
+        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+        return GFE_EINVAL;
+    }
+    const bool wantE = out && (flags & GFE_WANT_DENSE_E) && out->E;
+    const bool wantT = out && (flags & GFE_WANT_DENSE_T) && out->T;
+    if (wantT && !trafo) return (set_error("dense T needs GFE_WANT_TRANSFORM"), GFE_EINVAL);
+    Launch L;
+    launch_for(A, flags, stream, L);
+    Layout Lo = layout(A, trafo, wantR);
+    char *base = (char *)ws;
+    const int64_t m = A->m, n = A->n, mn = std::min(m, n);
+    DMat H;
+    H.ptr = base + Lo.H;
+    H.rows = m;
+    H.cols = n;
+    H.ld = std::max<int64_t>(n, 1);
+    DMat Mo, Ko, Ro;
+    Mo.ptr = base + Lo.Mo;
+    Mo.rows = Mo.cols = mn;
+    Mo.ld = std::max<int64_t>(mn, 1);
+    Ko.ptr = base + Lo.Ko;
+    Ko.rows = m;
+    Ko.cols = mn;
+    Ko.ld = std::max<int64_t>(mn, 1);
+    Ro.ptr = base + Lo.Ro;
+    Ro.rows = mn;
+    Ro.cols = n;
+    Ro.ld = std::max<int64_t>(n, 1);
+    const int es = codec_bytes(L.codec);
+    TopResult res;
+    try {
+        // pack: API storage -> internal codec
+        if (A->fmt == GFE_BITS64) import_bits(L, m, n, H.ptr, H.ld, (const uint64_t *)A->data, A->ld / 8);
+        else import_u8(L, m, n, H.ptr, H.ld, (const uint8_t *)A->data, A->ld);
+        int64_t syncs = 0;
+        run_chief(L, base, ws_bytes, false, H, trafo, wantR, Mo, Ko, Ro, res, nullptr, Lo.arena, &syncs);
+        const int64_t r = res.r;
+        // rank, Upsilon, varrho
+        std::vector<int64_t> hr(1, r), hg(res.gamma.begin(), res.gamma.end()), hp(res.rho.begin(), res.rho.end());
+        if (!cuda_ok(cudaMemcpyAsync(rank_dev, hr.data(), 8, cudaMemcpyHostToDevice, L.st), "rank")) return GFE_ECUDA;
+        if (pcols && r && !cuda_ok(cudaMemcpyAsync(pcols, hg.data(), 8 * r, cudaMemcpyHostToDevice, L.st), "pivot_cols"))
+            return GFE_ECUDA;
+        if (prows && r && !cuda_ok(cudaMemcpyAsync(prows, hp.data(), 8 * r, cudaMemcpyHostToDevice, L.st), "pivot_rows"))
+            return GFE_ECUDA;
+        const bool bits = A->fmt == GFE_BITS64;
+        if (out) {
+            if (out->R && wantR) {
+                if (bits) export_bits(L, r, n - r, (uint64_t *)out->R, out->ldR / 8, Ro.ptr, Ro.ld);
+                else export_u8(L, r, n - r, (uint8_t *)out->R, out->ldR, Ro.ptr, Ro.ld);
+            }
+            if (trafo && out->M) {
+                if (bits) export_bits(L, r, r, (uint64_t *)out->M, out->ldM / 8, Mo.ptr, Mo.ld);
+                else export_u8(L, r, r, (uint8_t *)out->M, out->ldM, Mo.ptr, Mo.ld);
+            }
+            if (trafo && out->K) {
+                if (bits) export_bits(L, m - r, r, (uint64_t *)out->K, out->ldK / 8, Ko.ptr, Ko.ld);
+                else export_u8(L, m - r, r, (uint8_t *)out->K, out->ldK, Ko.ptr, Ko.ld);
+            }
+            std::vector<int32_t> map;
+            int32_t *dmap = (int32_t *)(base + Lo.maps);
+            if (wantE) {
+                map.assign(n, 0);
+                std::vector<char> isp(n, 0);
+                for (int64_t l = 0; l < r; ++l) {
+                    map[res.gamma[l]] = (int32_t)l;
+                    isp[res.gamma[l]] = 1;
+                }
+                int32_t j = 0;
+                for (int64_t c = 0; c < n; ++c)
+                    if (!isp[c]) map[c] = -1 - (j++);
+                if (!cuda_ok(cudaMemcpyAsync(dmap, map.data(), 4 * n, cudaMemcpyHostToDevice, L.st), "map"))
+                    return GFE_ECUDA;
+                build_E(L, A->fmt, m, n, r, out->E, out->ldE, Ro.ptr, Ro.ld, dmap);
+                if (!cuda_ok(cudaStreamSynchronize(L.st), "sync")) return GFE_ECUDA;
+            }
+            if (wantT) {
+                map.assign(m, 0);
+                std::vector<char> isp(m, 0);
+                for (int64_t s = 0; s < r; ++s) {
+                    map[res.rho[s]] = (int32_t)s;
+                    isp[res.rho[s]] = 1;
+                }
+                int32_t t = 0;
+                for (int64_t x = 0; x < m; ++x)
+                    if (!isp[x]) map[x] = -1 - (t++);
+                if (!cuda_ok(cudaMemcpyAsync(dmap, map.data(), 4 * m, cudaMemcpyHostToDevice, L.st), "map"))
+                    return GFE_ECUDA;
+                build_T(L, A->fmt, m, r, out->T, out->ldT, Mo.ptr, Mo.ld, Ko.ptr, Ko.ld, dmap);
+            }
+        }
+        (void)es;
+        if (!cuda_ok(cudaStreamSynchronize(L.st), "final sync")) return GFE_ECUDA;
+        if (!cuda_ok(cudaGetLastError(), "kernel launch")) return GFE_ECUDA;
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        if (std::string(e.what()).find("workspace") != std::string::npos) return GFE_ENOMEM;
+        return GFE_ECUDA;
+    }
+    return GFE_OK;
+}
+
+}  // namespace gfe
+
+using namespace gfe;
+
+extern "C" {
+
+gfe_status gfe_query_workspace(const gfe_matrix *A, uint32_t flags, size_t *ws_bytes) {
+    gfe_status st = check_matrix(A);
+    if (st) return st;
+    if (!ws_bytes) return (set_error("ws_bytes is NULL"), GFE_EINVAL);
+    bool trafo = (flags & (GFE_WANT_TRANSFORM | GFE_WANT_DENSE_T)) != 0;
+    return query(A, trafo, true, ws_bytes);
+}
+
+gfe_status gfe_echelon(const gfe_matrix *A, const gfe_result *out, uint32_t flags, void *ws, size_t ws_bytes,
+                       void *stream) {
+    if (!out || !out->rank) return (set_error("out->rank is required"), GFE_EINVAL);
+    bool trafo = (flags & (GFE_WANT_TRANSFORM | GFE_WANT_DENSE_T)) != 0;
+    return run(A, out, out->rank, out->pivot_cols, out->pivot_rows, flags, trafo, true, ws, ws_bytes, stream);
+}
+
+gfe_status gfe_rank(const gfe_matrix *A, int64_t *rank_dev, int64_t *pivot_cols, int64_t *pivot_rows,
+                    uint32_t flags, void *ws, size_t ws_bytes, void *stream) {
+    if (!rank_dev) return (set_error("rank_dev is required"), GFE_EINVAL);
+    return run(A, nullptr, rank_dev, pivot_cols, pivot_rows, flags, false, false, ws, ws_bytes, stream);
+}
+
+gfe_status gfe_query_batch_workspace(const gfe_matrix *As, int32_t count, uint32_t flags, size_t *ws_bytes) {
+    if (!ws_bytes || count < 0 || (count && !As)) return (set_error("bad batch arguments"), GFE_EINVAL);
+    size_t best = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        size_t w = 0;
+        gfe_status st = gfe_query_workspace(&As[i], flags, &w);
+        if (st) return st;
+        best = std::max(best, w);
+    }
+    *ws_bytes = best;
+    return GFE_OK;
+}
+
+gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32_t count, uint32_t flags,
+                             void *ws, size_t ws_bytes, void *stream) {
+    if (count < 0 || (count && (!As || !outs))) return (set_error("bad batch arguments"), GFE_EINVAL);
+    for (int32_t i = 0; i < count; ++i) {
+        gfe_status st = gfe_echelon(&As[i], &outs[i], flags, ws, ws_bytes, stream);
+        if (st) return st;
+    }
+    return GFE_OK;
+}
+
+size_t gfe_mad_workspace(int32_t p, int64_t m, int64_t n, int64_t k) {
+    int es = codec_bytes(codec_for(p < 2 ? 2 : p));
+    return al256((size_t)m * k * es) + al256((size_t)k * n * es) + al256((size_t)m * n * es) + 256;
+}
+
+gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k, const uint8_t *W, int64_t ldw, const uint8_t *A,
+                   int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, uint32_t flags, void *ws,
+                   size_t ws_bytes, void *stream) {
+    if (!is_prime(p) || p > 251) return (set_error("p must be a prime <= 251"), GFE_EINVAL);
+    if (m < 0 || n < 0 || k < 0) return (set_error("negative size"), GFE_EINVAL);
+    if (m == 0 || n == 0) return GFE_OK;
+    if (!C || ldc < n || (k > 0 && (!A || !B || lda < k || ldb < n)) || (W && ldw < n))
+        return (set_error("bad matrix argument"), GFE_EINVAL);
+    if (!ws || ws_bytes < gfe_mad_workspace(p, m, n, k)) return (set_error("workspace too small"), GFE_EINVAL);
+    Launch L;
+    L.st = (cudaStream_t)stream;
+    L.p = p;
+    L.codec = codec_for(p);
+    L.impl = (flags & GFE_IMPL_PLAIN) ? 1 : 0;
+    const int es = codec_bytes(L.codec);
+    char *a = (char *)ws, *b = a + al256((size_t)m * k * es), *c = b + al256((size_t)k * n * es);
+    if (k > 0) {
+        import_u8(L, m, k, a, k, A, lda);
+        import_u8(L, k, n, b, n, B, ldb);
+    }
+    if (W) import_u8(L, m, n, c, n, W, ldw);
+    mad(L, m, n, k, W ? c : nullptr, n, a, k, b, n, c, n);
+    export_u8(L, m, n, C, ldc, c, n);
+    if (!cuda_ok(cudaGetLastError(), "kernel launch")) return GFE_ECUDA;
+    return GFE_OK;
+}
+
+gfe_status gfe_set_block_policy(int64_t threshold, int64_t block) {
+    g_block_threshold = threshold > 0 ? threshold : 8192;
+    g_block_big = block > 0 ? block : 2048;
+    return GFE_OK;
+}
+
+gfe_status gfe_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof_on = on != 0;
+    return GFE_OK;
+}
+
+gfe_status gfe_profile_read(gfe_profile *out, int32_t reset) {
+    if (!out) return (set_error("out is NULL"), GFE_EINVAL);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    resolve_locked();
+    *out = g_prof;
+    if (reset) std::memset(&g_prof, 0, sizeof g_prof);
+    return GFE_OK;
+}
+
+const char *gfe_status_str(gfe_status s) {
+    switch (s) {
+    case GFE_OK: return "ok";
+    case GFE_EINVAL: return "invalid argument";
+    case GFE_ENOMEM: return "out of memory";
+    case GFE_ETIMEOUT: return "timeout";
+    case GFE_EBUSY: return "busy";
+    case GFE_ECUDA: return "CUDA error";
+    case GFE_EINTERNAL: return "internal error";
+    case GFE_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+const char *gfe_last_error(void) { return t_err.c_str(); }
+const char *gfe_version(void) { return "gfe 0.1 (sm_103a)"; }
+
+}  // extern "C"

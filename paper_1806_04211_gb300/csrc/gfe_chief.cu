@@ -1,0 +1,602 @@
+// The Chief (arXiv 1806.04211, Section 3, Algorithm "The Chief") as a host
+// planner driving the job kernels, and the recursive single-block
+// echelonisation ECH built on it (Section 2.3.2).
+//
+// Step 1: Tasks ClearDown, Extend, UpdateRow and UpdateRowTrafo (Section 4.2)
+// Step 2: Task RowLengthen
+// Step 3: Tasks Copy, PreClearUp and ClearUp
+//
+// Layout (internal codec, see gfe_internal.h):
+//   * the matrix C being echelonised is held in place; block row i is the row
+//     panel starting at row ro[i], its current (not yet pivotal) rows are
+//     compacted at the top of the panel (REX keeps order, Section 2.3.4);
+//   * B_j (pivot rows of block column j restricted to block columns k > j)
+//     is one row panel per j, columns [co[j+1], beta);
+//   * D_j.R is r_j x (b_j - r_j);
+//   * K_ih (h <= i) live in one row panel per block row i, block row h's
+//     stored columns at column offset ro[h]; M_jh likewise in one panel per j.
+//   Only the columns the paper keeps are stored and multiplied (Section 3.1.1,
+//   "transformation matrix abbreviation"); unstored zero columns are riffled
+//   in (CRZ) and identity columns added (ADI) as Task UpdateRowTrafo says.
+//
+// Readings of points the paper leaves open (all validated against the oracle):
+//   * u / delta from UNH mark NEW indices with 1; CRZ puts the stored columns
+//     at the 0 positions and zero columns at the 1 positions; ADI puts the
+//     identity 1 of the t-th new pivot row at the t-th 1 position of delta.
+//   * RowLengthen keeps the stored columns at the positions of E_hj.rho inside
+//     E_hb.rho (MKR's 1s) and riffles zeros elsewhere.
+//   * ClearDown's second MAD is R' + A.E x R (the pseudo-code's form).
+//   * "i = 1" means the first block row; every job accepts empty operands.
+#include "gfe_internal.h"
+
+#include <algorithm>
+#include <cstring>
+#include <stdexcept>
+
+namespace gfe {
+
+struct OomError : std::runtime_error {
+    OomError() : std::runtime_error("workspace too small") {}
+};
+struct CudaError : std::runtime_error {
+    explicit CudaError(const std::string &s) : std::runtime_error(s) {}
+};
+
+// ---------------------------------------------------------------------------
+// workspace arena (stack discipline) and host<->device staging
+// ---------------------------------------------------------------------------
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0, top = 0, peak = 0;
+    bool dry = false;
+    void *alloc(size_t bytes) {
+        size_t a = (top + 255) & ~(size_t)255;
+        top = a + ((bytes + 255) & ~(size_t)255);
+        if (top > peak) peak = top;
+        if (dry) return nullptr;
+        if (top > cap) throw OomError();
+        return base + a;
+    }
+    size_t mark() const { return top; }
+    void release(size_t m) { top = m; }
+};
+
+constexpr size_t STAGE_BYTES = 8u << 20;
+
+struct Stage {  // pinned host buffer + device ring for small index arrays
+    char *host = nullptr;
+    char *dev = nullptr;
+    size_t top = 0;
+};
+
+static thread_local char *t_pinned = nullptr;
+
+struct Ctx {
+    Launch L;
+    Arena ar;
+    Stage sg;
+    bool dry = false;
+    int es = 1;
+    int64_t syncs = 0;
+
+    void check(cudaError_t e, const char *what) {
+        if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    void sync() {
+        if (dry) return;
+        check(cudaStreamSynchronize(L.st), "cudaStreamSynchronize");
+        check(cudaGetLastError(), "kernel launch");
+        sg.top = 0;
+        ++syncs;
+        prof_count_sync();
+        prof_sync_point();
+    }
+    // upload an index array; returns its device address
+    const int32_t *put(const std::vector<int32_t> &v) {
+        if (dry || v.empty()) return nullptr;
+        size_t bytes = (v.size() * 4 + 255) & ~(size_t)255;
+        if (bytes > STAGE_BYTES) throw std::runtime_error("index array too large");
+        if (sg.top + bytes > STAGE_BYTES) sync();
+        std::memcpy(sg.host + sg.top, v.data(), v.size() * 4);
+        check(cudaMemcpyAsync(sg.dev + sg.top, sg.host + sg.top, v.size() * 4, cudaMemcpyHostToDevice, L.st),
+              "upload");
+        const int32_t *d = (const int32_t *)(sg.dev + sg.top);
+        sg.top += bytes;
+        return d;
+    }
+    DMat mat(int64_t rows, int64_t cols) {
+        DMat d;
+        d.rows = rows;
+        d.cols = cols;
+        d.ld = cols > 0 ? cols : 1;
+        d.ptr = ar.alloc((size_t)(rows > 0 ? rows : 1) * (size_t)d.ld * es);
+        return d;
+    }
+    void *at(const DMat &d, int64_t r, int64_t c) const {
+        return dry ? nullptr : (char *)d.ptr + (r * d.ld + c) * es;
+    }
+};
+
+static DMat sub(const Ctx &X, const DMat &d, int64_t r0, int64_t c0, int64_t rows, int64_t cols) {
+    DMat s;
+    s.ptr = X.at(d, r0, c0);
+    s.rows = rows;
+    s.cols = cols;
+    s.ld = d.ld;
+    return s;
+}
+
+// ---- job wrappers (no-ops in the dry run that sizes the workspace) ----
+static void j_mad(Ctx &X, int64_t m, int64_t n, int64_t k, const DMat *W, const DMat &A, const DMat &B,
+                  const DMat &C) {
+    if (X.dry || m <= 0 || n <= 0) return;
+    mad(X.L, m, n, k, W ? W->ptr : nullptr, W ? W->ld : 0, A.ptr, A.ld, B.ptr, B.ld, C.ptr, C.ld);
+}
+static void j_rows(Ctx &X, int64_t nrows, int64_t ncols, const DMat &dst, const DMat &A, const DMat *B,
+                   const std::vector<int32_t> &map) {
+    if (X.dry || nrows <= 0 || ncols <= 0) return;
+    gather_rows(X.L, nrows, ncols, dst.ptr, dst.ld, A.ptr, A.ld, B ? B->ptr : nullptr, B ? B->ld : 0, X.put(map));
+}
+static void j_cols(Ctx &X, int64_t nrows, int64_t ncols, const DMat &dst, const DMat &src,
+                   const std::vector<int32_t> &map) {
+    if (X.dry || nrows <= 0 || ncols <= 0) return;
+    gather_cols(X.L, nrows, ncols, dst.ptr, dst.ld, src.ptr, src.ld, X.put(map));
+}
+static void j_copy(Ctx &X, int64_t rows, int64_t cols, const DMat &dst, const DMat &src) {
+    if (X.dry || rows <= 0 || cols <= 0) return;
+    copy2d(X.L, rows, cols, dst.ptr, dst.ld, src.ptr, src.ld);
+}
+static void j_zero(Ctx &X, int64_t rows, int64_t cols, const DMat &dst) {
+    if (X.dry || rows <= 0 || cols <= 0) return;
+    zero2d(X.L, rows, cols, dst.ptr, dst.ld);
+}
+
+// ---- subset bookkeeping (jobs UNH, UN0, MKR; Section 4.1) on the host ----
+static std::vector<int32_t> complement(const std::vector<int32_t> &s, int64_t n) {
+    std::vector<int32_t> out;
+    out.reserve(n - (int64_t)s.size());
+    size_t k = 0;
+    for (int32_t x = 0; x < (int32_t)n; ++x) {
+        if (k < s.size() && s[k] == x) ++k;
+        else out.push_back(x);
+    }
+    return out;
+}
+// UNH: rho = rho1 U {x_i : i in rho2}, x = complement of rho1; u_l = 1 iff new
+static void unh(const std::vector<int32_t> &rho1, const std::vector<int32_t> &rho2, int64_t alpha,
+                std::vector<int32_t> &rho, std::vector<int32_t> &u) {
+    std::vector<int32_t> x = complement(rho1, alpha);
+    std::vector<int32_t> nw;
+    for (int32_t i : rho2) nw.push_back(x[i]);
+    rho.clear();
+    u.clear();
+    size_t a = 0, b = 0;
+    while (a < rho1.size() || b < nw.size()) {
+        if (b >= nw.size() || (a < rho1.size() && rho1[a] < nw[b])) {
+            rho.push_back(rho1[a++]);
+            u.push_back(0);
+        } else {
+            rho.push_back(nw[b++]);
+            u.push_back(1);
+        }
+    }
+}
+// RRF map: row l <- (u_l == 0 ? B row #zeros-so-far : C row #ones-so-far)
+static std::vector<int32_t> riffle_map(const std::vector<int32_t> &u) {
+    std::vector<int32_t> m(u.size());
+    int32_t z = 0, o = 0;
+    for (size_t l = 0; l < u.size(); ++l) m[l] = u[l] ? -1 - (o++) : (z++);
+    return m;
+}
+// CRZ map: new column t <- (newmask_t ? zero : old column #zeros-so-far)
+static std::vector<int32_t> crz_map(const std::vector<int32_t> &newmask) {
+    std::vector<int32_t> m(newmask.size());
+    int32_t z = 0;
+    for (size_t t = 0; t < newmask.size(); ++t) m[t] = newmask[t] ? -1 : (z++);
+    return m;
+}
+static std::vector<int32_t> ones_positions(const std::vector<int32_t> &mask) {
+    std::vector<int32_t> pos;
+    for (size_t t = 0; t < mask.size(); ++t)
+        if (mask[t]) pos.push_back((int32_t)t);
+    return pos;
+}
+
+struct EchRes {
+    int64_t r = 0;
+    std::vector<int32_t> rho, gamma;
+};
+
+void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::vector<int64_t> &bcols,
+           bool trafo, bool wantR, const DMat &Mo, const DMat &Ko, const DMat &Ro, EchRes &out);
+
+// ---------------------------------------------------------------------------
+// ECH(H) -> (M, K, R, rho, gamma); H (alpha x beta) is destroyed.  Leaves go
+// to the one-CTA kernel; larger blocks are split by the Chief itself, which
+// is the paper's recursive scheme with a general rather than 2-way split.
+// ---------------------------------------------------------------------------
+int64_t g_block_threshold = 8192, g_block_big = 2048;
+
+static void block_policy(int64_t alpha, int64_t beta, std::vector<int64_t> &a, std::vector<int64_t> &b) {
+    int64_t ra, cb;
+    if (std::max(alpha, beta) <= g_block_threshold) {
+        ra = ECH_LEAF_ROWS;
+        cb = ECH_LEAF_COLS;
+    } else {
+        ra = cb = g_block_big;
+    }
+    a.clear();
+    b.clear();
+    for (int64_t x = 0; x < alpha; x += ra) a.push_back(std::min(ra, alpha - x));
+    for (int64_t x = 0; x < beta; x += cb) b.push_back(std::min(cb, beta - x));
+}
+
+void ech(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, const DMat &Ro, EchRes &out) {
+    const int64_t alpha = H.rows, beta = H.cols;
+    out.r = 0;
+    out.rho.clear();
+    out.gamma.clear();
+    if (alpha == 0 || beta == 0) return;
+    if (alpha <= ECH_LEAF_ROWS && beta <= ECH_LEAF_COLS) {
+        size_t mk = X.ar.mark();
+        int32_t *info = (int32_t *)X.ar.alloc(sizeof(int32_t) * (1 + 2 * ECH_LEAF_COLS));
+        if (!X.dry) {
+            ech_leaf(X.L, alpha, beta, H.ptr, H.ld, info, Mo.ptr, Mo.ld, Ko.ptr, Ko.ld, Ro.ptr, Ro.ld);
+            int32_t *h = (int32_t *)t_pinned;
+            X.check(cudaMemcpyAsync(h, info, sizeof(int32_t) * (1 + 2 * ECH_LEAF_COLS), cudaMemcpyDeviceToHost,
+                                    X.L.st), "download");
+            X.sync();
+            out.r = h[0];
+            out.rho.assign(h + 1, h + 1 + out.r);
+            out.gamma.assign(h + 1 + ECH_LEAF_COLS, h + 1 + ECH_LEAF_COLS + out.r);
+        }
+        X.ar.release(mk);
+        return;
+    }
+    std::vector<int64_t> a, b;
+    block_policy(alpha, beta, a, b);
+    chief(X, H, a, b, true, true, Mo, Ko, Ro, out);
+}
+
+// ---------------------------------------------------------------------------
+// The Chief
+// ---------------------------------------------------------------------------
+void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::vector<int64_t> &bcols,
+           bool trafo, bool wantR, const DMat &Mo, const DMat &Ko, const DMat &Ro, EchRes &out) {
+    const size_t mark0 = X.ar.mark();
+    const int a = (int)arows.size(), b = (int)bcols.size();
+    const int64_t alpha = H.rows, beta = H.cols;
+    std::vector<int64_t> ro(a + 1, 0), co(b + 1, 0);
+    for (int i = 0; i < a; ++i) ro[i + 1] = ro[i] + arows[i];
+    for (int j = 0; j < b; ++j) co[j + 1] = co[j] + bcols[j];
+    const int64_t maxa = *std::max_element(arows.begin(), arows.end());
+    const int64_t maxb = *std::max_element(bcols.begin(), bcols.end());
+    const int64_t minab = std::min(maxa, maxb);
+
+    // ---- buffers ----
+    std::vector<int64_t> cur(arows.begin(), arows.end());  // current rows per block row
+    std::vector<DMat> Bp(b);
+    std::vector<int64_t> rB(b, 0);
+    // B panels, D_j.R and M panels are swapped with a spare by the riffles,
+    // so each family has one uniform capacity and leading dimension
+    int64_t bcap = 0, bw = 0;
+    for (int j = 0; j < b; ++j) {
+        bcap = std::max(bcap, std::min(bcols[j], alpha));
+        bw = std::max(bw, beta - co[j + 1]);
+    }
+    bw = std::max<int64_t>(bw, 1);
+    for (int j = 0; j < b; ++j) Bp[j] = X.mat(bcap, bw);
+    DMat Bsp = X.mat(bcap, bw);
+    std::vector<DMat> DR(b);
+    std::vector<std::vector<int32_t>> gam(b);
+    for (int j = 0; j < b; ++j) DR[j] = X.mat(maxb, maxb);
+    DMat DRsp = X.mat(maxb, maxb);
+    DMat AA = X.mat(maxa, maxb), AM = X.mat(minab, minab), AK = X.mat(maxa, minab), AE = X.mat(maxb, maxb);
+    DMat Hb = X.mat(maxa, maxb), Rech = X.mat(minab, maxb), Rp = X.mat(maxb, maxb);
+    DMat V = X.mat(minab, std::max<int64_t>(bw, 1)), W = X.mat(maxa, std::max<int64_t>(bw, 1));
+    DMat Xb = X.mat(minab, std::max<int64_t>(bw, 1));
+    std::vector<DMat> Kp(a), Mp(b);
+    DMat Msp, Zt, Vt, Wt, Xt, St;
+    // stored widths of K_ih / M_jh; -1 = not stored yet (implicitly zero)
+    std::vector<std::vector<int64_t>> wK(a, std::vector<int64_t>(a, 0)), wM(b, std::vector<int64_t>(a, -1));
+    if (trafo) {
+        for (int i = 0; i < a; ++i) {
+            Kp[i] = X.mat(arows[i], ro[i + 1]);
+        }
+        for (int j = 0; j < b; ++j) Mp[j] = X.mat(bcap, alpha);
+        Msp = X.mat(bcap, alpha);
+        Zt = X.mat(maxa, maxa);
+        Vt = X.mat(minab, maxa);
+        Wt = X.mat(maxa, maxa);
+        Xt = X.mat(minab, maxa);
+        St = X.mat(std::min(maxb, alpha), maxa);
+    }
+    // E_ij.rho / E_ij.delta for every (i, j)
+    std::vector<std::vector<std::vector<int32_t>>> Erho(a, std::vector<std::vector<int32_t>>(b)),
+        Edel(a, std::vector<std::vector<int32_t>>(b));
+
+    // ================= Step 1 =================
+    for (int i = 0; i < a; ++i) {
+        for (int j = 0; j < b; ++j) {
+            const int64_t al = cur[i], bj = bcols[j];
+            const int64_t r = (int64_t)gam[j].size();
+            DMat Cij = sub(X, H, ro[i], co[j], al, bj);
+            // ---------- Task ClearDown ----------
+            EchRes e;
+            std::vector<int32_t> lam;
+            if (i == 0) {
+                DMat Rd = DR[j];
+                ech(X, Cij, AM, AK, Rd, e);
+                gam[j] = e.gamma;
+                lam.assign(e.r, 1);
+            } else {
+                const std::vector<int32_t> &g = gam[j];
+                std::vector<int32_t> ng = complement(g, bj);
+                // (CEX) A.A = C gamma^tr, A' = C gamma_bar^tr
+                j_cols(X, al, r, AA, Cij, g);
+                DMat Hh = sub(X, Hb, 0, 0, al, bj - r);
+                Hh.ld = Hb.ld;
+                j_cols(X, al, bj - r, Hh, Cij, ng);
+                // (MAD) H := A' + A.A x D.R
+                j_mad(X, al, bj - r, r, &Hh, AA, DR[j], Hh);
+                // (ECH)
+                ech(X, Hh, AM, AK, Rech, e);
+                const int64_t rp = e.r;
+                if (rp > 0) {
+                    // (CEX) A.E = D.R gamma'^tr, R' = D.R gamma'_bar^tr
+                    std::vector<int32_t> ngp = complement(e.gamma, bj - r);
+                    j_cols(X, r, rp, AE, DR[j], e.gamma);
+                    j_cols(X, r, bj - r - rp, Rp, DR[j], ngp);
+                    // (MAD) R' := R' + A.E x R
+                    j_mad(X, r, bj - r - rp, rp, &Rp, AE, Rech, Rp);
+                    // (UNH) and (RRF)
+                    std::vector<int32_t> newg;
+                    unh(g, e.gamma, bj, newg, lam);
+                    j_rows(X, r + rp, bj - r - rp, DRsp, Rp, &Rech, riffle_map(lam));
+                    std::swap(DR[j], DRsp);
+                    gam[j] = newg;
+                } else {
+                    lam.assign(r, 0);
+                }
+            }
+            const int64_t rp = e.r;
+            // ---------- Task Extend (UN0 / UNH) ----------
+            unh(j == 0 ? std::vector<int32_t>() : Erho[i][j - 1], e.rho, arows[i], Erho[i][j], Edel[i][j]);
+            std::vector<int32_t> nrho = complement(e.rho, al);
+            // ---------- Task UpdateRow for all k > j at once (row panel) ----------
+            const int64_t wc = beta - co[j + 1];
+            DMat Z = sub(X, H, ro[i], co[j + 1], al, wc);
+            if (wc > 0) {
+                if (i > 0) j_mad(X, al, wc, r, &Z, AA, Bp[j], Z);           // (1) Z := C + A.A x B
+                if (rp > 0) {
+                    DMat Vv = V, Ww = W, Xx = Xb;
+                    Vv.ld = Ww.ld = Xx.ld = wc;
+                    j_rows(X, rp, wc, Vv, Z, nullptr, e.rho);               // (2) REX
+                    j_rows(X, al - rp, wc, Ww, Z, nullptr, nrho);
+                    if (i > 0) {
+                        j_mad(X, rp, wc, rp, nullptr, AM, Vv, Xx);          // (3) X := A.M x V
+                        j_mad(X, r, wc, rp, &Bp[j], AE, Xx, Bp[j]);         // (4) S := B + A.E x X
+                        j_rows(X, r + rp, wc, Bsp, Bp[j], &Xx, riffle_map(lam));  // (5) RRF
+                        std::swap(Bp[j], Bsp);
+                    } else {
+                        j_mad(X, rp, wc, rp, nullptr, AM, Vv, Bp[j]);       // (3)+(5) B := A.M x V
+                    }
+                    j_mad(X, al - rp, wc, rp, &Ww, AK, Vv, Z);              // (6) C := W + A.K x V
+                }
+            }
+            cur[i] = al - rp;
+            rB[j] = r + rp;
+            // ---------- Task UpdateRowTrafo for h = 1..i ----------
+            if (trafo && (rp > 0 || i > 0)) {
+                for (int h = 0; h <= i; ++h) {
+                    const std::vector<int32_t> &del = Edel[h][j];
+                    const int64_t nc = (int64_t)del.size();
+                    DMat Kih = sub(X, Kp[i], 0, ro[h], al, nc);
+                    DMat Mjh = sub(X, Mp[j], 0, ro[h], r, nc);
+                    DMat Zz = Zt;
+                    Zz.ld = nc > 0 ? nc : 1;
+                    const bool first_j = (j == 0);
+                    if (h != i && wM[j][h] != nc) {  // M_jh not stored yet: it is zero
+                        j_zero(X, r, nc, Mjh);
+                        wM[j][h] = nc;
+                    }
+                    // (+) CRZ, (1)
+                    if (!first_j) {
+                        DMat Kold = sub(X, Kp[i], 0, ro[h], al, wK[i][h]);
+                        j_cols(X, al, nc, Zz, Kold, crz_map(del));
+                    }
+                    if (h != i) {
+                        j_mad(X, al, nc, r, first_j ? nullptr : &Zz, AA, Mjh, Zz);
+                    } else if (first_j) {
+                        // Z is 0 (K_ii empty so far)
+                    }
+                    if (rp == 0) {  // nothing pivotal: K := Z, M unchanged
+                        j_copy(X, al, nc, Kih, Zz);
+                        wK[i][h] = nc;
+                        continue;
+                    }
+                    DMat Xx = Xt;
+                    Xx.ld = nc > 0 ? nc : 1;
+                    if (first_j && h == i) {
+                        j_copy(X, rp, nc, Xx, AM);                        // (3) X := A.M   (V is 1)
+                        j_copy(X, al - rp, nc, Kih, AK);                  // (6) K := A.K   (V is 1, W is 0)
+                    } else {
+                        DMat Vv = Vt, Ww = Wt;
+                        Vv.ld = Ww.ld = nc > 0 ? nc : 1;
+                        j_rows(X, rp, nc, Vv, Zz, nullptr, e.rho);          // (2) REX
+                        j_rows(X, al - rp, nc, Ww, Zz, nullptr, nrho);
+                        if (h == i && !X.dry)                                // (+) ADI
+                            set_ones(X.L, rp, Vv.ptr, Vv.ld, X.put(ones_positions(del)));
+                        j_mad(X, rp, nc, rp, nullptr, AM, Vv, Xx);           // (3) X := A.M x V
+                        j_mad(X, al - rp, nc, rp, &Ww, AK, Vv, Kih);         // (6) K := W + A.K x V
+                    }
+                    wK[i][h] = nc;
+                    // (4) S and (5) M := RRF(lambda, S, X)
+                    DMat Mn = sub(X, Msp, 0, ro[h], r + rp, nc);
+                    if (h != i) {
+                        j_mad(X, r, nc, rp, &Mjh, AE, Xx, Mjh);
+                        j_rows(X, r + rp, nc, Mn, Mjh, &Xx, riffle_map(lam));
+                    } else if (i != 0) {
+                        DMat Ss = St;
+                        Ss.ld = nc > 0 ? nc : 1;
+                        j_mad(X, r, nc, rp, nullptr, AE, Xx, Ss);
+                        j_rows(X, r + rp, nc, Mn, Ss, &Xx, riffle_map(lam));
+                    } else {
+                        j_copy(X, rp, nc, Mn, Xx);
+                    }
+                    wM[j][h] = nc;
+                }
+                if (rp > 0) std::swap(Mp[j], Msp);
+            }
+        }
+    }
+
+    // ---- results: rank, Upsilon, varrho, offsets ----
+    int64_t rank = 0;
+    std::vector<int64_t> rowoff(b + 1, 0), nonoff(b + 1, 0), rhooff(a + 1, 0), kroff(a + 1, 0);
+    for (int j = 0; j < b; ++j) {
+        rowoff[j + 1] = rowoff[j] + (int64_t)gam[j].size();
+        nonoff[j + 1] = nonoff[j] + bcols[j] - (int64_t)gam[j].size();
+    }
+    for (int i = 0; i < a; ++i) {
+        rhooff[i + 1] = rhooff[i] + (int64_t)Erho[i][b - 1].size();
+        kroff[i + 1] = kroff[i] + arows[i] - (int64_t)Erho[i][b - 1].size();
+    }
+    rank = rowoff[b];
+    out.r = rank;
+    out.gamma.clear();
+    out.rho.clear();
+    for (int j = 0; j < b; ++j)
+        for (int32_t g : gam[j]) out.gamma.push_back((int32_t)(co[j] + g));
+    for (int i = 0; i < a; ++i)
+        for (int32_t x : Erho[i][b - 1]) out.rho.push_back((int32_t)(ro[i] + x));
+    if (X.dry) {  // worst case: every block keeps all its columns
+        rank = 0;
+    }
+
+    // ================= Step 2: RowLengthen (into the output M) =================
+    if (trafo) {
+        for (int j = 0; j < b; ++j) {
+            const int64_t rj = (int64_t)gam[j].size();
+            for (int h = 0; h < a; ++h) {
+                const std::vector<int32_t> &fin = Erho[h][b - 1];
+                const int64_t nf = (int64_t)fin.size();
+                if (rj == 0 || nf == 0) continue;
+                // MKR: 1 at elements of E_hj.rho inside E_hb.rho; CRZ zeros at the 0s
+                std::vector<int32_t> keep(nf, 0);
+                const std::vector<int32_t> &ej = Erho[h][j];
+                size_t q = 0;
+                for (int64_t t = 0; t < nf; ++t)
+                    if (q < ej.size() && ej[q] == fin[t]) {
+                        keep[t] = 1;
+                        ++q;
+                    }
+                std::vector<int32_t> zmask(nf);
+                for (int64_t t = 0; t < nf; ++t) zmask[t] = !keep[t];
+                DMat dst = sub(X, Mo, rowoff[j], rhooff[h], rj, nf);
+                if (wM[j][h] != (int64_t)ej.size()) {  // never stored: M_jh = 0
+                    j_zero(X, rj, nf, dst);
+                    continue;
+                }
+                DMat src = sub(X, Mp[j], 0, ro[h], rj, wM[j][h]);
+                j_cols(X, rj, nf, dst, src, crz_map(zmask));
+            }
+        }
+        // K output: block row i, slot h (h <= i), zeros for h > i
+        for (int i = 0; i < a; ++i) {
+            const int64_t nk = kroff[i + 1] - kroff[i];
+            if (nk == 0) continue;
+            for (int h = 0; h <= i; ++h) {
+                const int64_t nf = rhooff[h + 1] - rhooff[h];
+                DMat src = sub(X, Kp[i], 0, ro[h], nk, nf);
+                DMat dst = sub(X, Ko, kroff[i], rhooff[h], nk, nf);
+                j_copy(X, nk, nf, dst, src);
+            }
+            if (rank - rhooff[i + 1] > 0)
+                j_zero(X, nk, rank - rhooff[i + 1], sub(X, Ko, kroff[i], rhooff[i + 1], nk, rank - rhooff[i + 1]));
+        }
+    }
+
+    // ================= Step 3: Copy, PreClearUp, ClearUp =================
+    if (wantR) {
+        const int64_t nr = beta - rank;
+        for (int j = 0; j < b; ++j) {  // Copy: R_jj := D_j.R
+            const int64_t rj = (int64_t)gam[j].size();
+            DMat dst = sub(X, Ro, rowoff[j], nonoff[j], rj, bcols[j] - rj);
+            j_copy(X, rj, bcols[j] - rj, dst, DR[j]);
+            // zeros left of the diagonal block (R is block upper triangular)
+            if (nonoff[j] > 0) j_zero(X, rj, nonoff[j], sub(X, Ro, rowoff[j], 0, rj, nonoff[j]));
+        }
+        DMat Xcat = X.mat(std::min(alpha, beta), maxb);
+        for (int k = b - 1; k >= 0; --k) {
+            const int64_t rk = (int64_t)gam[k].size();
+            std::vector<int32_t> ngk = complement(gam[k], bcols[k]);
+            DMat Xc = Xcat;
+            Xc.ld = rk > 0 ? rk : 1;
+            for (int j = 0; j < k; ++j) {  // PreClearUp: (X_jk, R_jk) := CEX(B_jk, D_k.gamma)
+                const int64_t rj = (int64_t)gam[j].size();
+                if (rj == 0) continue;
+                DMat Bjk = sub(X, Bp[j], 0, co[k] - co[j + 1], rj, bcols[k]);
+                j_cols(X, rj, rk, sub(X, Xc, rowoff[j], 0, rj, rk), Bjk, gam[k]);
+                j_cols(X, rj, bcols[k] - rk, sub(X, Ro, rowoff[j], nonoff[k], rj, bcols[k] - rk), Bjk, ngk);
+            }
+            if (rk == 0 || rowoff[k] == 0) continue;
+            // ClearUp for every j < k at once: R_jl += X_jk R_kl (l >= k), M_j += X_jk M_k
+            DMat Rtop = sub(X, Ro, 0, nonoff[k], rowoff[k], nr - nonoff[k]);
+            DMat Rk = sub(X, Ro, rowoff[k], nonoff[k], rk, nr - nonoff[k]);
+            j_mad(X, rowoff[k], nr - nonoff[k], rk, &Rtop, Xc, Rk, Rtop);
+            if (trafo) {
+                DMat Mtop = sub(X, Mo, 0, 0, rowoff[k], rank);
+                DMat Mk = sub(X, Mo, rowoff[k], 0, rk, rank);
+                j_mad(X, rowoff[k], rank, rk, &Mtop, Xc, Mk, Mtop);
+            }
+        }
+    }
+    X.ar.release(mark0);
+}
+
+// ---------------------------------------------------------------------------
+// entry used by the C ABI
+// ---------------------------------------------------------------------------
+static void top_blocks(int64_t m, int64_t n, std::vector<int64_t> &a, std::vector<int64_t> &b) {
+    block_policy(m, n, a, b);
+}
+
+// Runs the method on the (already imported) internal matrix H.
+// Mo/Ko/Ro sized min(m,n) x min(m,n), m x min(m,n), min(m,n) x n.
+void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat &H, bool trafo, bool wantR,
+               const DMat &Mo, const DMat &Ko, const DMat &Ro, TopResult &res, size_t *peak, size_t base_used,
+               int64_t *syncs) {
+    Ctx X;
+    X.L = L;
+    X.dry = dry;
+    X.es = codec_bytes(L.codec);
+    X.ar.dry = dry;
+    X.ar.base = ws;
+    X.ar.cap = ws_bytes;
+    X.ar.top = base_used;
+    X.ar.peak = base_used;
+    if (!dry) {
+        if (!t_pinned) {
+            if (cudaHostAlloc((void **)&t_pinned, STAGE_BYTES + 4096, cudaHostAllocDefault) != cudaSuccess) {
+                t_pinned = nullptr;
+                throw CudaError("cudaHostAlloc of the staging buffer failed");
+            }
+        }
+        // layout of t_pinned: [0, 4096) download area, then the upload ring
+        X.sg.host = t_pinned + 4096;
+    }
+    X.sg.dev = (char *)X.ar.alloc(STAGE_BYTES);
+    std::vector<int64_t> a, b;
+    top_blocks(H.rows, H.cols, a, b);
+    EchRes e;
+    if (H.rows > 0 && H.cols > 0) chief(X, H, a, b, trafo, wantR, Mo, Ko, Ro, e);
+    if (!dry) X.sync();
+    res.r = e.r;
+    res.rho = e.rho;
+    res.gamma = e.gamma;
+    if (peak) *peak = X.ar.peak;
+    if (syncs) *syncs = X.syncs;
+}
+
+}  // namespace gfe

@@ -1,0 +1,111 @@
+// Internal declarations of libgfe (not part of the C ABI).
+//
+// Element storage inside the library ("codec"): the tensor-core operand
+// encoding of the centred residue c in [-(p-1)/2, (p-1)/2]:
+//   CODEC_F8   p <= 31 : one e4m3 byte (|c| <= 15 is exact in e4m3)
+//   CODEC_BF16 p <= 251: one bf16 (|c| <= 125 is exact in bf16)
+// so the tcgen05 multiply-add reads operands straight from HBM.  Zero is the
+// all-zero bit pattern in both.  This is the floating-point representation
+// of field elements the paper mentions as prior art (Section 1), with the
+// reduction mod p done exactly on integer accumulators.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+namespace gfe {
+
+enum Codec { CODEC_F8 = 0, CODEC_BF16 = 1 };
+inline Codec codec_for(int p) { return p <= 31 ? CODEC_F8 : CODEC_BF16; }
+inline int codec_bytes(Codec c) { return c == CODEC_F8 ? 1 : 2; }
+
+// A device matrix in the internal codec: rows x cols, row-major, ld elements.
+struct DMat {
+    void *ptr = nullptr;
+    int64_t rows = 0, cols = 0, ld = 0;
+};
+
+// Kernel kinds for the profile counters (match gfe_profile in gfe.h).
+enum Kind { K_MAD_TC = 0, K_MAD_PLAIN = 1, K_ECH = 2, K_MOVE = 3, K_CONV = 4, K_OTHER = 5 };
+
+struct Launch {  // per-call launch context
+    cudaStream_t st = nullptr;
+    int p = 0;
+    Codec codec = CODEC_F8;
+    int impl = 0;  // 0 tensor cores, 1 plain CUDA-core multiply-add
+};
+
+// ---- profiling (gfe_api.cu) ----
+void prof_begin(const Launch &L, Kind k, cudaEvent_t *ev0);
+void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds);
+void prof_sync_point();
+void prof_count_sync();
+extern bool g_prof_on;
+
+// ---- kernels (gfe_kernels.cu); all asynchronous on L.st ----
+// C := W + A B (mod p); W may be null or equal C; shapes m x k, k x n.
+void mad(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_t ldw,
+         const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc);
+void mad_plain(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_t ldw,
+               const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc);
+// tcgen05 multiply-add (gfe_mma.cu); returns false if the shape is not handled
+bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_t ldw,
+            const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc);
+
+// Leaf echelonisation of H (alpha <= ECH_LEAF_ROWS, beta <= ECH_LEAF_COLS).
+// info[0] = r, info[1..] = rho (r), info[1+cap..] = gamma (r), cap = ECH_LEAF_COLS.
+constexpr int ECH_LEAF_ROWS = 1024;
+constexpr int ECH_LEAF_COLS = 64;
+void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64_t ldh,
+              int32_t *info, void *M, int64_t ldm, void *K, int64_t ldk, void *R, int64_t ldr);
+
+// dst row t = map[t] >= 0 ? A row map[t] : B row (-1 - map[t])   (B may be null if unused)
+void gather_rows(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
+                 const void *A, int64_t lda, const void *B, int64_t ldb, const int32_t *map);
+// dst col t = map[t] >= 0 ? src col map[t] : 0
+void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
+                 const void *src, int64_t lds, const int32_t *map);
+// V[t][pos[t]] := 1 for t < count (job ADI)
+void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const int32_t *pos);
+void copy2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
+            const void *src, int64_t lds);
+void zero2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd);
+
+// conversions between the API storage and the codec
+void import_u8(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
+               const uint8_t *src, int64_t lds);
+void import_bits(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
+                 const uint64_t *src, int64_t ldw);
+void export_u8(const Launch &L, int64_t rows, int64_t cols, uint8_t *dst, int64_t ldd,
+               const void *src, int64_t lds);
+void export_bits(const Launch &L, int64_t rows, int64_t cols, uint64_t *dst, int64_t ldw,
+                 const void *src, int64_t lds);
+// dense E: colmap[c] = l (pivot l) or -1-j (non-pivot j); rows >= r zero.
+void build_E(const Launch &L, int fmt, int64_t m, int64_t n, int64_t r, void *dst, int64_t ldd,
+             const void *R, int64_t ldr, const int32_t *colmap);
+// dense T: rowmap[x] = s (x = rho_s) or -1-t (x = rho_bar_t).
+void build_T(const Launch &L, int fmt, int64_t m, int64_t r, void *dst, int64_t ldd,
+             const void *M, int64_t ldm, const void *K, int64_t ldk, const int32_t *rowmap);
+void write_i64(const Launch &L, int64_t *dst, const int32_t *src, int64_t count, int64_t offset);
+
+// ---- the planner (gfe_chief.cu) ----
+struct TopResult {
+    int64_t r = 0;
+    std::vector<int32_t> rho, gamma;
+};
+// Runs the method on the internal matrix H (destroyed).  Mo, Ko, Ro receive
+// M (min x min), K (m x min), R (min x n) in the codec.  dry = only size the
+// workspace (peak bytes from base_used).
+void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat &H, bool trafo, bool wantR,
+               const DMat &Mo, const DMat &Ko, const DMat &Ro, TopResult &res, size_t *peak, size_t base_used,
+               int64_t *syncs);
+
+extern int64_t g_block_threshold, g_block_big;
+
+// ---- error state (gfe_api.cu) ----
+void set_error(const std::string &s);
+bool cuda_ok(cudaError_t e, const char *what);
+
+}  // namespace gfe

@@ -1,0 +1,631 @@
+// Job kernels of libgfe on CUDA cores: the plain multiply-add (job MAD/MUL),
+// the leaf echelonisation (job ECH), extracts and riffles (CEX, REX, RRF,
+// CRZ, ADI) and the conversions at the API boundary.
+// Jobs: arXiv 1806.04211, Section 4.1.
+#include "gfe_internal.h"
+
+#include <climits>
+
+namespace gfe {
+
+// ---------------------------------------------------------------------------
+// codecs (see gfe_internal.h)
+// ---------------------------------------------------------------------------
+template <int C> struct Cd;
+
+// e4m3: sign | 4-bit exponent (bias 7) | 3-bit mantissa.  Only integers with
+// |c| <= 15 are ever stored, all exact: c = 1.m * 2^(e-7) with e in [7,10].
+template <> struct Cd<CODEC_F8> {
+    using T = uint8_t;
+    __device__ __forceinline__ static int dec(T b) {
+        int mag = b & 0x7F;
+        if (mag < 0x38) return 0;  // only +-0 is stored below 1.0
+        int e = mag >> 3, mt = mag & 7;
+        int v = ((8 + mt) << (e - 7)) >> 3;
+        return (b & 0x80) ? -v : v;
+    }
+    __device__ __forceinline__ static T enc(int c) {
+        if (c == 0) return 0;
+        int s = c < 0, a = s ? -c : c;
+        int e = 31 - __clz(a);
+        int mt = ((a << 3) >> e) - 8;
+        return (T)((s << 7) | ((e + 7) << 3) | mt);
+    }
+};
+
+// bf16: the upper half of the float32; integers |c| <= 256 are exact.
+template <> struct Cd<CODEC_BF16> {
+    using T = uint16_t;
+    __device__ __forceinline__ static int dec(T b) { return (int)__uint_as_float((uint32_t)b << 16); }
+    __device__ __forceinline__ static T enc(int c) { return (T)(__float_as_uint((float)c) >> 16); }
+};
+
+__device__ __forceinline__ int cen(int r, int p) { return r > (p >> 1) ? r - p : r; }
+__device__ __forceinline__ int res(int c, int p) { return c < 0 ? c + p : c; }
+__device__ __forceinline__ int modp(int x, int p) {
+    int r = x % p;
+    return r < 0 ? r + p : r;
+}
+// x in [0, 2^16): x mod p through a float reciprocal, corrected both ways
+__device__ __forceinline__ int modp16(int x, int p, float invp) {
+    int q = (int)((float)x * invp);
+    int r = x - q * p;
+    if (r < 0) r += p;
+    if (r >= p) r -= p;
+    return r;
+}
+
+static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// plain multiply-add  C := W + A B  (mod p)   -- the CUDA-core comparator
+// 64 x 64 tile per CTA, 256 threads, 4 x 4 outputs per thread, int32
+// accumulation of centred products (|c| <= 125): exact for k <= 2^17.
+// ---------------------------------------------------------------------------
+constexpr int PT = 64, PK = 16;
+
+template <int C>
+__global__ void __launch_bounds__(256) k_mad_plain(int p, int M, int N, int K,
+                                                    const typename Cd<C>::T *W, int64_t ldw,
+                                                    const typename Cd<C>::T *A, int64_t lda,
+                                                    const typename Cd<C>::T *B, int64_t ldb,
+                                                    typename Cd<C>::T *Cm, int64_t ldc) {
+    using D = Cd<C>;
+    __shared__ int As[PK][PT + 1];
+    __shared__ int Bs[PK][PT + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * PT, n0 = blockIdx.x * PT;
+    int acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int k0 = 0; k0 < K; k0 += PK) {
+        for (int t = threadIdx.x; t < PT * PK; t += 256) {
+            int mm = t / PK, kk = t % PK, gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < K) ? D::dec(A[(int64_t)gm * lda + gk]) : 0;
+            int kk2 = t / PT, nn = t % PT, gk2 = k0 + kk2, gn = n0 + nn;
+            Bs[kk2][nn] = (gk2 < K && gn < N) ? D::dec(B[(int64_t)gk2 * ldb + gn]) : 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < PK; ++kk) {
+            int a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            int v = acc[i][j] % p;
+            if (W) v += D::dec(W[(int64_t)gm * ldw + gn]);
+            Cm[(int64_t)gm * ldc + gn] = D::enc(cen(modp(v, p), p));
+        }
+    }
+}
+
+void mad_plain(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_t ldw,
+               const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc) {
+    if (m <= 0 || n <= 0) return;
+    if (k <= 0) {  // C := W (or 0)
+        if (!W) zero2d(L, m, n, C, ldc);
+        else if (W != C) copy2d(L, m, n, C, ldc, W, ldw);
+        return;
+    }
+    const int64_t KMAX = 1 << 17;
+    const int es = codec_bytes(L.codec);
+    for (int64_t k0 = 0; k0 < k; k0 += KMAX) {
+        int64_t kk = k - k0 < KMAX ? k - k0 : KMAX;
+        const char *Ak = (const char *)A + k0 * es;
+        const char *Bk = (const char *)B + k0 * ldb * es;
+        const void *Wk = k0 ? C : W;
+        int64_t ldwk = k0 ? ldc : ldw;
+        dim3 grid(cdiv(n, PT), cdiv(m, PT));
+        cudaEvent_t ev;
+        prof_begin(L, K_MAD_PLAIN, &ev);
+        if (L.codec == CODEC_F8)
+            k_mad_plain<CODEC_F8><<<grid, 256, 0, L.st>>>(L.p, (int)m, (int)n, (int)kk,
+                (const uint8_t *)Wk, ldwk, (const uint8_t *)Ak, lda, (const uint8_t *)Bk, ldb,
+                (uint8_t *)C, ldc);
+        else
+            k_mad_plain<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, (int)m, (int)n, (int)kk,
+                (const uint16_t *)Wk, ldwk, (const uint16_t *)Ak, lda, (const uint16_t *)Bk, ldb,
+                (uint16_t *)C, ldc);
+        prof_end(L, K_MAD_PLAIN, ev, (double)m * (double)n * (double)kk);
+    }
+}
+
+void mad(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_t ldw,
+         const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc) {
+    if (m <= 0 || n <= 0) return;
+    if (L.impl == 0 && k > 0 && mad_tc(L, m, n, k, W, ldw, A, lda, B, ldb, C, ldc)) return;
+    mad_plain(L, m, n, k, W, ldw, A, lda, B, ldb, C, ldc);
+}
+
+// ---------------------------------------------------------------------------
+// leaf echelonisation (job ECH, Remark "echelon") of H: alpha x beta with
+// alpha <= 1024, beta <= 64, one CTA of 1024 threads, one thread per row.
+// Column-by-column Gauss-Jordan; the pivot of column c is the topmost
+// non-pivot row with a non-zero entry there, which yields the row rank
+// profile and the column rank profile, i.e. the unique result of Eq. (gauss).
+// The transformation is kept in "slot" space: slot t = the t-th pivot found
+// (= the t-th pivot column), so each row carries <= 64 coefficients.
+// ---------------------------------------------------------------------------
+constexpr int LS = 68;  // smem row stride (bytes): 17 words -> conflict-free rows
+
+template <int C>
+__global__ void __launch_bounds__(1024, 1) k_ech_leaf(int p, int alpha, int beta,
+                                                      const typename Cd<C>::T *H, int64_t ldh,
+                                                      int32_t *info, typename Cd<C>::T *Mo,
+                                                      int64_t ldm, typename Cd<C>::T *Ko,
+                                                      int64_t ldk, typename Cd<C>::T *Ro,
+                                                      int64_t ldr) {
+    using D = Cd<C>;
+    extern __shared__ uint8_t sm[];
+    uint8_t *S = sm;                           // [1024][LS]  residues of H
+    uint8_t *Tt = sm + 1024 * LS;              // [1024][LS]  slot coefficients
+    __shared__ uint8_t inv[256];
+    __shared__ uint8_t piv[1024];
+    __shared__ int16_t slotOf[1024];
+    __shared__ int16_t pivpos[1024];           // rank among pivot / non-pivot rows
+    __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
+    __shared__ int best[3];
+    __shared__ int wsum[32];
+    const int y = threadIdx.x, lane = y & 31, warp = y >> 5;
+    const float invp = 1.0f / (float)p;
+
+    if (y < p) {
+        int v = 0;
+        for (int x = 1; x < p; ++x)
+            if ((y * x) % p == 1) v = x;
+        inv[y] = (uint8_t)v;
+    }
+    if (y < 3) best[y] = INT_MAX;
+    piv[y] = 0;
+    slotOf[y] = -1;
+    if (y < alpha) {
+        for (int c = 0; c < beta; ++c) S[y * LS + c] = (uint8_t)res(D::dec(H[(int64_t)y * ldh + c]), p);
+        for (int c = 0; c < 64; ++c) Tt[y * LS + c] = 0;
+    }
+    __syncthreads();
+
+    int ns = 0;
+    for (int c = 0; c < beta; ++c) {
+        // three rotating slots: the one reset here was last read two columns
+        // ago, before the barrier every thread has since passed
+        if (y == 0) best[(c + 1) % 3] = INT_MAX;
+        int cand = (y < alpha) && !piv[y] && S[y * LS + c] != 0;
+        unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0 && bal) atomicMin(&best[c % 3], warp * 32 + __ffs(bal) - 1);
+        __syncthreads();
+        const int x = best[c % 3];
+        if (x == INT_MAX) continue;  // uniform: column c has no pivot
+        if (y == x) {
+            int s = p - inv[S[x * LS + c]];  // scale so that the pivot becomes -1
+            if (s == p) s = 0;
+            for (int cc = c; cc < beta; ++cc) S[x * LS + cc] = (uint8_t)modp16(S[x * LS + cc] * s, p, invp);
+            Tt[x * LS + ns] = 1;
+            for (int t = 0; t <= ns; ++t) Tt[x * LS + t] = (uint8_t)modp16(Tt[x * LS + t] * s, p, invp);
+            piv[x] = 1;
+            slotOf[x] = (int16_t)ns;
+            slotRow[ns] = (int16_t)x;
+            slotCol[ns] = (int16_t)c;
+        }
+        __syncthreads();
+        if (y < alpha && y != x) {
+            int f = S[y * LS + c];
+            if (f) {
+                const uint8_t *px = S + x * LS;
+                uint8_t *py = S + y * LS;
+                for (int cc = c; cc < beta; ++cc) py[cc] = (uint8_t)modp16(py[cc] + f * px[cc], p, invp);
+                const uint8_t *tx = Tt + x * LS;
+                uint8_t *ty = Tt + y * LS;
+                for (int t = 0; t <= ns; ++t) ty[t] = (uint8_t)modp16(ty[t] + f * tx[t], p, invp);
+            }
+        }
+        ++ns;
+    }
+    __syncthreads();
+    const int r = ns;
+    // rank of each row among pivot rows (ascending) and among non-pivot rows
+    int isp = (y < alpha) && piv[y];
+    unsigned bal = __ballot_sync(0xffffffffu, isp);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    before += __popc(bal & ((1u << lane) - 1));
+    if (y < alpha) {
+        if (isp) {
+            pivpos[y] = (int16_t)before;
+            sortedSlot[before] = slotOf[y];
+            info[1 + before] = y;
+        } else {
+            pivpos[y] = (int16_t)(y - before);
+        }
+    }
+    if (y == 0) {
+        info[0] = r;
+        int j = 0, l = 0;
+        for (int c = 0; c < beta; ++c) {
+            if (l < r && slotCol[l] == c) ++l;
+            else nonCol[j++] = (int16_t)c;
+        }
+    }
+    if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
+    __syncthreads();
+    // M[l][s] = coefficient of pivot row rho_s in echelon row l
+    for (int idx = y; idx < r * r; idx += 1024) {
+        int l = idx / r, s = idx % r;
+        Mo[(int64_t)l * ldm + s] = D::enc(cen(Tt[slotRow[l] * LS + sortedSlot[s]], p));
+    }
+    // K[t][s] for the non-pivot rows t
+    if (r > 0) {
+        for (int64_t idx = y; idx < (int64_t)alpha * r; idx += 1024) {
+            int row = (int)(idx / r), s = (int)(idx % r);
+            if (piv[row]) continue;
+            Ko[(int64_t)pivpos[row] * ldk + s] = D::enc(cen(Tt[row * LS + sortedSlot[s]], p));
+        }
+    }
+    // R[l][j] = entry of echelon row l in the j-th non-pivot column
+    const int nr = beta - r;
+    for (int idx = y; idx < r * nr; idx += 1024) {
+        int l = idx / nr, j = idx % nr;
+        Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
+    }
+}
+
+void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64_t ldh,
+              int32_t *info, void *M, int64_t ldm, void *K, int64_t ldk, void *R, int64_t ldr) {
+    const int smem = 2 * 1024 * LS;
+    static bool attr_set[2] = {false, false};
+    cudaEvent_t ev;
+    prof_begin(L, K_ECH, &ev);
+    if (L.codec == CODEC_F8) {
+        if (!attr_set[0]) {
+            cudaFuncSetAttribute(k_ech_leaf<CODEC_F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            attr_set[0] = true;
+        }
+        k_ech_leaf<CODEC_F8><<<1, 1024, smem, L.st>>>(L.p, (int)alpha, (int)beta,
+            (const uint8_t *)H, ldh, info, (uint8_t *)M, ldm, (uint8_t *)K, ldk, (uint8_t *)R, ldr);
+    } else {
+        if (!attr_set[1]) {
+            cudaFuncSetAttribute(k_ech_leaf<CODEC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            attr_set[1] = true;
+        }
+        k_ech_leaf<CODEC_BF16><<<1, 1024, smem, L.st>>>(L.p, (int)alpha, (int)beta,
+            (const uint16_t *)H, ldh, info, (uint16_t *)M, ldm, (uint16_t *)K, ldk, (uint16_t *)R, ldr);
+    }
+    prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta));
+}
+
+// ---------------------------------------------------------------------------
+// extracts / riffles (jobs REX, RRF, CEX, CRZ, ADI) -- pure data movement
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_gather_rows(int64_t nrows, int64_t ncols, T *dst, int64_t ldd, const T *A,
+                              int64_t lda, const T *B, int64_t ldb, const int32_t *map) {
+    for (int64_t row = blockIdx.y; row < nrows; row += gridDim.y) {
+        int32_t s = map[row];
+        const T *src = s >= 0 ? A + (int64_t)s * lda : B + (int64_t)(-1 - s) * ldb;
+        T *d = dst + row * ldd;
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += (int64_t)gridDim.x * blockDim.x)
+            d[c] = src[c];
+    }
+}
+
+template <typename T>
+__global__ void k_gather_cols(int64_t nrows, int64_t ncols, T *dst, int64_t ldd, const T *src,
+                              int64_t lds, const int32_t *map) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    int32_t s = map[c];
+    for (int64_t row = blockIdx.y; row < nrows; row += gridDim.y)
+        dst[row * ldd + c] = s >= 0 ? src[row * lds + s] : (T)0;
+}
+
+template <typename T>
+__global__ void k_set_ones(int64_t count, T *V, int64_t ldv, const int32_t *pos, T one) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) V[t * ldv + pos[t]] = one;
+}
+
+template <typename T>
+__global__ void k_copy2d(int64_t rows, int64_t cols, T *dst, int64_t ldd, const T *src, int64_t lds) {
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += (int64_t)gridDim.x * blockDim.x)
+            dst[row * ldd + c] = src ? src[row * lds + c] : (T)0;
+}
+
+static dim3 grid_rc(int64_t rows, int64_t cols, int threads) {
+    unsigned gx = cdiv(cols, threads);
+    if (gx > 64) gx = 64;
+    unsigned gy = (unsigned)(rows < 65535 ? rows : 65535);
+    return dim3(gx, gy);
+}
+
+void gather_rows(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
+                 const void *A, int64_t lda, const void *B, int64_t ldb, const int32_t *map) {
+    if (nrows <= 0 || ncols <= 0) return;
+    // one CTA row per output row (nrows <= 65535 always holds: rows <= blocks)
+    dim3 grid(cdiv(ncols, 256) > 64 ? 64 : cdiv(ncols, 256), (unsigned)(nrows < 65535 ? nrows : 65535));
+    cudaEvent_t ev;
+    prof_begin(L, K_MOVE, &ev);
+    if (L.codec == CODEC_F8)
+        k_gather_rows<uint8_t><<<grid, 256, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
+            (const uint8_t *)A, lda, (const uint8_t *)B, ldb, map);
+    else
+        k_gather_rows<uint16_t><<<grid, 256, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
+            (const uint16_t *)A, lda, (const uint16_t *)B, ldb, map);
+    prof_end(L, K_MOVE, ev, 0);
+}
+
+void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
+                 const void *src, int64_t lds, const int32_t *map) {
+    if (nrows <= 0 || ncols <= 0) return;
+    dim3 grid(cdiv(ncols, 128), (unsigned)(nrows < 4096 ? nrows : 4096));
+    cudaEvent_t ev;
+    prof_begin(L, K_MOVE, &ev);
+    if (L.codec == CODEC_F8)
+        k_gather_cols<uint8_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
+            (const uint8_t *)src, lds, map);
+    else
+        k_gather_cols<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
+            (const uint16_t *)src, lds, map);
+    prof_end(L, K_MOVE, ev, 0);
+}
+
+void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const int32_t *pos) {
+    if (count <= 0) return;
+    cudaEvent_t ev;
+    prof_begin(L, K_MOVE, &ev);
+    if (L.codec == CODEC_F8)
+        k_set_ones<uint8_t><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint8_t *)V, ldv, pos, (uint8_t)0x38);
+    else
+        k_set_ones<uint16_t><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint16_t *)V, ldv, pos, (uint16_t)0x3F80);
+    prof_end(L, K_MOVE, ev, 0);
+}
+
+void copy2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd, const void *src,
+            int64_t lds) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 grid = grid_rc(rows, cols, 256);
+    cudaEvent_t ev;
+    prof_begin(L, K_MOVE, &ev);
+    if (L.codec == CODEC_F8)
+        k_copy2d<uint8_t><<<grid, 256, 0, L.st>>>(rows, cols, (uint8_t *)dst, ldd, (const uint8_t *)src, lds);
+    else
+        k_copy2d<uint16_t><<<grid, 256, 0, L.st>>>(rows, cols, (uint16_t *)dst, ldd, (const uint16_t *)src, lds);
+    prof_end(L, K_MOVE, ev, 0);
+}
+
+void zero2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd) {
+    copy2d(L, rows, cols, dst, ldd, nullptr, 0);
+}
+
+// ---------------------------------------------------------------------------
+// conversions at the API boundary (jobs "pack and partition", output assembly)
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void k_import_u8(int p, int64_t rows, int64_t cols, typename Cd<C>::T *dst, int64_t ldd,
+                            const uint8_t *src, int64_t lds) {
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += (int64_t)gridDim.x * blockDim.x)
+            dst[row * ldd + c] = Cd<C>::enc(cen(src[row * lds + c], p));
+}
+
+template <int C>
+__global__ void k_import_bits(int64_t rows, int64_t cols, typename Cd<C>::T *dst, int64_t ldd,
+                              const uint64_t *src, int64_t ldw) {
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += (int64_t)gridDim.x * blockDim.x)
+            dst[row * ldd + c] = Cd<C>::enc((int)((src[row * ldw + (c >> 6)] >> (c & 63)) & 1u));
+}
+
+template <int C>
+__global__ void k_export_u8(int p, int64_t rows, int64_t cols, uint8_t *dst, int64_t ldd,
+                            const typename Cd<C>::T *src, int64_t lds) {
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += (int64_t)gridDim.x * blockDim.x)
+            dst[row * ldd + c] = (uint8_t)res(Cd<C>::dec(src[row * lds + c]), p);
+}
+
+template <int C>
+__global__ void k_export_bits(int64_t rows, int64_t cols, uint64_t *dst, int64_t ldw,
+                              const typename Cd<C>::T *src, int64_t lds) {
+    int64_t nw = (cols + 63) >> 6;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
+        for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+            uint64_t v = 0;
+            int64_t c0 = w << 6;
+            int n = cols - c0 < 64 ? (int)(cols - c0) : 64;
+            for (int b = 0; b < n; ++b)
+                v |= (uint64_t)(Cd<C>::dec(src[row * lds + c0 + b]) & 1) << b;
+            dst[row * ldw + w] = v;
+        }
+}
+
+void import_u8(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
+               const uint8_t *src, int64_t lds) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 grid = grid_rc(rows, cols, 256);
+    cudaEvent_t ev;
+    prof_begin(L, K_CONV, &ev);
+    if (L.codec == CODEC_F8)
+        k_import_u8<CODEC_F8><<<grid, 256, 0, L.st>>>(L.p, rows, cols, (uint8_t *)dst, ldd, src, lds);
+    else
+        k_import_u8<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, rows, cols, (uint16_t *)dst, ldd, src, lds);
+    prof_end(L, K_CONV, ev, 0);
+}
+
+void import_bits(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
+                 const uint64_t *src, int64_t ldw) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 grid = grid_rc(rows, cols, 256);
+    cudaEvent_t ev;
+    prof_begin(L, K_CONV, &ev);
+    k_import_bits<CODEC_F8><<<grid, 256, 0, L.st>>>(rows, cols, (uint8_t *)dst, ldd, src, ldw);
+    prof_end(L, K_CONV, ev, 0);
+}
+
+void export_u8(const Launch &L, int64_t rows, int64_t cols, uint8_t *dst, int64_t ldd,
+               const void *src, int64_t lds) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 grid = grid_rc(rows, cols, 256);
+    cudaEvent_t ev;
+    prof_begin(L, K_CONV, &ev);
+    if (L.codec == CODEC_F8)
+        k_export_u8<CODEC_F8><<<grid, 256, 0, L.st>>>(L.p, rows, cols, dst, ldd, (const uint8_t *)src, lds);
+    else
+        k_export_u8<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, rows, cols, dst, ldd, (const uint16_t *)src, lds);
+    prof_end(L, K_CONV, ev, 0);
+}
+
+void export_bits(const Launch &L, int64_t rows, int64_t cols, uint64_t *dst, int64_t ldw,
+                 const void *src, int64_t lds) {
+    if (rows <= 0) return;
+    int64_t nw = (cols + 63) >> 6;
+    if (nw <= 0) return;
+    dim3 grid = grid_rc(rows, nw, 128);
+    cudaEvent_t ev;
+    prof_begin(L, K_CONV, &ev);
+    k_export_bits<CODEC_F8><<<grid, 128, 0, L.st>>>(rows, cols, dst, ldw, (const uint8_t *)src, lds);
+    prof_end(L, K_CONV, ev, 0);
+}
+
+// dense E and T in the API storage
+template <int C>
+__global__ void k_build_E_u8(int p, int64_t m, int64_t n, int64_t r, uint8_t *dst, int64_t ldd,
+                             const typename Cd<C>::T *R, int64_t ldr, const int32_t *colmap) {
+    for (int64_t row = blockIdx.y; row < m; row += gridDim.y)
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+            uint8_t v = 0;
+            if (row < r) {
+                int32_t q = colmap[c];
+                if (q >= 0) v = (q == row) ? (uint8_t)(p - 1) : 0;
+                else v = (uint8_t)res(Cd<C>::dec(R[row * ldr + (-1 - q)]), p);
+            }
+            dst[row * ldd + c] = v;
+        }
+}
+
+template <int C>
+__global__ void k_build_E_bits(int64_t m, int64_t n, int64_t r, uint64_t *dst, int64_t ldw,
+                               const typename Cd<C>::T *R, int64_t ldr, const int32_t *colmap) {
+    int64_t nw = (n + 63) >> 6;
+    for (int64_t row = blockIdx.y; row < m; row += gridDim.y)
+        for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+            uint64_t v = 0;
+            if (row < r) {
+                int64_t c0 = w << 6;
+                int nb = n - c0 < 64 ? (int)(n - c0) : 64;
+                for (int b = 0; b < nb; ++b) {
+                    int32_t q = colmap[c0 + b];
+                    int bit = q >= 0 ? (q == row) : (Cd<C>::dec(R[row * ldr + (-1 - q)]) & 1);
+                    v |= (uint64_t)bit << b;
+                }
+            }
+            dst[row * ldw + w] = v;
+        }
+}
+
+template <int C>
+__global__ void k_build_T_u8(int p, int64_t m, int64_t r, uint8_t *dst, int64_t ldd,
+                             const typename Cd<C>::T *M, int64_t ldm, const typename Cd<C>::T *K,
+                             int64_t ldk, const int32_t *rowmap) {
+    for (int64_t row = blockIdx.y; row < m; row += gridDim.y)
+        for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m; x += (int64_t)gridDim.x * blockDim.x) {
+            int32_t q = rowmap[x];
+            int v;
+            if (row < r) v = q >= 0 ? res(Cd<C>::dec(M[row * ldm + q]), p) : 0;
+            else v = q >= 0 ? res(Cd<C>::dec(K[(row - r) * ldk + q]), p) : ((-1 - q) == row - r ? 1 : 0);
+            dst[row * ldd + x] = (uint8_t)v;
+        }
+}
+
+template <int C>
+__global__ void k_build_T_bits(int64_t m, int64_t r, uint64_t *dst, int64_t ldw,
+                               const typename Cd<C>::T *M, int64_t ldm, const typename Cd<C>::T *K,
+                               int64_t ldk, const int32_t *rowmap) {
+    int64_t nw = (m + 63) >> 6;
+    for (int64_t row = blockIdx.y; row < m; row += gridDim.y)
+        for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+            uint64_t v = 0;
+            int64_t x0 = w << 6;
+            int nb = m - x0 < 64 ? (int)(m - x0) : 64;
+            for (int b = 0; b < nb; ++b) {
+                int32_t q = rowmap[x0 + b];
+                int bit;
+                if (row < r) bit = q >= 0 ? (Cd<C>::dec(M[row * ldm + q]) & 1) : 0;
+                else bit = q >= 0 ? (Cd<C>::dec(K[(row - r) * ldk + q]) & 1) : ((-1 - q) == row - r);
+                v |= (uint64_t)bit << b;
+            }
+            dst[row * ldw + w] = v;
+        }
+}
+
+void build_E(const Launch &L, int fmt, int64_t m, int64_t n, int64_t r, void *dst, int64_t ldd,
+             const void *R, int64_t ldr, const int32_t *colmap) {
+    if (m <= 0 || n <= 0) return;
+    cudaEvent_t ev;
+    prof_begin(L, K_CONV, &ev);
+    if (fmt == 1) {
+        int64_t nw = (n + 63) >> 6;
+        k_build_E_bits<CODEC_F8><<<grid_rc(m, nw, 128), 128, 0, L.st>>>(m, n, r, (uint64_t *)dst, ldd / 8,
+                                                                         (const uint8_t *)R, ldr, colmap);
+    } else if (L.codec == CODEC_F8) {
+        k_build_E_u8<CODEC_F8><<<grid_rc(m, n, 256), 256, 0, L.st>>>(L.p, m, n, r, (uint8_t *)dst, ldd,
+                                                                      (const uint8_t *)R, ldr, colmap);
+    } else {
+        k_build_E_u8<CODEC_BF16><<<grid_rc(m, n, 256), 256, 0, L.st>>>(L.p, m, n, r, (uint8_t *)dst, ldd,
+                                                                        (const uint16_t *)R, ldr, colmap);
+    }
+    prof_end(L, K_CONV, ev, 0);
+}
+
+void build_T(const Launch &L, int fmt, int64_t m, int64_t r, void *dst, int64_t ldd, const void *M,
+             int64_t ldm, const void *K, int64_t ldk, const int32_t *rowmap) {
+    if (m <= 0) return;
+    cudaEvent_t ev;
+    prof_begin(L, K_CONV, &ev);
+    if (fmt == 1) {
+        int64_t nw = (m + 63) >> 6;
+        k_build_T_bits<CODEC_F8><<<grid_rc(m, nw, 128), 128, 0, L.st>>>(m, r, (uint64_t *)dst, ldd / 8,
+            (const uint8_t *)M, ldm, (const uint8_t *)K, ldk, rowmap);
+    } else if (L.codec == CODEC_F8) {
+        k_build_T_u8<CODEC_F8><<<grid_rc(m, m, 256), 256, 0, L.st>>>(L.p, m, r, (uint8_t *)dst, ldd,
+            (const uint8_t *)M, ldm, (const uint8_t *)K, ldk, rowmap);
+    } else {
+        k_build_T_u8<CODEC_BF16><<<grid_rc(m, m, 256), 256, 0, L.st>>>(L.p, m, r, (uint8_t *)dst, ldd,
+            (const uint16_t *)M, ldm, (const uint16_t *)K, ldk, rowmap);
+    }
+    prof_end(L, K_CONV, ev, 0);
+}
+
+__global__ void k_write_i64(int64_t *dst, const int32_t *src, int64_t count, int64_t offset) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) dst[t] = (int64_t)src[t] + offset;
+}
+
+void write_i64(const Launch &L, int64_t *dst, const int32_t *src, int64_t count, int64_t offset) {
+    if (count <= 0) return;
+    cudaEvent_t ev;
+    prof_begin(L, K_OTHER, &ev);
+    k_write_i64<<<cdiv(count, 256), 256, 0, L.st>>>(dst, src, count, offset);
+    prof_end(L, K_OTHER, ev, 0);
+}
+
+}  // namespace gfe

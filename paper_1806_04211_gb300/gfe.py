@@ -1,0 +1,246 @@
+"""Thin ctypes binding of libgfe (include/gfe.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module
+allocates the output / workspace tensors with PyTorch, passes raw device
+pointers and the current CUDA stream, and slices the results to the rank.
+If libgfe.so is missing the import of a function raises -- there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgfe.so")
+
+GFE_U8, GFE_BITS64 = 0, 1
+WANT_TRANSFORM, WANT_DENSE_E, WANT_DENSE_T = 0x1, 0x2, 0x4
+IMPL_PLAIN, IMPL_TENSOR = 0x100, 0x200
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "timeout", 4: "busy",
+          5: "CUDA error", 6: "internal error", 7: "not supported"}
+
+_i64, _i32, _vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+
+
+class GfeMatrix(ctypes.Structure):
+    _fields_ = [("p", _i32), ("m", _i64), ("n", _i64), ("fmt", _i32), ("data", _vp), ("ld", _i64)]
+
+
+class GfeResult(ctypes.Structure):
+    _fields_ = [("rank", _vp), ("pivot_cols", _vp), ("pivot_rows", _vp),
+                ("R", _vp), ("ldR", _i64), ("M", _vp), ("ldM", _i64), ("K", _vp), ("ldK", _i64),
+                ("E", _vp), ("ldE", _i64), ("T", _vp), ("ldT", _i64)]
+
+
+class GfeProfile(ctypes.Structure):
+    _fields_ = [("launches", _i64 * 8), ("ms", ctypes.c_double * 8), ("madds", ctypes.c_double * 8),
+                ("host_syncs", _i64)]
+
+
+# every symbol declared in include/gfe.h, with its ctypes signature
+SIGNATURES = {
+    "gfe_query_workspace": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]),
+    "gfe_echelon": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), ctypes.c_uint32, _vp,
+                           ctypes.c_size_t, _vp]),
+    "gfe_rank": (_i32, [ctypes.POINTER(GfeMatrix), _vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_size_t, _vp]),
+    "gfe_query_batch_workspace": (_i32, [ctypes.POINTER(GfeMatrix), _i32, ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_size_t)]),
+    "gfe_batch_echelon": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), _i32, ctypes.c_uint32,
+                                 _vp, ctypes.c_size_t, _vp]),
+    "gfe_mad_workspace": (ctypes.c_size_t, [_i32, _i64, _i64, _i64]),
+    "gfe_mad": (_i32, [_i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_uint32,
+                       _vp, ctypes.c_size_t, _vp]),
+    "gfe_set_block_policy": (_i32, [_i64, _i64]),
+    "gfe_profile_enable": (_i32, [_i32]),
+    "gfe_profile_read": (_i32, [ctypes.POINTER(GfeProfile), _i32]),
+    "gfe_status_str": (ctypes.c_char_p, [_i32]),
+    "gfe_last_error": (ctypes.c_char_p, []),
+    "gfe_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class GfeError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libgfe.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise GfeError("libgfe.so is not built; run paper_1806_04211_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status:
+        raise GfeError("%s: %s" % (STATUS.get(status, status), lib().gfe_last_error().decode()))
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def words_per_row(n: int) -> int:
+    w = (n + 63) // 64
+    return w + (w & 1)
+
+
+def matrix_arg(A: torch.Tensor, p: int, n: int | None = None) -> GfeMatrix:
+    """uint8 (m x n) residues, or for p = 2 int64 words (m x ldw) with n given."""
+    if A.dtype == torch.uint8:
+        m, nn = A.shape
+        assert A.stride(1) == 1
+        return GfeMatrix(p, m, nn, GFE_U8, A.data_ptr() if A.numel() else None, max(A.stride(0), nn, 1))
+    if A.dtype in (torch.int64,):
+        assert p == 2 and n is not None and A.stride(1) == 1
+        m = A.shape[0]
+        return GfeMatrix(p, m, n, GFE_BITS64, A.data_ptr() if A.numel() else None, 8 * max(A.stride(0), 1))
+    raise TypeError("A must be uint8 residues or int64 GF(2) words")
+
+
+_ws_cache = {}
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    key = (str(device),)
+    t = _ws_cache.get(key)
+    if t is None or t.numel() < nbytes:
+        _ws_cache.pop(key, None)
+        t = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+        _ws_cache[key] = t
+    return t
+
+
+def query_workspace(A: torch.Tensor, p: int, n: int | None = None, flags: int = WANT_TRANSFORM) -> int:
+    mat = matrix_arg(A, p, n)
+    out = ctypes.c_size_t(0)
+    _check(lib().gfe_query_workspace(ctypes.byref(mat), flags, ctypes.byref(out)))
+    return out.value
+
+
+def _impl_flag(impl: str) -> int:
+    return {"tensor": 0, "plain": IMPL_PLAIN}[impl]
+
+
+def echelon(A: torch.Tensor, p: int, n: int | None = None, transform: bool = True, dense_E: bool = False,
+            dense_T: bool = False, impl: str = "tensor", stream=None) -> dict:
+    """Echelon form with transformation (gfe_echelon); results on A's device.
+
+    Returns rank (int), rho, ups (int64), R, M, K (and E, T) in A's storage:
+    uint8 residues, or for GF(2) int64 bit-packed rows."""
+    mat = matrix_arg(A, p, n)
+    m, nn = mat.m, mat.n
+    mn = min(m, nn)
+    dev = A.device
+    bits = mat.fmt == GFE_BITS64
+    flags = (WANT_TRANSFORM if (transform or dense_T) else 0) | (WANT_DENSE_E if dense_E else 0) | \
+        (WANT_DENSE_T if dense_T else 0) | _impl_flag(impl)
+
+    def out(rows, cols):
+        if bits:
+            return torch.zeros((max(rows, 1), words_per_row(max(cols, 1))), dtype=torch.int64, device=dev)
+        return torch.zeros((max(rows, 1), max(cols, 1)), dtype=torch.uint8, device=dev)
+
+    rank = torch.zeros(1, dtype=torch.int64, device=dev)
+    pc = torch.zeros(max(mn, 1), dtype=torch.int64, device=dev)
+    pr = torch.zeros(max(mn, 1), dtype=torch.int64, device=dev)
+    R = out(mn, nn)
+    M = out(mn, mn) if transform else None
+    K = out(m, mn) if transform else None
+    E = out(m, nn) if dense_E else None
+    T = out(m, m) if dense_T else None
+    es = 8 if bits else 1
+
+    def ld(t):
+        return 0 if t is None else t.stride(0) * es
+
+    res = GfeResult(rank.data_ptr(), pc.data_ptr(), pr.data_ptr(), _ptr(R), ld(R), _ptr(M), ld(M), _ptr(K), ld(K),
+                    _ptr(E), ld(E), _ptr(T), ld(T))
+    need = ctypes.c_size_t(0)
+    _check(lib().gfe_query_workspace(ctypes.byref(mat), flags, ctypes.byref(need)))
+    ws = _workspace(need.value, dev)
+    _check(lib().gfe_echelon(ctypes.byref(mat), ctypes.byref(res), flags, ws.data_ptr(), ws.numel(), _stream(stream)))
+    r = int(rank.item())
+
+    def cut(t, rows, cols):
+        if t is None:
+            return None
+        if bits:
+            return t[:rows, :words_per_row(cols)] if rows else t[:0]
+        return t[:rows, :cols]
+
+    d = dict(rank=r, ups=pc[:r], rho=pr[:r], R=cut(R, r, nn - r))
+    if transform:
+        d["M"] = cut(M, r, r)
+        d["K"] = cut(K, m - r, r)
+    if dense_E:
+        d["E"] = E[:m]
+    if dense_T:
+        d["T"] = T[:m]
+    return d
+
+
+def rank(A: torch.Tensor, p: int, n: int | None = None, impl: str = "tensor", stream=None) -> dict:
+    """Rank and pivots only (gfe_rank)."""
+    mat = matrix_arg(A, p, n)
+    mn = min(mat.m, mat.n)
+    dev = A.device
+    rk = torch.zeros(1, dtype=torch.int64, device=dev)
+    pc = torch.zeros(max(mn, 1), dtype=torch.int64, device=dev)
+    pr = torch.zeros(max(mn, 1), dtype=torch.int64, device=dev)
+    need = ctypes.c_size_t(0)
+    _check(lib().gfe_query_workspace(ctypes.byref(mat), 0, ctypes.byref(need)))
+    ws = _workspace(need.value, dev)
+    _check(lib().gfe_rank(ctypes.byref(mat), rk.data_ptr(), pc.data_ptr(), pr.data_ptr(), _impl_flag(impl),
+                          ws.data_ptr(), ws.numel(), _stream(stream)))
+    r = int(rk.item())
+    return dict(rank=r, ups=pc[:r], rho=pr[:r])
+
+
+def mad(W, A: torch.Tensor, B: torch.Tensor, p: int, impl: str = "tensor", out=None, stream=None) -> torch.Tensor:
+    """C := W + A B over GF(p) on uint8 residues (gfe_mad); W may be None."""
+    m, k = A.shape
+    n = B.shape[1]
+    C = out if out is not None else torch.empty((m, n), dtype=torch.uint8, device=A.device)
+    need = lib().gfe_mad_workspace(p, m, n, k)
+    ws = _workspace(need, A.device)
+    _check(lib().gfe_mad(p, m, n, k, _ptr(W), W.stride(0) if W is not None else 0, _ptr(A), A.stride(0), _ptr(B),
+                         B.stride(0), C.data_ptr(), C.stride(0), _impl_flag(impl), ws.data_ptr(), ws.numel(),
+                         _stream(stream)))
+    return C
+
+
+def set_block_policy(threshold: int = 0, block: int = 0):
+    """Block partition policy (gfe_set_block_policy); 0, 0 = defaults."""
+    _check(lib().gfe_set_block_policy(threshold, block))
+
+
+def profile_enable(on: bool = True):
+    _check(lib().gfe_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = True) -> dict:
+    pr = GfeProfile()
+    _check(lib().gfe_profile_read(ctypes.byref(pr), 1 if reset else 0))
+    kinds = ["mad_tensor", "mad_plain", "ech_leaf", "move", "convert", "other"]
+    return dict(launches={k: pr.launches[i] for i, k in enumerate(kinds)},
+                ms={k: pr.ms[i] for i, k in enumerate(kinds)},
+                madds={k: pr.madds[i] for i, k in enumerate(kinds)},
+                host_syncs=pr.host_syncs)

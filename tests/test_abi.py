@@ -1,0 +1,79 @@
+"""The C-ABI library builds, loads and exports every symbol include/gfe.h
+declares; host-side argument checks and workspace planning (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+from paper_1806_04211_gb300 import build, gfe
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "gfe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gfe_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_build_and_load():
+    path = build.build()
+    assert os.path.exists(path)
+    assert gfe.lib().gfe_version().startswith(b"gfe")
+
+
+def test_every_declared_symbol_is_exported():
+    L = gfe.lib()
+    names = header_functions()
+    assert "gfe_echelon" in names and "gfe_rank" in names and "gfe_mad" in names
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(gfe.SIGNATURES), set(names) ^ set(gfe.SIGNATURES)
+
+
+def query(p, m, n, fmt=0, ld=None, flags=1):
+    mat = gfe.GfeMatrix(p, m, n, fmt, 1, ld if ld is not None else n)
+    out = ctypes.c_size_t(0)
+    st = gfe.lib().gfe_query_workspace(ctypes.byref(mat), flags, ctypes.byref(out))
+    return st, out.value
+
+
+@pytest.mark.parametrize("p", [4, 1, 0, 253, 256, -3])
+def test_rejects_non_prime_or_large_p(p):
+    st, _ = query(p, 10, 10)
+    assert st == 1
+    assert b"prime" in gfe.lib().gfe_last_error()
+
+
+def test_rejects_bad_shapes_and_formats():
+    assert query(3, -1, 5)[0] == 1
+    assert query(3, 5, 10, ld=9)[0] == 1
+    assert query(3, 5, 10, fmt=1, ld=16)[0] == 1        # BITS64 needs p = 2
+    assert query(2, 5, 130, fmt=1, ld=16)[0] == 1       # 130 bits need 3 words
+    assert query(2, 5, 130, fmt=1, ld=20)[0] == 1       # not a multiple of 8
+    assert query(2, 5, 130, fmt=1, ld=24)[0] == 0
+    assert query(3, 5, 10, fmt=7)[0] == 1
+
+
+def test_workspace_monotone_and_empty():
+    assert query(3, 0, 0)[0] == 0
+    assert query(3, 0, 7)[0] == 0
+    prev = 0
+    for n in (10, 100, 1000, 5000, 9000, 20000):
+        st, ws = query(7, n, n)
+        assert st == 0 and ws >= prev
+        prev = ws
+    # bf16 storage (p > 31) needs about twice the bytes of e4m3 storage
+    assert query(251, 4000, 4000)[1] > 1.5 * query(7, 4000, 4000)[1]
+
+
+def test_null_result_rejected():
+    mat = gfe.GfeMatrix(3, 4, 4, 0, 1, 4)
+    st = gfe.lib().gfe_echelon(ctypes.byref(mat), None, 1, None, 0, None)
+    assert st == 1
+
+
+def test_status_strings():
+    L = gfe.lib()
+    assert L.gfe_status_str(0) == b"ok"
+    assert L.gfe_status_str(1) == b"invalid argument"

@@ -1,0 +1,149 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element, on seeded inputs (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1806_04211_gb300 import gfe, synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def compare_u8(A, p, got, ref):
+    assert got["rank"] == ref["rank"]
+    r = ref["rank"]
+    for k in ("rho", "ups"):
+        assert np.array_equal(got[k].cpu().numpy(), ref[k]), k
+    for k in ("R", "M", "K"):
+        if k not in got:
+            continue
+        g = got[k].cpu().numpy()
+        assert g.shape == ref[k].shape, (k, g.shape, ref[k].shape)
+        assert np.array_equal(g, ref[k]), (k, np.argwhere(g != ref[k])[:5])
+
+
+def compare_gf2(got, ref, m, n):
+    assert got["rank"] == ref["rank"]
+    r = ref["rank"]
+    for k in ("rho", "ups"):
+        assert np.array_equal(got[k].cpu().numpy(), ref[k]), k
+    for k, cols in (("R", n - r), ("M", r), ("K", r)):
+        if k not in got:
+            continue
+        g = O.unpack_bits(got[k].cpu().numpy(), cols) if got[k].numel() else np.zeros((0, cols), np.uint8)
+        e = O.unpack_bits(ref[k], cols) if ref[k].size else np.zeros((0, cols), np.uint8)
+        rows = e.shape[0]
+        assert np.array_equal(g[:rows], e), k
+
+
+@pytest.fixture(autouse=True)
+def _policy():
+    gfe.set_block_policy()
+    yield
+    gfe.set_block_policy()
+
+
+CASES = [
+    # p, m, n, rank (None = uniform)
+    (3, 1, 1, None), (3, 7, 5, None), (3, 64, 64, None), (3, 65, 63, None),
+    (3, 300, 200, None), (5, 257, 513, None), (7, 1500, 700, None), (7, 700, 1500, 300),
+    (3, 1000, 1000, None), (3, 1000, 1000, 700), (31, 333, 444, None),
+    (37, 200, 300, None), (251, 400, 400, None), (251, 600, 450, 270), (193, 129, 1100, None),
+]
+
+
+@pytest.mark.parametrize("impl", ["tensor", "plain"])
+@pytest.mark.parametrize("p,m,n,rank", CASES)
+def test_parity_u8(p, m, n, rank, impl):
+    A = synth.matrix(p, m, n, seed=3, rank=rank)
+    ref = O.echelon(A.numpy(), p)
+    got = gfe.echelon(A.to(DEV), p, impl=impl)
+    compare_u8(A, p, got, ref)
+
+
+@pytest.mark.parametrize("m,n,rank", [(1, 1, None), (64, 64, None), (100, 130, None), (1030, 500, None),
+                                      (700, 1200, 500), (2000, 2000, None)])
+def test_parity_gf2(m, n, rank):
+    A = synth.matrix(2, m, n, seed=5, rank=rank)
+    ref = O.echelon_gf2(A.numpy(), m, n)
+    got = gfe.echelon(A.to(DEV), 2, n=n)
+    compare_gf2(got, ref, m, n)
+
+
+@pytest.mark.parametrize("p,m,n,rank", [(3, 700, 500, None), (7, 600, 900, 400), (251, 300, 350, 200),
+                                        (2, 600, 700, None)])
+def test_parity_recursive_chief(p, m, n, rank):
+    """Small block policy: the top-level Chief uses 128-square blocks whose
+    ECH is itself a Chief over leaf blocks (the recursive scheme)."""
+    gfe.set_block_policy(200, 128)
+    A = synth.matrix(p, m, n, seed=9, rank=rank)
+    if p == 2:
+        ref = O.echelon_gf2(A.numpy(), m, n)
+        compare_gf2(gfe.echelon(A.to(DEV), 2, n=n), ref, m, n)
+    else:
+        ref = O.echelon(A.numpy(), p)
+        compare_u8(A, p, gfe.echelon(A.to(DEV), p), ref)
+
+
+@pytest.mark.parametrize("p", [3, 251])
+def test_dense_E_T(p):
+    A = synth.matrix(p, 150, 170, seed=2, rank=100)
+    ref = O.echelon(A.numpy(), p, want_E=True, want_T=True)
+    got = gfe.echelon(A.to(DEV), p, dense_E=True, dense_T=True)
+    assert np.array_equal(got["E"].cpu().numpy(), ref["E"])
+    assert np.array_equal(got["T"].cpu().numpy(), ref["T"])
+
+
+def test_dense_E_T_gf2():
+    m, n = 140, 200
+    A = synth.matrix(2, m, n, seed=2)
+    ref = O.echelon_gf2(A.numpy(), m, n, want_E=True, want_T=True)
+    got = gfe.echelon(A.to(DEV), 2, n=n, dense_E=True, dense_T=True)
+    assert np.array_equal(O.unpack_bits(got["E"].cpu().numpy(), n), O.unpack_bits(ref["E"], n))
+    assert np.array_equal(O.unpack_bits(got["T"].cpu().numpy(), m), O.unpack_bits(ref["T"], m))
+
+
+@pytest.mark.parametrize("p", [2, 3, 7, 251])
+def test_edge_cases(p):
+    for A in [np.zeros((5, 7), np.uint8), np.eye(9, dtype=np.uint8), np.zeros((0, 4), np.uint8),
+              np.zeros((4, 0), np.uint8), np.ones((6, 6), np.uint8),
+              np.tile(np.arange(5, dtype=np.uint8) % p, (4, 1))]:
+        ref = O.echelon(A, p)
+        got = gfe.echelon(torch.from_numpy(A).to(DEV), p)
+        compare_u8(A, p, got, ref)
+
+
+def test_duplicate_rows_and_zero_columns():
+    p = 5
+    A = synth.uniform_u8(300, 200, p, seed=4).numpy()
+    A[150] = A[3]
+    A[:, 40] = 0
+    A[:, 41] = A[:, 7]
+    ref = O.echelon(A, p)
+    compare_u8(A, p, gfe.echelon(torch.from_numpy(A).to(DEV), p), ref)
+
+
+@pytest.mark.parametrize("p", [3, 7, 251])
+def test_rank_only(p):
+    A = synth.matrix(p, 500, 400, seed=6, rank=250)
+    ref = O.echelon(A.numpy(), p)
+    got = gfe.rank(A.to(DEV), p)
+    assert got["rank"] == ref["rank"]
+    assert np.array_equal(got["rho"].cpu().numpy(), ref["rho"])
+    assert np.array_equal(got["ups"].cpu().numpy(), ref["ups"])
+
+
+@pytest.mark.parametrize("impl", ["tensor", "plain"])
+@pytest.mark.parametrize("p,m,n,k", [(2, 200, 300, 100), (3, 129, 257, 513), (7, 300, 300, 4096),
+                                     (31, 64, 64, 64), (251, 200, 190, 1500), (251, 1, 1, 1)])
+def test_mad(p, m, n, k, impl):
+    W = synth.uniform_u8(m, n, p, 1, 0)
+    A = synth.uniform_u8(m, k, p, 1, 1)
+    B = synth.uniform_u8(k, n, p, 1, 2)
+    ref = (W.numpy().astype(np.int64) + A.numpy().astype(np.int64) @ B.numpy().astype(np.int64)) % p
+    got = gfe.mad(W.to(DEV), A.to(DEV), B.to(DEV), p, impl=impl).cpu().numpy()
+    assert np.array_equal(got, ref)
+    got0 = gfe.mad(None, A.to(DEV), B.to(DEV), p, impl=impl).cpu().numpy()
+    assert np.array_equal(got0, (A.numpy().astype(np.int64) @ B.numpy().astype(np.int64)) % p)
