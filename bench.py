@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of exact echelon form + transformation over GF(p) (arXiv 1806.04211).
+
+One step = gfe_echelon (Steps 1-3 of the Chief, with transformation) of every
+matrix of the workload, inputs resident in HBM.  Metric: m*n*r / time in
+GF(p) multiply-adds per second (bit multiply-adds for GF(2)), the paper's
+cost model (Section 5: an alpha x beta block of rank r costs alpha*beta*r).
+
+Default workload: the bit-packed GF(2) configuration at n = 8192, i.e. one
+uniform Bernoulli(1/2) matrix and its rank-deficient twin (product of
+n x 0.75n and 0.75n x n factors), seeded (synth.py).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n N]
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank echelonises its own
+matrices (different seeds; no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GF(p) mul-adds/s for echelon+transform vs plain GPU path; serving p50/p99"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain CUDA-core comparator")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    return ap.parse_args()
+
+
+def workload(n):
+    # (p, m, n, rank-of-twin or None)
+    return [(2, n, n, None), (2, n, n, (3 * n) // 4)]
+
+
+def workload_name(n):
+    return "C2 GF(2) bit-packed n=%d: uniform + rank-%d twin" % (n, (3 * n) // 4)
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("GFE_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(ws, x, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def roofline(prof, codec_bytes):
+    """Roofline of the dominant kernel kind of the timed region."""
+    pk, src = peaks()
+    kinds = ["mad_tensor", "mad_plain"]
+    k = max(kinds, key=lambda x: prof["ms"][x])
+    ms, madds, launches = prof["ms"][k], prof["madds"][k], prof["timed"][k]
+    if ms <= 0 or launches == 0:
+        return None
+    if k == "mad_tensor":
+        # fp8 (e4m3) MMA: 2x the measured dense bf16 rate (nominal 4.5 / 2.25
+        # PFLOP/s); bf16 storage runs at the bf16 rate.  Sustained figure:
+        # the kernel is timed inside a long step.
+        ratio = 2.0 if codec_bytes == 1 else 1.0
+        peak = pk["bf16_tflops_sustained"] * ratio
+        achieved = 2.0 * madds / (ms * 1e-3) / 1e12
+        return {"kernel": "gfe_mma (tcgen05 %s)" % ("e4m3" if codec_bytes == 1 else "bf16"), "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "%s bf16 sustained x %.0f" % (src, ratio),
+                "launches": launches, "avg_launch_ms": ms / launches}
+    # CUDA-core multiply-add: 2 integer ops (IMAD) per multiply-add; peak =
+    # 152 SMs x 128 INT32 lanes x max SM clock
+    peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 * 2 / 1e12
+    achieved = 2.0 * madds / (ms * 1e-3) / 1e12
+    return {"kernel": "k_mad_plain (CUDA-core int32)", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "derived: 152 SM x 128 INT32 lanes x %s MHz x 2" % pk.get("sm_max_mhz", 2070.0),
+            "launches": launches, "avg_launch_ms": ms / launches}
+
+
+def cpu_baseline(n):
+    """The oracle, as it stands, on a bounded sample: the uniform GF(2) matrix
+    of the workload at n_s = min(n, 6144) (about 5-15 s on one core)."""
+    import numpy as np  # noqa: F401
+    from oracle import oracle as O
+    from paper_1806_04211_gb300 import synth
+    ns = min(n, 6144)
+    A = synth.matrix(2, ns, ns, seed=1).numpy()
+    t = time.perf_counter()
+    r = O.echelon_gf2(A, ns, ns, want_E=False, want_T=False)
+    dt = time.perf_counter() - t
+    return {"value": ns * ns * r["rank"] / dt, "unit": "mul-adds/s", "cores": 1, "kind": "oracle",
+            "sample": "one uniform GF(2) %dx%d matrix (bit-packed oracle, echelon + transformation), %.1f s"
+                      % (ns, ns, dt)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1806_04211_gb300 import synth
+    ns = min(args.n, 4096)
+    A = synth.matrix(2, ns, ns, seed=1).numpy()
+    for _ in range(args.warmup):
+        O.echelon_gf2(A, ns, ns)
+    times, units = [], 0.0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        r = O.echelon_gf2(A, ns, ns)
+        times.append(time.perf_counter() - t)
+        units += ns * ns * r["rank"]
+    tot = sum(times)
+    v = units / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "mul-adds/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (bit-packed GF(2))",
+            "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": workload_name(args.n), "sample": "uniform %dx%d per step" % (ns, ns)},
+            "cpu_baseline": {"value": v, "unit": "mul-adds/s", "cores": 1, "kind": "oracle",
+                             "sample": "uniform GF(2) %dx%d, bit-packed oracle, 1 thread" % (ns, ns)},
+            "e2e": {"value": v, "unit": "mul-adds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        barrier(ws)
+        return
+    import torch
+    from paper_1806_04211_gb300 import gfe, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    insts = []
+    for idx, (p, m, n, rk) in enumerate(workload(args.n)):
+        A = synth.matrix(p, m, n, seed=1 + 1000 * rank + idx, rank=rk, device=dev)
+        insts.append((p, m, n, A))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    codec_bytes = 1  # GF(2) is stored as e4m3 codes inside the library
+
+    def step(impl):
+        units = 0.0
+        for p, m, n, A in insts:
+            d = gfe.echelon(A, p, n=n, impl=impl)
+            units += m * n * d["rank"]
+        return units
+
+    def timed(impl, steps, prof_kinds=None):
+        per, units = [], 0.0
+        barrier(ws)
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            units += step(impl)
+            e1.record(stream)
+            e1.synchronize()
+            per.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        barrier(ws)
+        return per, units
+
+    for _ in range(args.warmup):
+        step("tensor")
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    gfe.profile_enable(True, kinds=["mad_tensor", "mad_plain"])
+    gfe.profile_read(True)
+    per, units = timed("tensor", args.steps)
+    prof = gfe.profile_read(True)
+    gfe.profile_enable(False)
+    clk = clocks.stop()
+    tot_ms = allmax(ws, sum(per), dev)
+    all_units = allsum(ws, units, dev)
+    value = all_units / (tot_ms * 1e-3)
+    launches = sum(prof["launches"].values())
+
+    # plain CUDA-core path on the same inputs (the comparator the metric names)
+    plain = None
+    if not args.no_plain:
+        for _ in range(1):
+            step("plain")
+        pper, punits = timed("plain", max(1, min(args.steps, 2)))
+        pt = allmax(ws, sum(pper), dev)
+        plain = {"value": allsum(ws, punits, dev) / (pt * 1e-3), "unit": "mul-adds/s",
+                 "ms_per_step": pt / len(pper)}
+
+    # end to end through the public API with host buffers: H2D of the inputs,
+    # echelonisation, D2H of every output (rank, pivots, R, M, K)
+    host_in = [(p, m, n, A.cpu().pin_memory()) for p, m, n, A in insts]
+    e2e_ms, e2e_units, h2d, d2h = 0.0, 0.0, 0, 0
+    barrier(ws)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p, m, n, Ah in host_in:
+            Ad = Ah.to(dev, non_blocking=True)
+            d = gfe.echelon(Ad, p, n=n)
+            outs = [d["ups"], d["rho"], d["R"], d["M"], d["K"]]
+            hs = [o.to("cpu") for o in outs]
+            e2e_units += m * n * d["rank"]
+            h2d += Ah.numel() * Ah.element_size()
+            d2h += 8 + sum(o.numel() * o.element_size() for o in hs)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_ms = allmax(ws, e2e_ms, dev)
+    e2e_units = allsum(ws, e2e_units, dev)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.n)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "mul-adds/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "e4m3 codes, exact integer accumulation",
+                "data": "synthetic (seeded SplitMix64; uniform + low-rank twin)",
+                "config": {"workload": workload_name(args.n), "p": 2, "n": args.n, "matrices_per_gpu": len(insts),
+                           "l2": "flushed between steps (256 MiB write)", "parallelism": "independent matrices per GPU"},
+                "roofline": roofline(prof, codec_bytes),
+                "plain_gpu_path": plain,
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_units / (e2e_ms * 1e-3), "unit": "mul-adds/s",
+                        "h2d_bytes_per_step": h2d // max(args.steps, 1), "d2h_bytes_per_step": d2h // max(args.steps, 1)},
+                "clocks": clk,
+                "gpu_launches": launches,
+                "profile": {"ms": prof["ms"], "launches": prof["launches"], "host_syncs": prof["host_syncs"]}}
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+
+
+if __name__ == "__main__":
+    main()

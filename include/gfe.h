@@ -149,15 +149,18 @@ gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k,
  */
 gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);
 
-/* Kernel-time profile of the calls made since the last reset (all streams).
- * Collected with CUDA events around every kernel launch while enabled. */
+/* Kernel profile of the calls made since the last reset (all streams).
+ * While enabled every launch is counted; launches of the kinds selected by
+ * the mask (bit k = kind k, -1 = all) are also timed with CUDA events
+ * recorded on the stream they are launched on.  mask 0 disables. */
 typedef struct {
     int64_t launches[8];     /* by kind: 0 MAD tensor, 1 MAD plain, 2 ECH leaf,   */
     double  ms[8];           /*   3 extract/riffle, 4 convert/assemble, 5 other   */
     double  madds[8];        /* algorithmic multiply-adds done by the MAD kinds  */
+    int64_t timed[8];        /* launches that were timed                         */
     int64_t host_syncs;      /* stream synchronisations made by the planner      */
 } gfe_profile;
-gfe_status gfe_profile_enable(int32_t on);
+gfe_status gfe_profile_enable(int32_t mask);
 gfe_status gfe_profile_read(gfe_profile *out, int32_t reset);
 
 const char *gfe_status_str(gfe_status s);

@@ -28,6 +28,7 @@ bool cuda_ok(cudaError_t e, const char *what) {
 // profiling: CUDA events around every launch while enabled
 // ---------------------------------------------------------------------------
 bool g_prof_on = false;
+static int32_t g_prof_mask = -1;  // kinds whose launches are timed with events
 static std::mutex g_prof_mu;
 static gfe_profile g_prof;
 struct Pending {
@@ -50,17 +51,20 @@ static cudaEvent_t ev_get() {
 }
 
 void prof_begin(const Launch &L, Kind k, cudaEvent_t *ev0) {
-    (void)k;
     *ev0 = nullptr;
     if (!g_prof_on) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.launches[k] += 1;
+    if (!(g_prof_mask & (1 << k))) return;
     *ev0 = ev_get();
     cudaEventRecord(*ev0, L.st);
 }
 
 void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds) {
-    if (!g_prof_on || !ev0) return;
+    if (!g_prof_on) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.madds[k] += madds;
+    if (!ev0) return;
     cudaEvent_t e1 = ev_get();
     cudaEventRecord(e1, L.st);
     g_pending.push_back({(int)k, ev0, e1, madds});
@@ -71,9 +75,8 @@ static void resolve_locked() {
         float ms = 0.f;
         cudaEventSynchronize(p.b);
         cudaEventElapsedTime(&ms, p.a, p.b);
-        g_prof.launches[p.kind] += 1;
         g_prof.ms[p.kind] += ms;
-        g_prof.madds[p.kind] += p.madds;
+        g_prof.timed[p.kind] += 1;
         g_evpool.push_back(p.a);
         g_evpool.push_back(p.b);
     }
@@ -370,9 +373,10 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block) {
     return GFE_OK;
 }
 
-gfe_status gfe_profile_enable(int32_t on) {
+gfe_status gfe_profile_enable(int32_t mask) {
     std::lock_guard<std::mutex> g(g_prof_mu);
-    g_prof_on = on != 0;
+    g_prof_on = mask != 0;
+    g_prof_mask = mask;
     return GFE_OK;
 }
 

@@ -37,7 +37,10 @@ class GfeResult(ctypes.Structure):
 
 class GfeProfile(ctypes.Structure):
     _fields_ = [("launches", _i64 * 8), ("ms", ctypes.c_double * 8), ("madds", ctypes.c_double * 8),
-                ("host_syncs", _i64)]
+                ("timed", _i64 * 8), ("host_syncs", _i64)]
+
+
+KINDS = ["mad_tensor", "mad_plain", "ech_leaf", "move", "convert", "other"]
 
 
 # every symbol declared in include/gfe.h, with its ctypes signature
@@ -106,10 +109,10 @@ def matrix_arg(A: torch.Tensor, p: int, n: int | None = None) -> GfeMatrix:
     """uint8 (m x n) residues, or for p = 2 int64 words (m x ldw) with n given."""
     if A.dtype == torch.uint8:
         m, nn = A.shape
-        assert A.stride(1) == 1
+        assert A.numel() == 0 or A.stride(1) == 1
         return GfeMatrix(p, m, nn, GFE_U8, A.data_ptr() if A.numel() else None, max(A.stride(0), nn, 1))
     if A.dtype in (torch.int64,):
-        assert p == 2 and n is not None and A.stride(1) == 1
+        assert p == 2 and n is not None and (A.numel() == 0 or A.stride(1) == 1)
         m = A.shape[0]
         return GfeMatrix(p, m, n, GFE_BITS64, A.data_ptr() if A.numel() else None, 8 * max(A.stride(0), 1))
     raise TypeError("A must be uint8 residues or int64 GF(2) words")
@@ -232,15 +235,19 @@ def set_block_policy(threshold: int = 0, block: int = 0):
     _check(lib().gfe_set_block_policy(threshold, block))
 
 
-def profile_enable(on: bool = True):
-    _check(lib().gfe_profile_enable(1 if on else 0))
+def profile_enable(on: bool = True, kinds=None):
+    """Count every launch; time (CUDA events) the given kinds (default all)."""
+    mask = 0
+    if on:
+        mask = -1 if kinds is None else sum(1 << KINDS.index(k) for k in kinds)
+    _check(lib().gfe_profile_enable(mask))
 
 
 def profile_read(reset: bool = True) -> dict:
     pr = GfeProfile()
     _check(lib().gfe_profile_read(ctypes.byref(pr), 1 if reset else 0))
-    kinds = ["mad_tensor", "mad_plain", "ech_leaf", "move", "convert", "other"]
-    return dict(launches={k: pr.launches[i] for i, k in enumerate(kinds)},
-                ms={k: pr.ms[i] for i, k in enumerate(kinds)},
-                madds={k: pr.madds[i] for i, k in enumerate(kinds)},
+    return dict(launches={k: pr.launches[i] for i, k in enumerate(KINDS)},
+                ms={k: pr.ms[i] for i, k in enumerate(KINDS)},
+                madds={k: pr.madds[i] for i, k in enumerate(KINDS)},
+                timed={k: pr.timed[i] for i, k in enumerate(KINDS)},
                 host_syncs=pr.host_syncs)
