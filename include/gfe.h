@@ -143,8 +143,9 @@ gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k,
  * Block partition policy of the planner (the "carefully chosen" block sizes
  * a_i, b_j of Section 3.1 and Section 5).  A block (or the whole input)
  * whose larger side exceeds `threshold` is split into square blocks of side
- * `block`; smaller ones into leaf blocks of at most 1024 rows x 64 columns,
- * which the one-CTA ECH kernel echelonises.  Defaults: 8192, 2048.  Process
+ * `block`; smaller ones into leaf blocks of at most 1024 rows x 64 columns
+ * (256 columns for GF(2)), which the one-CTA ECH kernel echelonises.
+ * Defaults: 2048, 2048.  Process
  * wide; values <= 0 restore the defaults.  Results never depend on it.
  */
 gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);

@@ -122,6 +122,7 @@ static gfe_status check_matrix(const gfe_matrix *A) {
 }
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+static int64_t ld64(int64_t x) { return x > 0 ? (x + 63) / 64 * 64 : 64; }
 
 struct Layout {
     size_t H, Mo, Ko, Ro, maps, arena, total;
@@ -133,13 +134,13 @@ static Layout layout(const gfe_matrix *A, bool trafo, bool wantR) {
     Layout Lo;
     size_t off = 0;
     Lo.H = off;
-    off += al256((size_t)std::max<int64_t>(m, 1) * std::max<int64_t>(n, 1) * es);
+    off += al256((size_t)std::max<int64_t>(m, 1) * ld64(n) * es);
     Lo.Mo = off;
-    off += trafo ? al256((size_t)std::max<int64_t>(mn, 1) * std::max<int64_t>(mn, 1) * es) : 256;
+    off += trafo ? al256((size_t)std::max<int64_t>(mn, 1) * ld64(mn) * es) : 256;
     Lo.Ko = off;
-    off += trafo ? al256((size_t)std::max<int64_t>(m, 1) * std::max<int64_t>(mn, 1) * es) : 256;
+    off += trafo ? al256((size_t)std::max<int64_t>(m, 1) * ld64(mn) * es) : 256;
     Lo.Ro = off;
-    off += wantR ? al256((size_t)std::max<int64_t>(mn, 1) * std::max<int64_t>(n, 1) * es) : 256;
+    off += wantR ? al256((size_t)std::max<int64_t>(mn, 1) * ld64(n) * es) : 256;
     Lo.maps = off;
     off += al256((size_t)(m + n + 2) * 4);
     Lo.arena = off;
@@ -161,7 +162,7 @@ static gfe_status query(const gfe_matrix *A, bool trafo, bool wantR, size_t *ws)
     DMat H;
     H.rows = A->m;
     H.cols = A->n;
-    H.ld = std::max<int64_t>(A->n, 1);
+    H.ld = ld64(A->n);
     DMat Mo, Ko, Ro;
     TopResult res;
     size_t peak = 0;
@@ -199,19 +200,19 @@ static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_
     H.ptr = base + Lo.H;
     H.rows = m;
     H.cols = n;
-    H.ld = std::max<int64_t>(n, 1);
+    H.ld = ld64(n);
     DMat Mo, Ko, Ro;
     Mo.ptr = base + Lo.Mo;
     Mo.rows = Mo.cols = mn;
-    Mo.ld = std::max<int64_t>(mn, 1);
+    Mo.ld = ld64(mn);
     Ko.ptr = base + Lo.Ko;
     Ko.rows = m;
     Ko.cols = mn;
-    Ko.ld = std::max<int64_t>(mn, 1);
+    Ko.ld = ld64(mn);
     Ro.ptr = base + Lo.Ro;
     Ro.rows = mn;
     Ro.cols = n;
-    Ro.ld = std::max<int64_t>(n, 1);
+    Ro.ld = ld64(n);
     const int es = codec_bytes(L.codec);
     TopResult res;
     try {
@@ -277,6 +278,10 @@ static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_
         (void)es;
         if (!cuda_ok(cudaStreamSynchronize(L.st), "final sync")) return GFE_ECUDA;
         if (!cuda_ok(cudaGetLastError(), "kernel launch")) return GFE_ECUDA;
+        if (tc_error_flag(true)) {
+            set_error("a tensor-core multiply-add timed out waiting on its pipeline");
+            return GFE_ETIMEOUT;
+        }
     } catch (const std::exception &e) {
         set_error(e.what());
         if (std::string(e.what()).find("workspace") != std::string::npos) return GFE_ENOMEM;
@@ -337,7 +342,7 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
 
 size_t gfe_mad_workspace(int32_t p, int64_t m, int64_t n, int64_t k) {
     int es = codec_bytes(codec_for(p < 2 ? 2 : p));
-    return al256((size_t)m * k * es) + al256((size_t)k * n * es) + al256((size_t)m * n * es) + 256;
+    return al256((size_t)m * ld64(k) * es) + al256((size_t)k * ld64(n) * es) + al256((size_t)m * ld64(n) * es) + 256;
 }
 
 gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k, const uint8_t *W, int64_t ldw, const uint8_t *A,
@@ -355,20 +360,22 @@ gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k, const uint8_t *W,
     L.codec = codec_for(p);
     L.impl = (flags & GFE_IMPL_PLAIN) ? 1 : 0;
     const int es = codec_bytes(L.codec);
-    char *a = (char *)ws, *b = a + al256((size_t)m * k * es), *c = b + al256((size_t)k * n * es);
+    const int64_t lk = ld64(k), ln = ld64(n);
+    char *a = (char *)ws, *b = a + al256((size_t)m * lk * es), *c = b + al256((size_t)k * ln * es);
     if (k > 0) {
-        import_u8(L, m, k, a, k, A, lda);
-        import_u8(L, k, n, b, n, B, ldb);
+        import_u8(L, m, k, a, lk, A, lda);
+        import_u8(L, k, n, b, ln, B, ldb);
     }
-    if (W) import_u8(L, m, n, c, n, W, ldw);
-    mad(L, m, n, k, W ? c : nullptr, n, a, k, b, n, c, n);
-    export_u8(L, m, n, C, ldc, c, n);
+    if (W) import_u8(L, m, n, c, ln, W, ldw);
+    mad(L, m, n, k, W ? c : nullptr, ln, a, lk, b, ln, c, ln);
+    export_u8(L, m, n, C, ldc, c, ln);
+    if (tc_error_flag(true)) return (set_error("tensor-core multiply-add timed out"), GFE_ETIMEOUT);
     if (!cuda_ok(cudaGetLastError(), "kernel launch")) return GFE_ECUDA;
     return GFE_OK;
 }
 
 gfe_status gfe_set_block_policy(int64_t threshold, int64_t block) {
-    g_block_threshold = threshold > 0 ? threshold : 8192;
+    g_block_threshold = threshold > 0 ? threshold : 2048;
     g_block_big = block > 0 ? block : 2048;
     return GFE_OK;
 }

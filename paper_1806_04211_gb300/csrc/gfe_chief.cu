@@ -104,11 +104,13 @@ struct Ctx {
         sg.top += bytes;
         return d;
     }
+    // leading dimensions are multiples of 64 elements (128 B): every view
+    // that starts at a block boundary is then a legal TMA operand
     DMat mat(int64_t rows, int64_t cols) {
         DMat d;
         d.rows = rows;
         d.cols = cols;
-        d.ld = cols > 0 ? cols : 1;
+        d.ld = cols > 0 ? (cols + 63) / 64 * 64 : 64;
         d.ptr = ar.alloc((size_t)(rows > 0 ? rows : 1) * (size_t)d.ld * es);
         return d;
     }
@@ -215,13 +217,13 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
 // to the one-CTA kernel; larger blocks are split by the Chief itself, which
 // is the paper's recursive scheme with a general rather than 2-way split.
 // ---------------------------------------------------------------------------
-int64_t g_block_threshold = 8192, g_block_big = 2048;
+int64_t g_block_threshold = 2048, g_block_big = 2048;
 
-static void block_policy(int64_t alpha, int64_t beta, std::vector<int64_t> &a, std::vector<int64_t> &b) {
+static void block_policy(int p, int64_t alpha, int64_t beta, std::vector<int64_t> &a, std::vector<int64_t> &b) {
     int64_t ra, cb;
     if (std::max(alpha, beta) <= g_block_threshold) {
         ra = ECH_LEAF_ROWS;
-        cb = ECH_LEAF_COLS;
+        cb = ech_leaf_cols(p);
     } else {
         ra = cb = g_block_big;
     }
@@ -237,24 +239,25 @@ void ech(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, const DMat &Ro, 
     out.rho.clear();
     out.gamma.clear();
     if (alpha == 0 || beta == 0) return;
-    if (alpha <= ECH_LEAF_ROWS && beta <= ECH_LEAF_COLS) {
+    const int lc = ech_leaf_cols(X.L.p);
+    if (alpha <= ECH_LEAF_ROWS && beta <= lc) {
         size_t mk = X.ar.mark();
-        int32_t *info = (int32_t *)X.ar.alloc(sizeof(int32_t) * (1 + 2 * ECH_LEAF_COLS));
+        int32_t *info = (int32_t *)X.ar.alloc(sizeof(int32_t) * (1 + 2 * lc));
         if (!X.dry) {
             ech_leaf(X.L, alpha, beta, H.ptr, H.ld, info, Mo.ptr, Mo.ld, Ko.ptr, Ko.ld, Ro.ptr, Ro.ld);
             int32_t *h = (int32_t *)t_pinned;
-            X.check(cudaMemcpyAsync(h, info, sizeof(int32_t) * (1 + 2 * ECH_LEAF_COLS), cudaMemcpyDeviceToHost,
-                                    X.L.st), "download");
+            X.check(cudaMemcpyAsync(h, info, sizeof(int32_t) * (1 + 2 * lc), cudaMemcpyDeviceToHost, X.L.st),
+                    "download");
             X.sync();
             out.r = h[0];
             out.rho.assign(h + 1, h + 1 + out.r);
-            out.gamma.assign(h + 1 + ECH_LEAF_COLS, h + 1 + ECH_LEAF_COLS + out.r);
+            out.gamma.assign(h + 1 + lc, h + 1 + lc + out.r);
         }
         X.ar.release(mk);
         return;
     }
     std::vector<int64_t> a, b;
-    block_policy(alpha, beta, a, b);
+    block_policy(X.L.p, alpha, beta, a, b);
     chief(X, H, a, b, true, true, Mo, Ko, Ro, out);
 }
 
@@ -335,7 +338,6 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                 // (CEX) A.A = C gamma^tr, A' = C gamma_bar^tr
                 j_cols(X, al, r, AA, Cij, g);
                 DMat Hh = sub(X, Hb, 0, 0, al, bj - r);
-                Hh.ld = Hb.ld;
                 j_cols(X, al, bj - r, Hh, Cij, ng);
                 // (MAD) H := A' + A.A x D.R
                 j_mad(X, al, bj - r, r, &Hh, AA, DR[j], Hh);
@@ -370,7 +372,6 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                 if (i > 0) j_mad(X, al, wc, r, &Z, AA, Bp[j], Z);           // (1) Z := C + A.A x B
                 if (rp > 0) {
                     DMat Vv = V, Ww = W, Xx = Xb;
-                    Vv.ld = Ww.ld = Xx.ld = wc;
                     j_rows(X, rp, wc, Vv, Z, nullptr, e.rho);               // (2) REX
                     j_rows(X, al - rp, wc, Ww, Z, nullptr, nrho);
                     if (i > 0) {
@@ -394,7 +395,6 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                     DMat Kih = sub(X, Kp[i], 0, ro[h], al, nc);
                     DMat Mjh = sub(X, Mp[j], 0, ro[h], r, nc);
                     DMat Zz = Zt;
-                    Zz.ld = nc > 0 ? nc : 1;
                     const bool first_j = (j == 0);
                     if (h != i && wM[j][h] != nc) {  // M_jh not stored yet: it is zero
                         j_zero(X, r, nc, Mjh);
@@ -416,13 +416,11 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                         continue;
                     }
                     DMat Xx = Xt;
-                    Xx.ld = nc > 0 ? nc : 1;
                     if (first_j && h == i) {
                         j_copy(X, rp, nc, Xx, AM);                        // (3) X := A.M   (V is 1)
                         j_copy(X, al - rp, nc, Kih, AK);                  // (6) K := A.K   (V is 1, W is 0)
                     } else {
                         DMat Vv = Vt, Ww = Wt;
-                        Vv.ld = Ww.ld = nc > 0 ? nc : 1;
                         j_rows(X, rp, nc, Vv, Zz, nullptr, e.rho);          // (2) REX
                         j_rows(X, al - rp, nc, Ww, Zz, nullptr, nrho);
                         if (h == i && !X.dry)                                // (+) ADI
@@ -438,7 +436,6 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                         j_rows(X, r + rp, nc, Mn, Mjh, &Xx, riffle_map(lam));
                     } else if (i != 0) {
                         DMat Ss = St;
-                        Ss.ld = nc > 0 ? nc : 1;
                         j_mad(X, r, nc, rp, nullptr, AE, Xx, Ss);
                         j_rows(X, r + rp, nc, Mn, Ss, &Xx, riffle_map(lam));
                     } else {
@@ -518,39 +515,46 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     }
 
     // ================= Step 3: Copy, PreClearUp, ClearUp =================
+    // R is assembled in a workspace whose block columns start at multiples
+    // of 64 (padding columns stay zero), so every ClearUp operand is a legal
+    // TMA tensor; the dense R is gathered from it at the end.
     if (wantR) {
         const int64_t nr = beta - rank;
+        std::vector<int64_t> pad(b + 1, 0);
+        for (int j = 0; j < b; ++j) pad[j + 1] = pad[j] + (bcols[j] - (int64_t)gam[j].size() + 63) / 64 * 64;
+        DMat Rw = X.mat(std::min(alpha, beta), std::max<int64_t>(pad[b], 1));
+        j_zero(X, rank, pad[b], Rw);
         for (int j = 0; j < b; ++j) {  // Copy: R_jj := D_j.R
             const int64_t rj = (int64_t)gam[j].size();
-            DMat dst = sub(X, Ro, rowoff[j], nonoff[j], rj, bcols[j] - rj);
-            j_copy(X, rj, bcols[j] - rj, dst, DR[j]);
-            // zeros left of the diagonal block (R is block upper triangular)
-            if (nonoff[j] > 0) j_zero(X, rj, nonoff[j], sub(X, Ro, rowoff[j], 0, rj, nonoff[j]));
+            j_copy(X, rj, bcols[j] - rj, sub(X, Rw, rowoff[j], pad[j], rj, bcols[j] - rj), DR[j]);
         }
         DMat Xcat = X.mat(std::min(alpha, beta), maxb);
         for (int k = b - 1; k >= 0; --k) {
             const int64_t rk = (int64_t)gam[k].size();
             std::vector<int32_t> ngk = complement(gam[k], bcols[k]);
-            DMat Xc = Xcat;
-            Xc.ld = rk > 0 ? rk : 1;
             for (int j = 0; j < k; ++j) {  // PreClearUp: (X_jk, R_jk) := CEX(B_jk, D_k.gamma)
                 const int64_t rj = (int64_t)gam[j].size();
                 if (rj == 0) continue;
                 DMat Bjk = sub(X, Bp[j], 0, co[k] - co[j + 1], rj, bcols[k]);
-                j_cols(X, rj, rk, sub(X, Xc, rowoff[j], 0, rj, rk), Bjk, gam[k]);
-                j_cols(X, rj, bcols[k] - rk, sub(X, Ro, rowoff[j], nonoff[k], rj, bcols[k] - rk), Bjk, ngk);
+                j_cols(X, rj, rk, sub(X, Xcat, rowoff[j], 0, rj, rk), Bjk, gam[k]);
+                j_cols(X, rj, bcols[k] - rk, sub(X, Rw, rowoff[j], pad[k], rj, bcols[k] - rk), Bjk, ngk);
             }
             if (rk == 0 || rowoff[k] == 0) continue;
             // ClearUp for every j < k at once: R_jl += X_jk R_kl (l >= k), M_j += X_jk M_k
-            DMat Rtop = sub(X, Ro, 0, nonoff[k], rowoff[k], nr - nonoff[k]);
-            DMat Rk = sub(X, Ro, rowoff[k], nonoff[k], rk, nr - nonoff[k]);
-            j_mad(X, rowoff[k], nr - nonoff[k], rk, &Rtop, Xc, Rk, Rtop);
+            DMat Rtop = sub(X, Rw, 0, pad[k], rowoff[k], pad[b] - pad[k]);
+            DMat Rk = sub(X, Rw, rowoff[k], pad[k], rk, pad[b] - pad[k]);
+            j_mad(X, rowoff[k], pad[b] - pad[k], rk, &Rtop, Xcat, Rk, Rtop);
             if (trafo) {
                 DMat Mtop = sub(X, Mo, 0, 0, rowoff[k], rank);
                 DMat Mk = sub(X, Mo, rowoff[k], 0, rk, rank);
-                j_mad(X, rowoff[k], rank, rk, &Mtop, Xc, Mk, Mtop);
+                j_mad(X, rowoff[k], rank, rk, &Mtop, Xcat, Mk, Mtop);
             }
         }
+        // dense R: non-pivot column t of block k sits at pad[k] + (t - nonoff[k])
+        std::vector<int32_t> gmap(nr);
+        for (int k = 0; k < b; ++k)
+            for (int64_t t = nonoff[k]; t < nonoff[k + 1]; ++t) gmap[t] = (int32_t)(pad[k] + t - nonoff[k]);
+        j_cols(X, rank, nr, Ro, Rw, gmap);
     }
     X.ar.release(mark0);
 }
@@ -558,8 +562,8 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
 // ---------------------------------------------------------------------------
 // entry used by the C ABI
 // ---------------------------------------------------------------------------
-static void top_blocks(int64_t m, int64_t n, std::vector<int64_t> &a, std::vector<int64_t> &b) {
-    block_policy(m, n, a, b);
+static void top_blocks(int p, int64_t m, int64_t n, std::vector<int64_t> &a, std::vector<int64_t> &b) {
+    block_policy(p, m, n, a, b);
 }
 
 // Runs the method on the (already imported) internal matrix H.
@@ -588,7 +592,7 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
     }
     X.sg.dev = (char *)X.ar.alloc(STAGE_BYTES);
     std::vector<int64_t> a, b;
-    top_blocks(H.rows, H.cols, a, b);
+    top_blocks(L.p, H.rows, H.cols, a, b);
     EchRes e;
     if (H.rows > 0 && H.cols > 0) chief(X, H, a, b, trafo, wantR, Mo, Ko, Ro, e);
     if (!dry) X.sync();

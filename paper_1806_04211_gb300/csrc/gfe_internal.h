@@ -2,8 +2,8 @@
 //
 // Element storage inside the library ("codec"): the tensor-core operand
 // encoding of the centred residue c in [-(p-1)/2, (p-1)/2]:
+//   CODEC_BF16 p <= 251: one bf16 (|c| <= 125 is exact in bf16)  [in use]
 //   CODEC_F8   p <= 31 : one e4m3 byte (|c| <= 15 is exact in e4m3)
-//   CODEC_BF16 p <= 251: one bf16 (|c| <= 125 is exact in bf16)
 // so the tcgen05 multiply-add reads operands straight from HBM.  Zero is the
 // all-zero bit pattern in both.  This is the floating-point representation
 // of field elements the paper mentions as prior art (Section 1), with the
@@ -18,7 +18,9 @@
 namespace gfe {
 
 enum Codec { CODEC_F8 = 0, CODEC_BF16 = 1 };
-inline Codec codec_for(int p) { return p <= 31 ? CODEC_F8 : CODEC_BF16; }
+// bf16 for every p: the tensor-core multiply-add (kind::f16) takes bf16
+// operands in both K-major and MN-major layout.
+inline Codec codec_for(int) { return CODEC_BF16; }
 inline int codec_bytes(Codec c) { return c == CODEC_F8 ? 1 : 2; }
 
 // A device matrix in the internal codec: rows x cols, row-major, ld elements.
@@ -54,10 +56,16 @@ void mad_plain(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, 
 bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_t ldw,
             const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc);
 
-// Leaf echelonisation of H (alpha <= ECH_LEAF_ROWS, beta <= ECH_LEAF_COLS).
-// info[0] = r, info[1..] = rho (r), info[1+cap..] = gamma (r), cap = ECH_LEAF_COLS.
+// error word of the tensor-core kernel (a bounded wait ran out); read + reset
+int tc_error_flag(bool reset);
+int64_t tc_k_chunk(int p);
+
+// Leaf echelonisation of H (alpha <= ECH_LEAF_ROWS, beta <= ech_leaf_cols(p)).
+// info[0] = r, info[1..] = rho (r), info[1+cap..] = gamma (r), cap = ech_leaf_cols(p).
 constexpr int ECH_LEAF_ROWS = 1024;
-constexpr int ECH_LEAF_COLS = 64;
+constexpr int ECH_LEAF_COLS = 64;       // p > 2: byte rows in shared memory
+constexpr int ECH_LEAF_COLS_GF2 = 256;  // p = 2: 64-bit words in registers
+int ech_leaf_cols(int p);
 void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64_t ldh,
               int32_t *info, void *M, int64_t ldm, void *K, int64_t ldk, void *R, int64_t ldr);
 

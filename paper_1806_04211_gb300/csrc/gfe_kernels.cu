@@ -288,8 +288,173 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(int p, int alpha, int beta
     }
 }
 
+// ---------------------------------------------------------------------------
+// leaf echelonisation over GF(2): the same column-by-column Gauss-Jordan with
+// the topmost-row rule, but each thread holds its row (<= 256 columns) and
+// its <= 256 slot coefficients as 64-bit words in registers, so eliminating
+// a row is one XOR per word.  The candidate rows of every warp publish their
+// words before the barrier; after it the pivot (the smallest candidate row)
+// is read from its warp's buffer, so each column costs one barrier.
+// ---------------------------------------------------------------------------
+// register-resident word arrays: select / update word i without local memory
+template <int W> __device__ __forceinline__ uint64_t wpick(const uint64_t (&a)[W], int i) {
+    uint64_t v = a[0];
+#pragma unroll
+    for (int w = 1; w < W; ++w)
+        if (i == w) v = a[w];
+    return v;
+}
+template <int W> __device__ __forceinline__ void wxor(uint64_t (&a)[W], int i, uint64_t m) {
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        if (i == w) a[w] ^= m;
+}
+
+template <int W, typename T>
+__global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, const T *H, int64_t ldh,
+                                                          int32_t *info, T *Mo, int64_t ldm, T *Ko,
+                                                          int64_t ldk, T *Ro, int64_t ldr, T one) {
+    extern __shared__ uint64_t smw[];
+    uint64_t *hw = smw;                 // [1024][W] rows after elimination
+    uint64_t *tw = smw + 1024 * W;      // [1024][W] slot coefficients
+    __shared__ uint64_t wbuf[3][32][2 * W];
+    __shared__ int best[3];
+    __shared__ uint8_t piv[1024];
+    __shared__ int16_t slotOf[1024], pivpos[1024];
+    __shared__ int16_t slotRow[64 * W], slotCol[64 * W], sortedSlot[64 * W], nonCol[64 * W];
+    __shared__ int wsum[32];
+    const int y = threadIdx.x, lane = y & 31, warp = y >> 5;
+    uint64_t h[W], t[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        h[w] = 0;
+        t[w] = 0;
+    }
+    if (y < alpha) {
+        const T *row = H + (int64_t)y * ldh;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            for (int c = 64 * w; c < beta && c < 64 * (w + 1); ++c)
+                if (row[c]) h[w] |= (uint64_t)1 << (c & 63);
+    }
+    if (y < 3) best[y] = INT_MAX;
+    piv[y] = 0;
+    slotOf[y] = -1;
+    bool isp = false;
+    __syncthreads();
+    int ns = 0;
+    for (int c = 0; c < beta; ++c) {
+        const int b = c % 3;
+        if (y == 0) best[(c + 1) % 3] = INT_MAX;
+        const int cw = c >> 6;
+        const bool hit = (wpick<W>(h, cw) >> (c & 63)) & 1;
+        const bool cand = (y < alpha) && !isp && hit;
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (bal && lane == __ffs(bal) - 1) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                wbuf[b][warp][w] = h[w];
+                wbuf[b][warp][W + w] = t[w];
+            }
+            atomicMin(&best[b], y);
+        }
+        __syncthreads();
+        const int x = best[b];
+        if (x == INT_MAX) continue;  // uniform: column c has no pivot
+        const uint64_t *px = wbuf[b][x >> 5];
+        if (y == x) {
+            wxor<W>(t, ns >> 6, (uint64_t)1 << (ns & 63));  // own identity in slot ns
+            isp = true;
+            piv[y] = 1;
+            slotOf[y] = (int16_t)ns;
+            slotRow[ns] = (int16_t)y;
+            slotCol[ns] = (int16_t)c;
+        } else if (hit) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                h[w] ^= px[w];
+                t[w] ^= px[W + w];
+            }
+            wxor<W>(t, ns >> 6, (uint64_t)1 << (ns & 63));  // the pivot's own identity
+        }
+        ++ns;
+    }
+    const int r = ns;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        hw[y * W + w] = h[w];
+        tw[y * W + w] = t[w];
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, isp);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    before += __popc(bal & ((1u << lane) - 1));
+    if (y < alpha) {
+        if (isp) {
+            pivpos[y] = (int16_t)before;
+            sortedSlot[before] = slotOf[y];
+            info[1 + before] = y;
+        } else {
+            pivpos[y] = (int16_t)(y - before);
+        }
+    }
+    if (y == 0) {
+        info[0] = r;
+        int j = 0, l = 0;
+        for (int c = 0; c < beta; ++c) {
+            if (l < r && slotCol[l] == c) ++l;
+            else nonCol[j++] = (int16_t)c;
+        }
+    }
+    if (y < r) info[1 + 64 * W + y] = slotCol[y];
+    __syncthreads();
+    for (int idx = y; idx < r * r; idx += 1024) {
+        int l = idx / r, s = idx % r, q = sortedSlot[s];
+        Mo[(int64_t)l * ldm + s] = ((tw[slotRow[l] * W + (q >> 6)] >> (q & 63)) & 1) ? one : (T)0;
+    }
+    if (r > 0) {
+        for (int64_t idx = y; idx < (int64_t)alpha * r; idx += 1024) {
+            int row = (int)(idx / r), s = (int)(idx % r), q = sortedSlot[s];
+            if (piv[row]) continue;
+            Ko[(int64_t)pivpos[row] * ldk + s] = ((tw[row * W + (q >> 6)] >> (q & 63)) & 1) ? one : (T)0;
+        }
+    }
+    const int nr = beta - r;
+    for (int idx = y; idx < r * nr; idx += 1024) {
+        int l = idx / nr, j = idx % nr, c = nonCol[j];
+        Ro[(int64_t)l * ldr + j] = ((hw[slotRow[l] * W + (c >> 6)] >> (c & 63)) & 1) ? one : (T)0;
+    }
+}
+
+int ech_leaf_cols(int p) { return p == 2 ? ECH_LEAF_COLS_GF2 : ECH_LEAF_COLS; }
+
 void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64_t ldh,
               int32_t *info, void *M, int64_t ldm, void *K, int64_t ldk, void *R, int64_t ldr) {
+    if (L.p == 2) {
+        const int smem = 2 * 1024 * 4 * 8;
+        static bool attr[2] = {false, false};
+        cudaEvent_t ev;
+        prof_begin(L, K_ECH, &ev);
+        if (L.codec == CODEC_F8) {
+            if (!attr[0]) {
+                cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                attr[0] = true;
+            }
+            k_ech_leaf_gf2<4, uint8_t><<<1, 1024, smem, L.st>>>((int)alpha, (int)beta, (const uint8_t *)H, ldh, info,
+                (uint8_t *)M, ldm, (uint8_t *)K, ldk, (uint8_t *)R, ldr, (uint8_t)0x38);
+        } else {
+            if (!attr[1]) {
+                cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                attr[1] = true;
+            }
+            k_ech_leaf_gf2<4, uint16_t><<<1, 1024, smem, L.st>>>((int)alpha, (int)beta, (const uint16_t *)H, ldh,
+                info, (uint16_t *)M, ldm, (uint16_t *)K, ldk, (uint16_t *)R, ldr, (uint16_t)0x3F80);
+        }
+        prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta));
+        return;
+    }
     const int smem = 2 * 1024 * LS;
     static bool attr_set[2] = {false, false};
     cudaEvent_t ev;
@@ -477,7 +642,10 @@ void import_bits(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t
     dim3 grid = grid_rc(rows, cols, 256);
     cudaEvent_t ev;
     prof_begin(L, K_CONV, &ev);
-    k_import_bits<CODEC_F8><<<grid, 256, 0, L.st>>>(rows, cols, (uint8_t *)dst, ldd, src, ldw);
+    if (L.codec == CODEC_F8)
+        k_import_bits<CODEC_F8><<<grid, 256, 0, L.st>>>(rows, cols, (uint8_t *)dst, ldd, src, ldw);
+    else
+        k_import_bits<CODEC_BF16><<<grid, 256, 0, L.st>>>(rows, cols, (uint16_t *)dst, ldd, src, ldw);
     prof_end(L, K_CONV, ev, 0);
 }
 
@@ -502,7 +670,10 @@ void export_bits(const Launch &L, int64_t rows, int64_t cols, uint64_t *dst, int
     dim3 grid = grid_rc(rows, nw, 128);
     cudaEvent_t ev;
     prof_begin(L, K_CONV, &ev);
-    k_export_bits<CODEC_F8><<<grid, 128, 0, L.st>>>(rows, cols, dst, ldw, (const uint8_t *)src, lds);
+    if (L.codec == CODEC_F8)
+        k_export_bits<CODEC_F8><<<grid, 128, 0, L.st>>>(rows, cols, dst, ldw, (const uint8_t *)src, lds);
+    else
+        k_export_bits<CODEC_BF16><<<grid, 128, 0, L.st>>>(rows, cols, dst, ldw, (const uint16_t *)src, lds);
     prof_end(L, K_CONV, ev, 0);
 }
 
@@ -584,8 +755,12 @@ void build_E(const Launch &L, int fmt, int64_t m, int64_t n, int64_t r, void *ds
     prof_begin(L, K_CONV, &ev);
     if (fmt == 1) {
         int64_t nw = (n + 63) >> 6;
-        k_build_E_bits<CODEC_F8><<<grid_rc(m, nw, 128), 128, 0, L.st>>>(m, n, r, (uint64_t *)dst, ldd / 8,
-                                                                         (const uint8_t *)R, ldr, colmap);
+        if (L.codec == CODEC_F8)
+            k_build_E_bits<CODEC_F8><<<grid_rc(m, nw, 128), 128, 0, L.st>>>(m, n, r, (uint64_t *)dst, ldd / 8,
+                                                                             (const uint8_t *)R, ldr, colmap);
+        else
+            k_build_E_bits<CODEC_BF16><<<grid_rc(m, nw, 128), 128, 0, L.st>>>(m, n, r, (uint64_t *)dst, ldd / 8,
+                                                                               (const uint16_t *)R, ldr, colmap);
     } else if (L.codec == CODEC_F8) {
         k_build_E_u8<CODEC_F8><<<grid_rc(m, n, 256), 256, 0, L.st>>>(L.p, m, n, r, (uint8_t *)dst, ldd,
                                                                       (const uint8_t *)R, ldr, colmap);
@@ -603,8 +778,12 @@ void build_T(const Launch &L, int fmt, int64_t m, int64_t r, void *dst, int64_t 
     prof_begin(L, K_CONV, &ev);
     if (fmt == 1) {
         int64_t nw = (m + 63) >> 6;
-        k_build_T_bits<CODEC_F8><<<grid_rc(m, nw, 128), 128, 0, L.st>>>(m, r, (uint64_t *)dst, ldd / 8,
-            (const uint8_t *)M, ldm, (const uint8_t *)K, ldk, rowmap);
+        if (L.codec == CODEC_F8)
+            k_build_T_bits<CODEC_F8><<<grid_rc(m, nw, 128), 128, 0, L.st>>>(m, r, (uint64_t *)dst, ldd / 8,
+                (const uint8_t *)M, ldm, (const uint8_t *)K, ldk, rowmap);
+        else
+            k_build_T_bits<CODEC_BF16><<<grid_rc(m, nw, 128), 128, 0, L.st>>>(m, r, (uint64_t *)dst, ldd / 8,
+                (const uint16_t *)M, ldm, (const uint16_t *)K, ldk, rowmap);
     } else if (L.codec == CODEC_F8) {
         k_build_T_u8<CODEC_F8><<<grid_rc(m, m, 256), 256, 0, L.st>>>(L.p, m, r, (uint8_t *)dst, ldd,
             (const uint8_t *)M, ldm, (const uint8_t *)K, ldk, rowmap);

@@ -147,3 +147,42 @@ def test_mad(p, m, n, k, impl):
     assert np.array_equal(got, ref)
     got0 = gfe.mad(None, A.to(DEV), B.to(DEV), p, impl=impl).cpu().numpy()
     assert np.array_equal(got0, (A.numpy().astype(np.int64) @ B.numpy().astype(np.int64)) % p)
+
+
+def _kchunk(p):
+    cmax = 1 if p == 2 else (p - 1) // 2
+    return ((1 << 24) - 1) // (cmax * cmax) // 64 * 64
+
+
+@pytest.mark.parametrize("p", [2, 3, 7, 31, 251])
+def test_mad_tensor_exact_at_the_accumulation_bound(p):
+    """Every product at the largest centred magnitude, same sign, with K past
+    the exact-accumulation chunk: the fp32 partial sums reach just below 2^24."""
+    cmax_res = 1 if p == 2 else (p - 1) // 2          # centred +cmax
+    k = _kchunk(p) + 200 if p > 7 else 4096
+    m, n = 130, 300
+    A = torch.full((m, k), cmax_res, dtype=torch.uint8)
+    B = torch.full((k, n), cmax_res, dtype=torch.uint8)
+    B[:, 1::2] = (p - cmax_res) % p                    # -cmax in odd columns
+    W = synth.uniform_u8(m, n, p, 2, 0)
+    ref = (W.numpy().astype(np.int64) + A.numpy().astype(np.int64) @ B.numpy().astype(np.int64)) % p
+    gfe.profile_enable(True)
+    gfe.profile_read(True)
+    got = gfe.mad(W.to(DEV), A.to(DEV), B.to(DEV), p, impl="tensor").cpu().numpy()
+    prof = gfe.profile_read(True)
+    gfe.profile_enable(False)
+    assert prof["launches"]["mad_tensor"] >= 1 and prof["launches"]["mad_plain"] == 0
+    assert np.array_equal(got, ref)
+
+
+def test_tensor_path_is_taken_in_echelon():
+    p, n = 7, 3000
+    A = synth.matrix(p, n, n, seed=8, rank=2000)
+    gfe.profile_enable(True)
+    gfe.profile_read(True)
+    got = gfe.echelon(A.to(DEV), p)
+    prof = gfe.profile_read(True)
+    gfe.profile_enable(False)
+    assert got["rank"] == 2000
+    assert prof["launches"]["mad_tensor"] > 0
+    assert prof["madds"]["mad_tensor"] > 10 * prof["madds"]["mad_plain"]
