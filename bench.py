@@ -6,7 +6,7 @@ matrix of the workload, inputs resident in HBM.  Metric: m*n*r / time in
 GF(p) multiply-adds per second (bit multiply-adds for GF(2)), the paper's
 cost model (Section 5: an alpha x beta block of rank r costs alpha*beta*r).
 
-Default workload: the bit-packed GF(2) configuration at n = 8192, i.e. one
+Default workload: the bit-packed GF(2) configuration at n = 32768, i.e. one
 uniform Bernoulli(1/2) matrix and its rank-deficient twin (product of
 n x 0.75n and 0.75n x n factors), seeded (synth.py).
 
@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain CUDA-core comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     return ap.parse_args()
@@ -182,12 +182,11 @@ def roofline(prof, codec_bytes):
 
 
 def cpu_baseline(n):
-    """The oracle, as it stands, on a bounded sample: the uniform GF(2) matrix
-    of the workload at n_s = min(n, 6144) (about 5-15 s on one core)."""
-    import numpy as np  # noqa: F401
+    """The oracle, as it stands, on a bounded sample: a uniform GF(2) matrix
+    of side n_s = min(n, 8192) drawn like the workload's (about 5-15 s on one core)."""
     from oracle import oracle as O
     from paper_1806_04211_gb300 import synth
-    ns = min(n, 6144)
+    ns = min(n, 8192)
     A = synth.matrix(2, ns, ns, seed=1).numpy()
     t = time.perf_counter()
     r = O.echelon_gf2(A, ns, ns, want_E=False, want_T=False)
@@ -243,7 +242,7 @@ def main():
         A = synth.matrix(p, m, n, seed=1 + 1000 * rank + idx, rank=rk, device=dev)
         insts.append((p, m, n, A))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    codec_bytes = 1  # GF(2) is stored as e4m3 codes inside the library
+    codec_bytes = 2  # entries are stored as bf16 centred residues inside the library
 
     def step(impl):
         units = 0.0
@@ -325,7 +324,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "mul-adds/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "e4m3 codes, exact integer accumulation",
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands, fp32 exact-integer accumulation",
                 "data": "synthetic (seeded SplitMix64; uniform + low-rank twin)",
                 "config": {"workload": workload_name(args.n), "p": 2, "n": args.n, "matrices_per_gpu": len(insts),
                            "l2": "flushed between steps (256 MiB write)", "parallelism": "independent matrices per GPU"},

@@ -286,9 +286,32 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ---- host side ----
+// error word of the kernel: one per device (a module-scope device variable,
+// zero at load); its device address is looked up once per device
+__device__ int g_tc_err;
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_once;
-int *g_err = nullptr;  // device error word of the tensor-core kernel
+std::mutex g_dev_mu;
+constexpr int MAX_DEV = 64;
+int *g_err_dev[MAX_DEV] = {};
+bool g_attr_dev[MAX_DEV] = {};
+
+// per-device set-up with the device current; returns the error word
+int *dev_setup() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return nullptr;
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    if (!g_attr_dev[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_tc_err) != cudaSuccess) return nullptr;
+        if (cudaFuncSetAttribute(k_mad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess)
+            return nullptr;
+        g_err_dev[dev] = (int *)p;
+        g_attr_dev[dev] = true;
+    }
+    return g_err_dev[dev];
+}
 
 bool init_tc() {
     std::call_once(g_once, [] {
@@ -298,14 +321,6 @@ bool init_tc() {
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-        if (cudaFuncSetAttribute(k_mad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess)
-            g_encode = nullptr;
-        if (cudaMalloc(&g_err, sizeof(int)) != cudaSuccess) {
-            g_err = nullptr;
-            g_encode = nullptr;
-        } else {
-            cudaMemset(g_err, 0, sizeof(int));
-        }
     });
     return g_encode != nullptr;
 }
@@ -340,6 +355,8 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
     if (!al16(A) || !al16(B) || (lda * 2) % 16 || (ldb * 2) % 16) return false;
     if (m > (1 << 30) || n > (1 << 30)) return false;
     if (!init_tc()) return false;
+    int *err = dev_setup();
+    if (!err) return false;
     const int64_t kc = tc_k_chunk(L.p);
     for (int64_t k0 = 0; k0 < k; k0 += kc) {
         const int64_t kk = k - k0 < kc ? k - k0 : kc;
@@ -357,17 +374,24 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
         cudaEvent_t ev;
         prof_begin(L, K_MAD_TC, &ev);
         k_mad_tc<<<grid, 128, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, (const uint16_t *)Wk, ldwk,
-                                               (uint16_t *)C, ldc, g_err);
+                                               (uint16_t *)C, ldc, err);
         prof_end(L, K_MAD_TC, ev, (double)m * (double)n * (double)kk);
     }
     return true;
 }
 
 int tc_error_flag(bool reset) {
-    if (!g_err) return 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return 0;
+    int *e = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_dev_mu);
+        e = g_err_dev[dev];
+    }
+    if (!e) return 0;
     int h = 0;
-    cudaMemcpy(&h, g_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (reset && h) cudaMemset(g_err, 0, sizeof(int));
+    cudaMemcpy(&h, e, sizeof(int), cudaMemcpyDeviceToHost);
+    if (reset && h) cudaMemset(e, 0, sizeof(int));
     return h;
 }
 
