@@ -140,6 +140,26 @@ gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k,
                    uint32_t flags, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * gfe_mad_noalloc -- the same multiply-add as gfe_mad, C := W + A B over
+ * GF(p) on GFE_U8 residues, for callers that must not allocate device memory
+ * (a fixed device-memory budget owned by the caller, or a path where
+ * cudaMalloc / cudaFree could block or synchronise the device).  The paper
+ * has no counterpart; this is an interface convenience of this library.
+ * Needs no workspace: its scratch is a library-owned device array of
+ * gfe_mad_noalloc_max_bytes() bytes (32 MiB) that every GPU loading the
+ * library holds until exit.  A product whose scratch (gfe_mad_workspace())
+ * would exceed it is rejected with GFE_EINVAL.  The first call on each device
+ * (with that device current) looks up the array's device address -- make it
+ * before any stream capture.  All calls on a device share the array: calls
+ * whose work overlaps on the GPU race and must be ordered by the caller.
+ */
+size_t gfe_mad_noalloc_max_bytes(void);
+gfe_status gfe_mad_noalloc(int32_t p, int64_t m, int64_t n, int64_t k,
+                           const uint8_t *W, int64_t ldw, const uint8_t *A, int64_t lda,
+                           const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                           uint32_t flags, void *stream);
+
+/*
  * Block partition policy of the planner (the "carefully chosen" block sizes
  * a_i, b_j of Section 3.1 and Section 5).  A block (or the whole input)
  * whose larger side exceeds `threshold` is split into square blocks of side

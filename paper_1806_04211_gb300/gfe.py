@@ -56,6 +56,9 @@ SIGNATURES = {
     "gfe_mad_workspace": (ctypes.c_size_t, [_i32, _i64, _i64, _i64]),
     "gfe_mad": (_i32, [_i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_uint32,
                        _vp, ctypes.c_size_t, _vp]),
+    "gfe_mad_noalloc_max_bytes": (ctypes.c_size_t, []),
+    "gfe_mad_noalloc": (_i32, [_i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_uint32,
+                               _vp]),
     "gfe_set_block_policy": (_i32, [_i64, _i64]),
     "gfe_profile_enable": (_i32, [_i32]),
     "gfe_profile_read": (_i32, [ctypes.POINTER(GfeProfile), _i32]),
@@ -228,6 +231,17 @@ def mad(W, A: torch.Tensor, B: torch.Tensor, p: int, impl: str = "tensor", out=N
                          B.stride(0), C.data_ptr(), C.stride(0), _impl_flag(impl), ws.data_ptr(), ws.numel(),
                          _stream(stream)))
     return C
+
+
+def mad_noalloc(W, A: torch.Tensor, B: torch.Tensor, p: int, out: torch.Tensor, impl: str = "tensor", stream=None):
+    """gfe_mad_noalloc: C := W + A B over GF(p) into `out` without any device
+    allocation by the library (its scratch is a fixed library-owned array)."""
+    m, k = A.shape
+    n = B.shape[1]
+    _check(lib().gfe_mad_noalloc(p, m, n, k, _ptr(W), W.stride(0) if W is not None else 0, _ptr(A), A.stride(0),
+                                 _ptr(B), B.stride(0), out.data_ptr(), out.stride(0), _impl_flag(impl),
+                                 _stream(stream)))
+    return out
 
 
 def set_block_policy(threshold: int = 0, block: int = 0):
