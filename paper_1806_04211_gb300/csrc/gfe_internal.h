@@ -2,8 +2,8 @@
 //
 // Element storage inside the library ("codec"): the tensor-core operand
 // encoding of the centred residue c in [-(p-1)/2, (p-1)/2]:
-//   CODEC_BF16 p <= 251: one bf16 (|c| <= 125 is exact in bf16)  [in use]
 //   CODEC_F8   p <= 31 : one e4m3 byte (|c| <= 15 is exact in e4m3)
+//   CODEC_BF16 p <= 251: one bf16 (|c| <= 125 is exact in bf16)
 // so the tcgen05 multiply-add reads operands straight from HBM.  Zero is the
 // all-zero bit pattern in both.  This is the floating-point representation
 // of field elements the paper mentions as prior art (Section 1), with the
@@ -18,9 +18,9 @@
 namespace gfe {
 
 enum Codec { CODEC_F8 = 0, CODEC_BF16 = 1 };
-// bf16 for every p: the tensor-core multiply-add (kind::f16) takes bf16
-// operands in both K-major and MN-major layout.
-inline Codec codec_for(int) { return CODEC_BF16; }
+// e4m3 for p <= 31 (tcgen05 kind::f8f6f4), bf16 above (kind::f16); both
+// types are accepted by the tensor cores in K-major and MN-major layout.
+inline Codec codec_for(int p) { return p <= 31 ? CODEC_F8 : CODEC_BF16; }
 inline int codec_bytes(Codec c) { return c == CODEC_F8 ? 1 : 2; }
 
 // A device matrix in the internal codec: rows x cols, row-major, ld elements.

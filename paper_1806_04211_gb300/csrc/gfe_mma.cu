@@ -2,8 +2,9 @@
 // (the job MAD of arXiv 1806.04211, Section 4.1; the dominant cost of the
 // method, Section 5).
 //
-// Operands are stored as bf16 centred residues (|c| <= 125, exact in bf16).
-// The MMA (tcgen05.mma kind::f16, bf16 x bf16 -> fp32 in TMEM) is exact as
+// Operands are stored as centred residues: e4m3 for p <= 31 (|c| <= 15,
+// tcgen05.mma kind::f8f6f4) or bf16 (|c| <= 125, kind::f16), both with fp32
+// accumulation in TMEM.  The MMA is exact as
 // long as every partial sum is an integer below 2^24 in magnitude, so the
 // host splits K into chunks of at most (2^24 - 1) / cmax^2 (cmax = the
 // largest centred magnitude, (p-1)/2, or 1 for GF(2)); each chunk's result
@@ -11,10 +12,11 @@
 // representation of field elements the paper cites as prior art (Section 1)
 // with the exact integer reduction done here.
 //
-// Kernel: one CTA of 128 threads per 128 x 256 tile of C.
-//   warp 0 lane 0 : TMA producer (A tile 128 x 64, K-major, 128B swizzle;
-//                   B tile 64 x 256 as four 64 x 64 MN-major slabs)
-//   warp 1 lane 0 : MMA issuer (4 x tcgen05.mma M128 N256 K16 per stage)
+// Kernel: one CTA of 128 threads per 128 x 256 tile of C; a stage holds 128
+// bytes of K per row (64 bf16 / 128 e4m3).
+//   warp 0 lane 0 : TMA producer (A tile 128 rows x 128 B, K-major, 128B
+//                   swizzle; B as MN-major slabs 128 B wide)
+//   warp 1 lane 0 : MMA issuer (4 x tcgen05.mma M128 N256, 32 bytes of K each)
 //   all 4 warps   : epilogue, warp w reads TMEM lanes 32w..32w+31
 // Four pipeline stages with full/empty mbarriers; every wait is bounded by a
 // %globaltimer limit after which the CTA records an error, frees its TMEM
@@ -30,11 +32,27 @@ namespace gfe {
 
 namespace {
 
-constexpr int TBM = 128, TBN = 256, TBK = 64, TSTAGES = 4;
-constexpr int A_STAGE = TBM * TBK * 2;  // 16 KB
-constexpr int B_SLAB = TBK * 64 * 2;    // 8 KB: 64 K-rows x 64 N-columns
-constexpr int B_STAGE = 4 * B_SLAB;     // 32 KB
-constexpr int TC_SMEM = TSTAGES * (A_STAGE + B_STAGE) + 1024 + 256;
+constexpr int TBM = 128, TBN = 256, TSTAGES = 4;
+
+// Per element width: a stage holds 128 bytes of K per row (64 bf16 or 128
+// e4m3), one MMA instruction consumes 32 bytes of K (16 bf16 or 32 e4m3), and
+// B arrives as 128-byte-wide MN-major slabs (64 or 128 columns).
+template <bool F8> struct Cfg {
+    static constexpr int ES = F8 ? 1 : 2;
+    static constexpr int TBK = 128 / ES;
+    static constexpr int KPI = 32 / ES;
+    static constexpr int SLAB_N = 128 / ES;
+    static constexpr int NSLAB = TBN / SLAB_N;
+    static constexpr int A_STAGE = TBM * 128;        // 16 KB
+    static constexpr int B_SLAB = TBK * 128;         // TBK K-rows x 128 B
+    static constexpr int B_STAGE = NSLAB * B_SLAB;   // 32 KB
+    // instruction descriptor: D f32; A, B bf16 (kind::f16) or e4m3
+    // (kind::f8f6f4); A K-major, B MN-major; N = 256, M = 128
+    static constexpr uint32_t IDESC = (1u << 4) | ((F8 ? 0u : 1u) << 7) | ((F8 ? 0u : 1u) << 10) | (0u << 15) |
+                                      (1u << 16) | ((uint32_t)(TBN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+};
+constexpr int TC_SMEM = TSTAGES * (Cfg<false>::A_STAGE + Cfg<false>::B_STAGE) + 1024 + 256;
+constexpr int TBK = 64;  // K granule that keeps chunk offsets 16-byte aligned for both widths
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -96,13 +114,21 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;
 }
 
-// instruction descriptor, kind::f16: D f32, A and B bf16, A K-major,
-// B MN-major, N = 256, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (1u << 16) |
-                           ((uint32_t)(TBN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
-
 __device__ __forceinline__ int bf16_int(uint16_t b) { return (int)__uint_as_float((uint32_t)b << 16); }
 __device__ __forceinline__ uint16_t int_bf16(int c) { return (uint16_t)(__float_as_uint((float)c) >> 16); }
+// e4m3 of a centred residue |c| <= 15 (all such integers are exact in e4m3)
+__device__ __forceinline__ int e4m3_int(uint32_t b) {
+    const int mag = b & 0x7F;
+    if (mag < 0x38) return 0;
+    const int v = ((8 + (mag & 7)) << ((mag >> 3) - 7)) >> 3;
+    return (b & 0x80) ? -v : v;
+}
+__device__ __forceinline__ uint32_t int_e4m3(int c) {
+    if (c == 0) return 0;
+    const int sg = c < 0, a = sg ? -c : c;
+    const int e = 31 - __clz(a);
+    return (uint32_t)((sg << 7) | ((e + 7) << 3) | (((a << 3) >> e) - 8));
+}
 
 // x mod p in [0, p) for |x| < 2^24: the float quotient is off by at most one
 __device__ __forceinline__ int modp_f(int x, int p, float invp) {
@@ -119,9 +145,12 @@ __device__ __forceinline__ int centre(int r, int p) {
     return r > (p >> 1) ? r - p : r;
 }
 
+template <bool F8>
 __global__ void __launch_bounds__(128, 1)
     k_mad_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int p, int M,
-             int N, int K, const uint16_t *W, int64_t ldw, uint16_t *C, int64_t ldc, int *err) {
+             int N, int K, const void *Wv, int64_t ldw, void *Cv, int64_t ldc, int *err) {
+    using G = Cfg<F8>;
+    constexpr int TBK = G::TBK, A_STAGE = G::A_STAGE, B_STAGE = G::B_STAGE, B_SLAB = G::B_SLAB;
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = sm;
@@ -132,7 +161,8 @@ __global__ void __launch_bounds__(128, 1)
     __shared__ int bad;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+    // M tiles vary fastest: CTAs resident together share the same B columns
+    const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
     const int nk = (K + TBK - 1) / TBK;
 
     if (threadIdx.x == 0) {
@@ -166,7 +196,8 @@ __global__ void __launch_bounds__(128, 1)
             mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
             tma_load_2d(sA + s * A_STAGE, &mapA, kb * TBK, m0, &full[s]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tma_load_2d(sB + s * B_STAGE + q * B_SLAB, &mapB, n0 + 64 * q, kb * TBK, &full[s]);
+            for (int q = 0; q < G::NSLAB; ++q)
+                tma_load_2d(sB + s * B_STAGE + q * B_SLAB, &mapB, n0 + G::SLAB_N * q, kb * TBK, &full[s]);
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
@@ -182,16 +213,22 @@ __global__ void __launch_bounds__(128, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(sA + s * A_STAGE), b0 = smem_u32(sB + s * B_STAGE);
 #pragma unroll
-            for (int kk = 0; kk < TBK / 16; ++kk) {
-                // A: K-major, advance 16 elements (32 B) inside the swizzle atom
+            for (int kk = 0; kk < TBK / G::KPI; ++kk) {
+                // A: K-major, advance 32 bytes of K inside the swizzle atom
                 const uint64_t ad = sdesc(a0 + kk * 32, 16, 1024);
-                // B: MN-major, 16 K-rows = 2 KB further; slabs 8 KB apart
-                const uint64_t bd = sdesc(b0 + kk * 2048, B_SLAB, 1024);
+                // B: MN-major, KPI K-rows of 128 B further; slabs B_SLAB apart
+                const uint64_t bd = sdesc(b0 + kk * G::KPI * 128, B_SLAB, 1024);
                 const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                if constexpr (F8)
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(G::IDESC), "r"(acc));
+                else
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(G::IDESC), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&empty[s]))
@@ -211,8 +248,8 @@ __global__ void __launch_bounds__(128, 1)
         const int row = m0 + warp * 32 + lane;
         const float invp = 1.0f / (float)p;
         // 16-byte vector access of W and C when their rows are 16-byte aligned
-        const bool vec = ((ldc * 2) % 16 == 0) && (((uintptr_t)C & 15) == 0) &&
-                         (!W || (((ldw * 2) % 16 == 0) && (((uintptr_t)W & 15) == 0)));
+        const bool vec = ((ldc * G::ES) % 16 == 0) && (((uintptr_t)Cv & 15) == 0) &&
+                         (!Wv || (((ldw * G::ES) % 16 == 0) && (((uintptr_t)Wv & 15) == 0)));
 #pragma unroll 1
         for (int c0 = 0; c0 < TBN; c0 += 32) {
             uint32_t v[32];
@@ -233,28 +270,58 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) out[j] = modp_f((int)__uint_as_float(v[j]), p, invp);
                 if (vec && cb + 32 <= N) {
-                    if (W) {
-                        const uint4 *wp = (const uint4 *)(W + (int64_t)row * ldw + cb);
+                    if constexpr (F8) {
+                        const uint8_t *W = (const uint8_t *)Wv;
+                        if (W) {
+                            const uint4 *wp = (const uint4 *)(W + (int64_t)row * ldw + cb);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            uint4 w4 = wp[q];
-                            const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+                            for (int q = 0; q < 2; ++q) {
+                                const uint4 w4 = wp[q];
+                                const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                            for (int h = 0; h < 4; ++h) {
-                                out[8 * q + 2 * h] += bf16_int((uint16_t)(ww[h] & 0xFFFF));
-                                out[8 * q + 2 * h + 1] += bf16_int((uint16_t)(ww[h] >> 16));
+                                for (int h = 0; h < 4; ++h)
+#pragma unroll
+                                    for (int b = 0; b < 4; ++b) out[16 * q + 4 * h + b] += e4m3_int((ww[h] >> (8 * b)) & 0xFF);
                             }
                         }
-                    }
-                    uint4 *cp = (uint4 *)(C + (int64_t)row * ldc + cb);
+                        uint4 *cp = (uint4 *)((uint8_t *)Cv + (int64_t)row * ldc + cb);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t ww[4];
+                        for (int q = 0; q < 2; ++q) {
+                            uint32_t ww[4];
 #pragma unroll
-                        for (int h = 0; h < 4; ++h)
-                            ww[h] = (uint32_t)int_bf16(centre(out[8 * q + 2 * h], p)) |
-                                    ((uint32_t)int_bf16(centre(out[8 * q + 2 * h + 1], p)) << 16);
-                        cp[q] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+                            for (int h = 0; h < 4; ++h) {
+                                uint32_t x = 0;
+#pragma unroll
+                                for (int b = 0; b < 4; ++b) x |= int_e4m3(centre(out[16 * q + 4 * h + b], p)) << (8 * b);
+                                ww[h] = x;
+                            }
+                            cp[q] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+                        }
+                    } else {
+                        const uint16_t *W = (const uint16_t *)Wv;
+                        if (W) {
+                            const uint4 *wp = (const uint4 *)(W + (int64_t)row * ldw + cb);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const uint4 w4 = wp[q];
+                                const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                                for (int h = 0; h < 4; ++h) {
+                                    out[8 * q + 2 * h] += bf16_int((uint16_t)(ww[h] & 0xFFFF));
+                                    out[8 * q + 2 * h + 1] += bf16_int((uint16_t)(ww[h] >> 16));
+                                }
+                            }
+                        }
+                        uint4 *cp = (uint4 *)((uint16_t *)Cv + (int64_t)row * ldc + cb);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            uint32_t ww[4];
+#pragma unroll
+                            for (int h = 0; h < 4; ++h)
+                                ww[h] = (uint32_t)int_bf16(centre(out[8 * q + 2 * h], p)) |
+                                        ((uint32_t)int_bf16(centre(out[8 * q + 2 * h + 1], p)) << 16);
+                            cp[q] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+                        }
                     }
                 } else {
 #pragma unroll
@@ -262,8 +329,13 @@ __global__ void __launch_bounds__(128, 1)
                         const int col = cb + j;
                         if (col < N) {
                             int x = out[j];
-                            if (W) x += bf16_int(W[(int64_t)row * ldw + col]);
-                            C[(int64_t)row * ldc + col] = int_bf16(centre(x, p));
+                            if constexpr (F8) {
+                                if (Wv) x += e4m3_int(((const uint8_t *)Wv)[(int64_t)row * ldw + col]);
+                                ((uint8_t *)Cv)[(int64_t)row * ldc + col] = (uint8_t)int_e4m3(centre(x, p));
+                            } else {
+                                if (Wv) x += bf16_int(((const uint16_t *)Wv)[(int64_t)row * ldw + col]);
+                                ((uint16_t *)Cv)[(int64_t)row * ldc + col] = int_bf16(centre(x, p));
+                            }
                         }
                     }
                 }
@@ -305,7 +377,9 @@ int *dev_setup() {
     if (!g_attr_dev[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_tc_err) != cudaSuccess) return nullptr;
-        if (cudaFuncSetAttribute(k_mad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_mad_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_mad_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess)
             return nullptr;
         g_err_dev[dev] = (int *)p;
         g_attr_dev[dev] = true;
@@ -325,14 +399,16 @@ bool init_tc() {
     return g_encode != nullptr;
 }
 
-// 2-D bf16 tensor map: inner dimension `inner` (contiguous), `outer` rows
-// of pitch `ld` elements, box (64, box_outer), 128-byte swizzle, zero fill.
-bool make_map(CUtensorMap *map, const void *base, int64_t inner, int64_t outer, int64_t ld, int box_outer) {
+// 2-D tensor map of bf16 (es = 2) or byte (es = 1) elements: inner dimension
+// `inner` (contiguous), `outer` rows of pitch `ld` elements, box of 128
+// bytes x box_outer, 128-byte swizzle, zero fill out of bounds.
+bool make_map(CUtensorMap *map, const void *base, int64_t inner, int64_t outer, int64_t ld, int box_outer, int es) {
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {64, (cuuint32_t)box_outer};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                          const_cast<void *>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -342,7 +418,7 @@ inline bool al16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
 
-// largest K (multiple of the 64-deep k-block) whose partial sums stay exact
+// largest K (multiple of 64) whose fp32 partial sums stay exact integers
 int64_t tc_k_chunk(int p) {
     const int64_t cmax = p == 2 ? 1 : (p - 1) / 2;
     const int64_t kc = (((int64_t)1 << 24) - 1) / (cmax * cmax);
@@ -351,30 +427,33 @@ int64_t tc_k_chunk(int p) {
 
 bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_t ldw, const void *A, int64_t lda,
             const void *B, int64_t ldb, void *C, int64_t ldc) {
-    if (L.codec != CODEC_BF16) return false;
-    if (!al16(A) || !al16(B) || (lda * 2) % 16 || (ldb * 2) % 16) return false;
-    if (m > (1 << 30) || n > (1 << 30)) return false;
+    const bool f8 = L.codec == CODEC_F8;
+    const int es = f8 ? 1 : 2;
+    if (!al16(A) || !al16(B) || (lda * es) % 16 || (ldb * es) % 16) return false;
+    if (m > (1 << 30) || n > ((int64_t)65535 * TBN)) return false;
     if (!init_tc()) return false;
     int *err = dev_setup();
     if (!err) return false;
     const int64_t kc = tc_k_chunk(L.p);
     for (int64_t k0 = 0; k0 < k; k0 += kc) {
         const int64_t kk = k - k0 < kc ? k - k0 : kc;
-        const uint16_t *Ak = (const uint16_t *)A + k0;
-        const uint16_t *Bk = (const uint16_t *)B + k0 * ldb;
+        const char *Ak = (const char *)A + k0 * es;
+        const char *Bk = (const char *)B + k0 * ldb * es;
         CUtensorMap ma, mb;
-        if (!make_map(&ma, Ak, kk, m, lda, TBM) || !make_map(&mb, Bk, n, kk, ldb, TBK)) {
+        if (!make_map(&ma, Ak, kk, m, lda, TBM, es) || !make_map(&mb, Bk, n, kk, ldb, 128 / es, es)) {
             if (k0 == 0) return false;  // nothing launched yet: the caller takes the plain path
             mad_plain(L, m, n, k - k0, C, ldc, Ak, lda, Bk, ldb, C, ldc);
             return true;
         }
         const void *Wk = k0 ? C : W;
         const int64_t ldwk = k0 ? ldc : ldw;
-        dim3 grid((unsigned)((n + TBN - 1) / TBN), (unsigned)((m + TBM - 1) / TBM));
+        dim3 grid((unsigned)((m + TBM - 1) / TBM), (unsigned)((n + TBN - 1) / TBN));
         cudaEvent_t ev;
         prof_begin(L, K_MAD_TC, &ev);
-        k_mad_tc<<<grid, 128, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, (const uint16_t *)Wk, ldwk,
-                                               (uint16_t *)C, ldc, err);
+        if (f8)
+            k_mad_tc<true><<<grid, 128, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C, ldc, err);
+        else
+            k_mad_tc<false><<<grid, 128, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C, ldc, err);
         prof_end(L, K_MAD_TC, ev, (double)m * (double)n * (double)kk);
     }
     return true;

@@ -154,21 +154,24 @@ def _kchunk(p):
     return ((1 << 24) - 1) // (cmax * cmax) // 64 * 64
 
 
-@pytest.mark.parametrize("p", [2, 3, 7, 31, 251])
+@pytest.mark.parametrize("p", [2, 3, 7, 31, 37, 251])
 def test_mad_tensor_exact_at_the_accumulation_bound(p):
-    """Every product at the largest centred magnitude, same sign, with K past
-    the exact-accumulation chunk: the fp32 partial sums reach just below 2^24."""
-    cmax_res = 1 if p == 2 else (p - 1) // 2          # centred +cmax
-    k = _kchunk(p) + 200 if p > 7 else 4096
-    m, n = 130, 300
-    A = torch.full((m, k), cmax_res, dtype=torch.uint8)
-    B = torch.full((k, n), cmax_res, dtype=torch.uint8)
-    B[:, 1::2] = (p - cmax_res) % p                    # -cmax in odd columns
+    """Every product at the largest centred magnitude and of one sign per
+    column, with K just past the exact-accumulation chunk (capped at 2^20 for
+    p <= 3): the fp32 partial sums come within one chunk of 2^24 (2^20).  The
+    expected value is the closed form K * (+-cmax^2) + W mod p."""
+    cmax = 1 if p == 2 else (p - 1) // 2
+    k = min(_kchunk(p) + 200, 1 << 20)
+    m, n = 8, 40
+    A = torch.full((m, k), cmax, dtype=torch.uint8, device=DEV)
+    B = torch.full((k, n), cmax, dtype=torch.uint8, device=DEV)
+    B[:, 1::2] = (p - cmax) % p                        # -cmax in odd columns
     W = synth.uniform_u8(m, n, p, 2, 0)
-    ref = (W.numpy().astype(np.int64) + A.numpy().astype(np.int64) @ B.numpy().astype(np.int64)) % p
+    sign = np.where(np.arange(n) % 2 == 0, 1, -1)
+    ref = (W.numpy().astype(np.int64) + (k * cmax * cmax) * sign[None, :]) % p
     gfe.profile_enable(True)
     gfe.profile_read(True)
-    got = gfe.mad(W.to(DEV), A.to(DEV), B.to(DEV), p, impl="tensor").cpu().numpy()
+    got = gfe.mad(W.to(DEV), A, B, p, impl="tensor").cpu().numpy()
     prof = gfe.profile_read(True)
     gfe.profile_enable(False)
     assert prof["launches"]["mad_tensor"] >= 1 and prof["launches"]["mad_plain"] == 0
