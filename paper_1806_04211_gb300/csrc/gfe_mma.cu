@@ -12,19 +12,22 @@
 // representation of field elements the paper cites as prior art (Section 1)
 // with the exact integer reduction done here.
 //
-// Kernel: one CTA of 128 threads per 128 x 256 tile of C; a stage holds 128
-// bytes of K per row (64 bf16 / 128 e4m3).
-//   warp 0 lane 0 : TMA producer (A tile 128 rows x 128 B, K-major, 128B
-//                   swizzle; B as MN-major slabs 128 B wide)
-//   warp 1 lane 0 : MMA issuer (4 x tcgen05.mma M128 N256, 32 bytes of K each)
-//   all 4 warps   : epilogue, warp w reads TMEM lanes 32w..32w+31
-// Four pipeline stages with full/empty mbarriers; every wait is bounded by a
-// %globaltimer limit after which the CTA records an error, frees its TMEM
-// and returns.
+// Kernel (persistent, one CTA of 320 threads per SM, 128 x 256 tiles):
+//   warp 0 lane 0 : TMA producer (A tile 128 rows x 128 B of K, K-major,
+//                   128B swizzle; B as 128-byte-wide MN-major slabs)
+//   warp 1 lane 0 : MMA issuer (4 x tcgen05.mma M128 N256, 32 bytes of K
+//                   each, per stage) into one of two TMEM accumulators
+//   warps 2..9    : epilogue, warp w reads TMEM lanes 32(w%4).. and one half
+//                   of the columns; reduces mod p in fp32 (exact below 2^24),
+//                   adds W and packs with cvt to e4m3x2 / bf16x2
+// Four pipeline stages with full/empty mbarriers and two accumulator
+// full/empty pairs; every wait is bounded by a %globaltimer limit after
+// which the CTA records an error, frees its TMEM and returns.
 #include "gfe_internal.h"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <mutex>
 
@@ -114,39 +117,42 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;
 }
 
-__device__ __forceinline__ int bf16_int(uint16_t b) { return (int)__uint_as_float((uint32_t)b << 16); }
-__device__ __forceinline__ uint16_t int_bf16(int c) { return (uint16_t)(__float_as_uint((float)c) >> 16); }
-// e4m3 of a centred residue |c| <= 15 (all such integers are exact in e4m3)
-__device__ __forceinline__ int e4m3_int(uint32_t b) {
-    const int mag = b & 0x7F;
-    if (mag < 0x38) return 0;
-    const int v = ((8 + (mag & 7)) << ((mag >> 3) - 7)) >> 3;
-    return (b & 0x80) ? -v : v;
-}
-__device__ __forceinline__ uint32_t int_e4m3(int c) {
-    if (c == 0) return 0;
-    const int sg = c < 0, a = sg ? -c : c;
-    const int e = 31 - __clz(a);
-    return (uint32_t)((sg << 7) | ((e + 7) << 3) | (((a << 3) >> e) - 8));
+// mod p of an exactly integer-valued float |x| < 2^24: the quotient from the
+// reciprocal is off by at most one and the fma residual is exact
+__device__ __forceinline__ float fmodp(float x, float pf, float invp) {
+    const float q = floorf(x * invp);
+    float r = fmaf(-q, pf, x);
+    r = r < 0.f ? r + pf : r;
+    return r >= pf ? r - pf : r;
 }
 
-// x mod p in [0, p) for |x| < 2^24: the float quotient is off by at most one
-__device__ __forceinline__ int modp_f(int x, int p, float invp) {
-    const int q = (int)floorf((float)x * invp);
-    int r = x - q * p;
-    if (r < 0) r += p;
-    if (r >= p) r -= p;
-    return r;
+__device__ __forceinline__ uint32_t pack_e4m3x2(float lo, float hi) {
+    uint16_t d;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+    return d;
 }
-// r in [-(p-1)/2 - p, 2p): the centred representative of r mod p
-__device__ __forceinline__ int centre(int r, int p) {
-    if (r < 0) r += p;
-    if (r >= p) r -= p;
-    return r > (p >> 1) ? r - p : r;
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ void unpack_e4m3x2(uint32_t two, float &lo, float &hi) {
+    uint32_t h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"((uint16_t)two));
+    lo = __half2float(__ushort_as_half((unsigned short)(h2 & 0xFFFF)));
+    hi = __half2float(__ushort_as_half((unsigned short)(h2 >> 16)));
 }
 
+constexpr int TC_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int EPI_WARPS = 8;
+
+// Persistent: CTA c handles tiles c, c + gridDim.x, ...; tile t covers rows
+// (t % mt) * 128 and columns (t / mt) * 256 (M fastest, so CTAs resident at
+// the same time share B's columns).  The accumulator is double-buffered in
+// TMEM (2 x 256 fp32 columns) so the epilogue of one tile overlaps the MMAs
+// of the next.
 template <bool F8>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_mad_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int p, int M,
              int N, int K, const void *Wv, int64_t ldw, void *Cv, int64_t ldc, int *err) {
     using G = Cfg<F8>;
@@ -156,13 +162,13 @@ __global__ void __launch_bounds__(128, 1)
     uint8_t *sA = sm;
     uint8_t *sB = sm + TSTAGES * A_STAGE;
     uint64_t *bars = (uint64_t *)(sm + TSTAGES * (A_STAGE + B_STAGE));
-    uint64_t *full = bars, *empty = bars + TSTAGES, *accb = bars + 2 * TSTAGES;
+    uint64_t *full = bars, *empty = bars + TSTAGES;
+    uint64_t *accf = bars + 2 * TSTAGES, *acce = bars + 2 * TSTAGES + 2;
     __shared__ uint32_t tmem_base;
-    __shared__ int bad;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // M tiles vary fastest: CTAs resident together share the same B columns
-    const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
+    const int mt = (M + TBM - 1) / TBM, nt = (N + TBN - 1) / TBN;
+    const int ntiles = mt * nt;
     const int nk = (K + TBK - 1) / TBK;
 
     if (threadIdx.x == 0) {
@@ -170,13 +176,15 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
-        bad = 0;
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], EPI_WARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(TBN));
+                     "r"(2 * TBN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -184,177 +192,217 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
-    if (warp == 0 && lane == 0) {
-        // ---- TMA producer ----
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % TSTAGES;
-            const uint32_t ph = (uint32_t)(kb / TSTAGES) & 1u;
-            if (kb >= TSTAGES && !mbar_wait(&empty[s], ph ^ 1u, err)) {
-                bad = 1;
-                break;
-            }
-            mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
-            tma_load_2d(sA + s * A_STAGE, &mapA, kb * TBK, m0, &full[s]);
+    if (warp == 0) {
+        // ---- TMA producer (one lane) ----
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int m0 = (t % mt) * TBM, n0 = (t / mt) * TBN;
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = it % TSTAGES;
+                    const uint32_t ph = (uint32_t)(it / TSTAGES) & 1u;
+                    if (it >= TSTAGES && !mbar_wait(&empty[s], ph ^ 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
+                    tma_load_2d(sA + s * A_STAGE, &mapA, kb * TBK, m0, &full[s]);
 #pragma unroll
-            for (int q = 0; q < G::NSLAB; ++q)
-                tma_load_2d(sB + s * B_STAGE + q * B_SLAB, &mapB, n0 + G::SLAB_N * q, kb * TBK, &full[s]);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer ----
-        bool ok = true;
-        for (int kb = 0; kb < nk && ok; ++kb) {
-            const int s = kb % TSTAGES;
-            const uint32_t ph = (uint32_t)(kb / TSTAGES) & 1u;
-            if (!mbar_wait(&full[s], ph, err)) {
-                ok = false;
-                bad = 1;
-                break;
+                    for (int q = 0; q < G::NSLAB; ++q)
+                        tma_load_2d(sB + s * B_STAGE + q * B_SLAB, &mapB, n0 + G::SLAB_N * q, kb * TBK, &full[s]);
+                }
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA + s * A_STAGE), b0 = smem_u32(sB + s * B_STAGE);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMA issuer (one lane) ----
+        if (lane == 0) {
+            int it = 0, i = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+                const int b = i & 1;
+                const uint32_t use = (uint32_t)(i >> 1);
+                if (i >= 2 && !mbar_wait(&acce[b], (use & 1u) ^ 1u, err)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(b * TBN);
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = it % TSTAGES;
+                    const uint32_t ph = (uint32_t)(it / TSTAGES) & 1u;
+                    if (!mbar_wait(&full[s], ph, err)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(sA + s * A_STAGE), b0 = smem_u32(sB + s * B_STAGE);
 #pragma unroll
-            for (int kk = 0; kk < TBK / G::KPI; ++kk) {
-                // A: K-major, advance 32 bytes of K inside the swizzle atom
-                const uint64_t ad = sdesc(a0 + kk * 32, 16, 1024);
-                // B: MN-major, KPI K-rows of 128 B further; slabs B_SLAB apart
-                const uint64_t bd = sdesc(b0 + kk * G::KPI * 128, B_SLAB, 1024);
-                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                if constexpr (F8)
-                    asm volatile(
-                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(G::IDESC), "r"(acc));
-                else
-                    asm volatile(
-                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(G::IDESC), "r"(acc));
+                    for (int kk = 0; kk < TBK / G::KPI; ++kk) {
+                        const uint64_t ad = sdesc(a0 + kk * 32, 16, 1024);
+                        const uint64_t bd = sdesc(b0 + kk * G::KPI * 128, B_SLAB, 1024);
+                        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                        if constexpr (F8)
+                            asm volatile(
+                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                                "l"(ad), "l"(bd), "r"(G::IDESC), "r"(acc));
+                        else
+                            asm volatile(
+                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                                "l"(ad), "l"(bd), "r"(G::IDESC), "r"(acc));
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&empty[s]))
+                                 : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&accf[b]))
+                             : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&empty[s]))
-                         : "memory");
         }
-        if (ok)
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(accb))
-                         : "memory");
-    }
-    __syncwarp();
-
-    // ---- epilogue: TMEM -> registers -> (+W) mod p -> C ----
-    const bool have = __all_sync(0xffffffffu, mbar_wait(accb, 0, err));
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (have) {
-        const int row = m0 + warp * 32 + lane;
-        const float invp = 1.0f / (float)p;
-        // 16-byte vector access of W and C when their rows are 16-byte aligned
+        __syncwarp();
+    } else {
+        // ---- epilogue: 8 warps; warp w reads TMEM lanes 32*(w%4).. and one
+        //      half (128 columns) of the 256-column accumulator ----
+        const int e = warp - 2;
+        const int quarter = warp & 3, half = e >> 2;
+        const float pf = (float)p, invp = 1.0f / (float)p, halfp = (float)(p >> 1);
         const bool vec = ((ldc * G::ES) % 16 == 0) && (((uintptr_t)Cv & 15) == 0) &&
                          (!Wv || (((ldw * G::ES) % 16 == 0) && (((uintptr_t)Wv & 15) == 0)));
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int b = i & 1;
+            const uint32_t use = (uint32_t)(i >> 1);
+            const bool have = __all_sync(0xffffffffu, mbar_wait(&accf[b], use & 1u, err));
+            if (!have) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (t % mt) * TBM, n0 = (t / mt) * TBN;
+            const int row = m0 + quarter * 32 + lane;
 #pragma unroll 1
-        for (int c0 = 0; c0 < TBN; c0 += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < M) {
+            for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TBN + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                    "[%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row >= M) continue;
                 const int cb = n0 + c0;
-                int out[32];
+                float x[32];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) out[j] = modp_f((int)__uint_as_float(v[j]), p, invp);
-                if (vec && cb + 32 <= N) {
-                    if constexpr (F8) {
-                        const uint8_t *W = (const uint8_t *)Wv;
-                        if (W) {
-                            const uint4 *wp = (const uint4 *)(W + (int64_t)row * ldw + cb);
+                for (int j = 0; j < 32; ++j) x[j] = fmodp(__uint_as_float(v[j]), pf, invp);
+                const bool full_chunk = vec && cb + 32 <= N;
+                // + W (centred, |w| <= (p-1)/2), back into [0, p), then centred
+                if (Wv) {
+                    if (full_chunk) {
+                        if constexpr (F8) {
+                            const uint4 *wp = (const uint4 *)((const uint8_t *)Wv + (int64_t)row * ldw + cb);
 #pragma unroll
                             for (int q = 0; q < 2; ++q) {
                                 const uint4 w4 = wp[q];
                                 const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                                for (int h = 0; h < 4; ++h)
-#pragma unroll
-                                    for (int b = 0; b < 4; ++b) out[16 * q + 4 * h + b] += e4m3_int((ww[h] >> (8 * b)) & 0xFF);
+                                for (int h = 0; h < 4; ++h) {
+                                    float a0, a1, a2, a3;
+                                    unpack_e4m3x2(ww[h] & 0xFFFF, a0, a1);
+                                    unpack_e4m3x2(ww[h] >> 16, a2, a3);
+                                    x[16 * q + 4 * h] += a0;
+                                    x[16 * q + 4 * h + 1] += a1;
+                                    x[16 * q + 4 * h + 2] += a2;
+                                    x[16 * q + 4 * h + 3] += a3;
+                                }
                             }
-                        }
-                        uint4 *cp = (uint4 *)((uint8_t *)Cv + (int64_t)row * ldc + cb);
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            uint32_t ww[4];
-#pragma unroll
-                            for (int h = 0; h < 4; ++h) {
-                                uint32_t x = 0;
-#pragma unroll
-                                for (int b = 0; b < 4; ++b) x |= int_e4m3(centre(out[16 * q + 4 * h + b], p)) << (8 * b);
-                                ww[h] = x;
-                            }
-                            cp[q] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
-                        }
-                    } else {
-                        const uint16_t *W = (const uint16_t *)Wv;
-                        if (W) {
-                            const uint4 *wp = (const uint4 *)(W + (int64_t)row * ldw + cb);
+                        } else {
+                            const uint4 *wp = (const uint4 *)((const uint16_t *)Wv + (int64_t)row * ldw + cb);
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
                                 const uint4 w4 = wp[q];
                                 const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                                 for (int h = 0; h < 4; ++h) {
-                                    out[8 * q + 2 * h] += bf16_int((uint16_t)(ww[h] & 0xFFFF));
-                                    out[8 * q + 2 * h + 1] += bf16_int((uint16_t)(ww[h] >> 16));
+                                    x[8 * q + 2 * h] += __uint_as_float(ww[h] << 16);
+                                    x[8 * q + 2 * h + 1] += __uint_as_float(ww[h] & 0xFFFF0000u);
                                 }
                             }
                         }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (cb + j >= N) continue;
+                            if constexpr (F8) {
+                                float lo, hi;
+                                unpack_e4m3x2(((const uint8_t *)Wv)[(int64_t)row * ldw + cb + j], lo, hi);
+                                x[j] += lo;
+                            } else {
+                                x[j] += __uint_as_float((uint32_t)((const uint16_t *)Wv)[(int64_t)row * ldw + cb + j]
+                                                        << 16);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        float r = x[j];
+                        r = r < 0.f ? r + pf : r;
+                        x[j] = r >= pf ? r - pf : r;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) x[j] = x[j] > halfp ? x[j] - pf : x[j];
+                if (full_chunk) {
+                    if constexpr (F8) {
+                        uint4 *cp = (uint4 *)((uint8_t *)Cv + (int64_t)row * ldc + cb);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            uint32_t ww[4];
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const int j = 16 * q + 4 * h;
+                                ww[h] = pack_e4m3x2(x[j], x[j + 1]) | (pack_e4m3x2(x[j + 2], x[j + 3]) << 16);
+                            }
+                            cp[q] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+                        }
+                    } else {
                         uint4 *cp = (uint4 *)((uint16_t *)Cv + (int64_t)row * ldc + cb);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             uint32_t ww[4];
 #pragma unroll
-                            for (int h = 0; h < 4; ++h)
-                                ww[h] = (uint32_t)int_bf16(centre(out[8 * q + 2 * h], p)) |
-                                        ((uint32_t)int_bf16(centre(out[8 * q + 2 * h + 1], p)) << 16);
+                            for (int h = 0; h < 4; ++h) ww[h] = pack_bf16x2(x[8 * q + 2 * h], x[8 * q + 2 * h + 1]);
                             cp[q] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
                         }
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int col = cb + j;
-                        if (col < N) {
-                            int x = out[j];
-                            if constexpr (F8) {
-                                if (Wv) x += e4m3_int(((const uint8_t *)Wv)[(int64_t)row * ldw + col]);
-                                ((uint8_t *)Cv)[(int64_t)row * ldc + col] = (uint8_t)int_e4m3(centre(x, p));
-                            } else {
-                                if (Wv) x += bf16_int(((const uint16_t *)Wv)[(int64_t)row * ldw + col]);
-                                ((uint16_t *)Cv)[(int64_t)row * ldc + col] = int_bf16(centre(x, p));
-                            }
-                        }
+                        if (cb + j >= N) continue;
+                        if constexpr (F8)
+                            ((uint8_t *)Cv)[(int64_t)row * ldc + cb + j] = (uint8_t)(pack_e4m3x2(x[j], 0.f) & 0xFF);
+                        else
+                            ((uint16_t *)Cv)[(int64_t)row * ldc + cb + j] = (uint16_t)(pack_bf16x2(x[j], 0.f) & 0xFFFF);
                     }
                 }
             }
+            // this warp has read its part of accumulator b: release it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (bad && threadIdx.x == 0) {
-        // drain the TMA loads that may still be in flight (bounded)
-        for (int s = 0; s < TSTAGES; ++s) {
-            uint64_t t0 = gtimer();
-            while (!mbar_test(&full[s], 0) && !mbar_test(&full[s], 1) && gtimer() - t0 < WAIT_NS / 4) {
-            }
-        }
-    }
-    __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
 }
 
 // ---- host side ----
@@ -368,6 +416,8 @@ std::mutex g_dev_mu;
 constexpr int MAX_DEV = 64;
 int *g_err_dev[MAX_DEV] = {};
 bool g_attr_dev[MAX_DEV] = {};
+
+int g_num_sms = 148;
 
 // per-device set-up with the device current; returns the error word
 int *dev_setup() {
@@ -383,6 +433,9 @@ int *dev_setup() {
             return nullptr;
         g_err_dev[dev] = (int *)p;
         g_attr_dev[dev] = true;
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            g_num_sms = nsm;
     }
     return g_err_dev[dev];
 }
@@ -430,7 +483,7 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
     const bool f8 = L.codec == CODEC_F8;
     const int es = f8 ? 1 : 2;
     if (!al16(A) || !al16(B) || (lda * es) % 16 || (ldb * es) % 16) return false;
-    if (m > (1 << 30) || n > ((int64_t)65535 * TBN)) return false;
+    if (m > (1 << 30) || n > (1 << 30) || ((m + TBM - 1) / TBM) * ((n + TBN - 1) / TBN) > INT32_MAX) return false;
     if (!init_tc()) return false;
     int *err = dev_setup();
     if (!err) return false;
@@ -447,13 +500,16 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
         }
         const void *Wk = k0 ? C : W;
         const int64_t ldwk = k0 ? ldc : ldw;
-        dim3 grid((unsigned)((m + TBM - 1) / TBM), (unsigned)((n + TBN - 1) / TBN));
+        const int64_t tiles = ((m + TBM - 1) / TBM) * ((n + TBN - 1) / TBN);
+        const unsigned grid = (unsigned)(tiles < g_num_sms ? tiles : g_num_sms);
         cudaEvent_t ev;
         prof_begin(L, K_MAD_TC, &ev);
         if (f8)
-            k_mad_tc<true><<<grid, 128, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C, ldc, err);
+            k_mad_tc<true><<<grid, TC_THREADS, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C,
+                                                                ldc, err);
         else
-            k_mad_tc<false><<<grid, 128, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C, ldc, err);
+            k_mad_tc<false><<<grid, TC_THREADS, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C,
+                                                                 ldc, err);
         prof_end(L, K_MAD_TC, ev, (double)m * (double)n * (double)kk);
     }
     return true;
