@@ -176,7 +176,9 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);
  * recorded on the stream they are launched on.  mask 0 disables. */
 typedef struct {
     int64_t launches[8];     /* by kind: 0 MAD tensor, 1 MAD plain, 2 ECH leaf,   */
-    double  ms[8];           /*   3 extract/riffle, 4 convert/assemble, 5 other   */
+    double  ms[8];           /*   3 row extract/riffle (REX, RRF), 4 column        */
+                             /*   extract/riffle (CEX, CRZ), 5 copy/zero/ADI,     */
+                             /*   6 convert/assemble, 7 other                     */
     double  madds[8];        /* algorithmic multiply-adds done by the MAD kinds  */
     int64_t timed[8];        /* launches that were timed                         */
     int64_t host_syncs;      /* stream synchronisations made by the planner      */

@@ -128,6 +128,13 @@ static DMat sub(const Ctx &X, const DMat &d, int64_t r0, int64_t c0, int64_t row
     return s;
 }
 
+// a view that the tensor-core multiply-add can take as its A or B operand
+// (16-byte aligned start and pitch); always true in the dry run
+static bool tma_ok(const Ctx &X, const DMat &d) {
+    if (X.dry) return true;
+    return ((uintptr_t)d.ptr & 15) == 0 && (d.ld * X.es) % 16 == 0;
+}
+
 // ---- job wrappers (no-ops in the dry run that sizes the workspace) ----
 static void j_mad(Ctx &X, int64_t m, int64_t n, int64_t k, const DMat *W, const DMat &A, const DMat &B,
                   const DMat &C) {
@@ -327,6 +334,7 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
             // ---------- Task ClearDown ----------
             EchRes e;
             std::vector<int32_t> lam;
+            DMat AAv = AA;  // A.A (a gathered copy or a view of C_ij)
             if (i == 0) {
                 DMat Rd = DR[j];
                 ech(X, Cij, AM, AK, Rd, e);
@@ -335,12 +343,22 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
             } else {
                 const std::vector<int32_t> &g = gam[j];
                 std::vector<int32_t> ng = complement(g, bj);
-                // (CEX) A.A = C gamma^tr, A' = C gamma_bar^tr
-                j_cols(X, al, r, AA, Cij, g);
-                DMat Hh = sub(X, Hb, 0, 0, al, bj - r);
-                j_cols(X, al, bj - r, Hh, Cij, ng);
+                // (CEX) A.A = C gamma^tr, A' = C gamma_bar^tr.  When gamma is the
+                // leading columns 0..r-1 both are column ranges of C: use views
+                // (C_ij is dead after ClearDown; ECH may overwrite A' in place).
+                bool prefix = true;
+                for (int64_t t = 0; t < r && prefix; ++t) prefix = g[t] == t;
+                DMat Hh;
+                if (prefix && tma_ok(X, Cij)) {
+                    AAv = sub(X, Cij, 0, 0, al, r);
+                    Hh = sub(X, Cij, 0, r, al, bj - r);
+                } else {
+                    j_cols(X, al, r, AA, Cij, g);
+                    Hh = sub(X, Hb, 0, 0, al, bj - r);
+                    j_cols(X, al, bj - r, Hh, Cij, ng);
+                }
                 // (MAD) H := A' + A.A x D.R
-                j_mad(X, al, bj - r, r, &Hh, AA, DR[j], Hh);
+                j_mad(X, al, bj - r, r, &Hh, AAv, DR[j], Hh);
                 // (ECH)
                 ech(X, Hh, AM, AK, Rech, e);
                 const int64_t rp = e.r;
@@ -369,7 +387,7 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
             const int64_t wc = beta - co[j + 1];
             DMat Z = sub(X, H, ro[i], co[j + 1], al, wc);
             if (wc > 0) {
-                if (i > 0) j_mad(X, al, wc, r, &Z, AA, Bp[j], Z);           // (1) Z := C + A.A x B
+                if (i > 0) j_mad(X, al, wc, r, &Z, AAv, Bp[j], Z);          // (1) Z := C + A.A x B
                 if (rp > 0) {
                     DMat Vv = V, Ww = W, Xx = Xb;
                     j_rows(X, rp, wc, Vv, Z, nullptr, e.rho);               // (2) REX
@@ -394,24 +412,26 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                     const int64_t nc = (int64_t)del.size();
                     DMat Kih = sub(X, Kp[i], 0, ro[h], al, nc);
                     DMat Mjh = sub(X, Mp[j], 0, ro[h], r, nc);
-                    DMat Zz = Zt;
                     const bool first_j = (j == 0);
                     if (h != i && wM[j][h] != nc) {  // M_jh not stored yet: it is zero
                         j_zero(X, r, nc, Mjh);
                         wM[j][h] = nc;
                     }
+                    // Z is built in place in K_ih's slot when CRZ would not move
+                    // a column (no new pivot rows of block row h here), or when
+                    // K_ih is 0 so far (j = 1, h != i); otherwise in Zt.
+                    bool nonew = true;
+                    for (int32_t dbit : del) nonew = nonew && dbit == 0;
+                    const bool inplace = first_j ? (h != i) : nonew;
+                    DMat Zz = inplace ? Kih : Zt;
                     // (+) CRZ, (1)
-                    if (!first_j) {
+                    if (!first_j && !inplace) {
                         DMat Kold = sub(X, Kp[i], 0, ro[h], al, wK[i][h]);
                         j_cols(X, al, nc, Zz, Kold, crz_map(del));
                     }
-                    if (h != i) {
-                        j_mad(X, al, nc, r, first_j ? nullptr : &Zz, AA, Mjh, Zz);
-                    } else if (first_j) {
-                        // Z is 0 (K_ii empty so far)
-                    }
+                    if (h != i) j_mad(X, al, nc, r, first_j ? nullptr : &Zz, AAv, Mjh, Zz);
                     if (rp == 0) {  // nothing pivotal: K := Z, M unchanged
-                        j_copy(X, al, nc, Kih, Zz);
+                        if (!inplace) j_copy(X, al, nc, Kih, Zz);
                         wK[i][h] = nc;
                         continue;
                     }

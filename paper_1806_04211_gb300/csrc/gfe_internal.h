@@ -30,7 +30,7 @@ struct DMat {
 };
 
 // Kernel kinds for the profile counters (match gfe_profile in gfe.h).
-enum Kind { K_MAD_TC = 0, K_MAD_PLAIN = 1, K_ECH = 2, K_MOVE = 3, K_CONV = 4, K_OTHER = 5 };
+enum Kind { K_MAD_TC = 0, K_MAD_PLAIN = 1, K_ECH = 2, K_ROWS = 3, K_COLS = 4, K_COPY = 5, K_CONV = 6, K_OTHER = 7 };
 
 struct Launch {  // per-call launch context
     cudaStream_t st = nullptr;

@@ -196,9 +196,15 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(int p, int alpha, int beta
     if (y < 3) best[y] = INT_MAX;
     piv[y] = 0;
     slotOf[y] = -1;
-    if (y < alpha) {
-        for (int c = 0; c < beta; ++c) S[y * LS + c] = (uint8_t)res(D::dec(H[(int64_t)y * ldh + c]), p);
-        for (int c = 0; c < 64; ++c) Tt[y * LS + c] = 0;
+    // coalesced load: warp w reads its 32 rows, lane l columns l and l + 32
+    for (int rr = 0; rr < 32; ++rr) {
+        const int row = warp * 32 + rr;
+        if (row >= alpha) break;
+        const typename D::T *hr = H + (int64_t)row * ldh;
+        S[row * LS + lane] = lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
+        S[row * LS + 32 + lane] = 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
+        Tt[row * LS + lane] = 0;
+        Tt[row * LS + 32 + lane] = 0;
     }
     __syncthreads();
 
@@ -267,25 +273,24 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(int p, int alpha, int beta
     }
     if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
     __syncthreads();
+    // outputs: one row per warp, lanes along the columns (coalesced)
     // M[l][s] = coefficient of pivot row rho_s in echelon row l
-    for (int idx = y; idx < r * r; idx += 1024) {
-        int l = idx / r, s = idx % r;
-        Mo[(int64_t)l * ldm + s] = D::enc(cen(Tt[slotRow[l] * LS + sortedSlot[s]], p));
-    }
+    for (int l = warp; l < r; l += 32)
+        for (int s = lane; s < r; s += 32)
+            Mo[(int64_t)l * ldm + s] = D::enc(cen(Tt[slotRow[l] * LS + sortedSlot[s]], p));
     // K[t][s] for the non-pivot rows t
     if (r > 0) {
-        for (int64_t idx = y; idx < (int64_t)alpha * r; idx += 1024) {
-            int row = (int)(idx / r), s = (int)(idx % r);
+        for (int row = warp; row < alpha; row += 32) {
             if (piv[row]) continue;
-            Ko[(int64_t)pivpos[row] * ldk + s] = D::enc(cen(Tt[row * LS + sortedSlot[s]], p));
+            for (int s = lane; s < r; s += 32)
+                Ko[(int64_t)pivpos[row] * ldk + s] = D::enc(cen(Tt[row * LS + sortedSlot[s]], p));
         }
     }
     // R[l][j] = entry of echelon row l in the j-th non-pivot column
     const int nr = beta - r;
-    for (int idx = y; idx < r * nr; idx += 1024) {
-        int l = idx / nr, j = idx % nr;
-        Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
-    }
+    for (int l = warp; l < r; l += 32)
+        for (int j = lane; j < nr; j += 32)
+            Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
 }
 
 // ---------------------------------------------------------------------------
@@ -330,13 +335,47 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         h[w] = 0;
         t[w] = 0;
     }
-    if (y < alpha) {
-        const T *row = H + (int64_t)y * ldh;
+    // coalesced load: warp w reads its 32 rows one at a time, lane l the 8
+    // columns 8l..8l+7, and stores their non-zero pattern as byte l of the
+    // row's bitmask (W = 4 words = 32 bytes)
+    {
+        static_assert(W == 4, "one bitmask byte per lane");
+        uint8_t *hb = (uint8_t *)hw;
+        for (int rr = 0; rr < 32; ++rr) {
+            const int row = warp * 32 + rr;
+            uint32_t mask = 0;
+            if (row < alpha) {
+                const T *rp = H + (int64_t)row * ldh + 8 * lane;
+                const int c0 = 8 * lane;
+                if (c0 + 8 <= beta && ((uintptr_t)rp & (8 * sizeof(T) - 1)) == 0) {
+                    if constexpr (sizeof(T) == 1) {
+                        const uint2 v = *(const uint2 *)rp;
 #pragma unroll
-        for (int w = 0; w < W; ++w)
-            for (int c = 64 * w; c < beta && c < 64 * (w + 1); ++c)
-                if (row[c]) h[w] |= (uint64_t)1 << (c & 63);
+                        for (int b = 0; b < 4; ++b) {
+                            mask |= ((v.x >> (8 * b)) & 0xFF) ? 1u << b : 0u;
+                            mask |= ((v.y >> (8 * b)) & 0xFF) ? 1u << (4 + b) : 0u;
+                        }
+                    } else {
+                        const uint4 v = *(const uint4 *)rp;
+                        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            mask |= (vv[b] & 0xFFFF) ? 1u << (2 * b) : 0u;
+                            mask |= (vv[b] >> 16) ? 1u << (2 * b + 1) : 0u;
+                        }
+                    }
+                } else {
+                    for (int b = 0; b < 8 && c0 + b < beta; ++b)
+                        if (rp[b]) mask |= 1u << b;
+                }
+            }
+            hb[row * 8 * W + lane] = (uint8_t)mask;
+        }
     }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < W; ++w) h[w] = hw[y * W + w];
+    __syncthreads();
     if (y < 3) best[y] = INT_MAX;
     piv[y] = 0;
     slotOf[y] = -1;
@@ -410,21 +449,32 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
     }
     if (y < r) info[1 + 64 * W + y] = slotCol[y];
     __syncthreads();
-    for (int idx = y; idx < r * r; idx += 1024) {
-        int l = idx / r, s = idx % r, q = sortedSlot[s];
-        Mo[(int64_t)l * ldm + s] = ((tw[slotRow[l] * W + (q >> 6)] >> (q & 63)) & 1) ? one : (T)0;
+    // outputs: one row per warp, lanes along the columns (coalesced)
+    for (int l = warp; l < r; l += 32) {
+        const uint64_t *tl = tw + slotRow[l] * W;
+        for (int s = lane; s < r; s += 32) {
+            const int q = sortedSlot[s];
+            Mo[(int64_t)l * ldm + s] = ((tl[q >> 6] >> (q & 63)) & 1) ? one : (T)0;
+        }
     }
     if (r > 0) {
-        for (int64_t idx = y; idx < (int64_t)alpha * r; idx += 1024) {
-            int row = (int)(idx / r), s = (int)(idx % r), q = sortedSlot[s];
+        for (int row = warp; row < alpha; row += 32) {
             if (piv[row]) continue;
-            Ko[(int64_t)pivpos[row] * ldk + s] = ((tw[row * W + (q >> 6)] >> (q & 63)) & 1) ? one : (T)0;
+            const uint64_t *tr = tw + row * W;
+            T *ko = Ko + (int64_t)pivpos[row] * ldk;
+            for (int s = lane; s < r; s += 32) {
+                const int q = sortedSlot[s];
+                ko[s] = ((tr[q >> 6] >> (q & 63)) & 1) ? one : (T)0;
+            }
         }
     }
     const int nr = beta - r;
-    for (int idx = y; idx < r * nr; idx += 1024) {
-        int l = idx / nr, j = idx % nr, c = nonCol[j];
-        Ro[(int64_t)l * ldr + j] = ((hw[slotRow[l] * W + (c >> 6)] >> (c & 63)) & 1) ? one : (T)0;
+    for (int l = warp; l < r; l += 32) {
+        const uint64_t *hl = hw + slotRow[l] * W;
+        for (int j = lane; j < nr; j += 32) {
+            const int c = nonCol[j];
+            Ro[(int64_t)l * ldr + j] = ((hl[c >> 6] >> (c & 63)) & 1) ? one : (T)0;
+        }
     }
 }
 
@@ -528,14 +578,14 @@ void gather_rows(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64
     // one CTA row per output row (nrows <= 65535 always holds: rows <= blocks)
     dim3 grid(cdiv(ncols, 256) > 64 ? 64 : cdiv(ncols, 256), (unsigned)(nrows < 65535 ? nrows : 65535));
     cudaEvent_t ev;
-    prof_begin(L, K_MOVE, &ev);
+    prof_begin(L, K_ROWS, &ev);
     if (L.codec == CODEC_F8)
         k_gather_rows<uint8_t><<<grid, 256, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
             (const uint8_t *)A, lda, (const uint8_t *)B, ldb, map);
     else
         k_gather_rows<uint16_t><<<grid, 256, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
             (const uint16_t *)A, lda, (const uint16_t *)B, ldb, map);
-    prof_end(L, K_MOVE, ev, 0);
+    prof_end(L, K_ROWS, ev, 0);
 }
 
 void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
@@ -543,25 +593,25 @@ void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64
     if (nrows <= 0 || ncols <= 0) return;
     dim3 grid(cdiv(ncols, 128), (unsigned)(nrows < 4096 ? nrows : 4096));
     cudaEvent_t ev;
-    prof_begin(L, K_MOVE, &ev);
+    prof_begin(L, K_COLS, &ev);
     if (L.codec == CODEC_F8)
         k_gather_cols<uint8_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
             (const uint8_t *)src, lds, map);
     else
         k_gather_cols<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
             (const uint16_t *)src, lds, map);
-    prof_end(L, K_MOVE, ev, 0);
+    prof_end(L, K_COLS, ev, 0);
 }
 
 void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const int32_t *pos) {
     if (count <= 0) return;
     cudaEvent_t ev;
-    prof_begin(L, K_MOVE, &ev);
+    prof_begin(L, K_COPY, &ev);
     if (L.codec == CODEC_F8)
         k_set_ones<uint8_t><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint8_t *)V, ldv, pos, (uint8_t)0x38);
     else
         k_set_ones<uint16_t><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint16_t *)V, ldv, pos, (uint16_t)0x3F80);
-    prof_end(L, K_MOVE, ev, 0);
+    prof_end(L, K_COPY, ev, 0);
 }
 
 void copy2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd, const void *src,
@@ -569,12 +619,12 @@ void copy2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
     if (rows <= 0 || cols <= 0) return;
     dim3 grid = grid_rc(rows, cols, 256);
     cudaEvent_t ev;
-    prof_begin(L, K_MOVE, &ev);
+    prof_begin(L, K_COPY, &ev);
     if (L.codec == CODEC_F8)
         k_copy2d<uint8_t><<<grid, 256, 0, L.st>>>(rows, cols, (uint8_t *)dst, ldd, (const uint8_t *)src, lds);
     else
         k_copy2d<uint16_t><<<grid, 256, 0, L.st>>>(rows, cols, (uint16_t *)dst, ldd, (const uint16_t *)src, lds);
-    prof_end(L, K_MOVE, ev, 0);
+    prof_end(L, K_COPY, ev, 0);
 }
 
 void zero2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd) {

@@ -40,7 +40,7 @@ class GfeProfile(ctypes.Structure):
                 ("timed", _i64 * 8), ("host_syncs", _i64)]
 
 
-KINDS = ["mad_tensor", "mad_plain", "ech_leaf", "move", "convert", "other"]
+KINDS = ["mad_tensor", "mad_plain", "ech_leaf", "rows", "cols", "copy", "convert", "other"]
 
 
 # every symbol declared in include/gfe.h, with its ctypes signature
