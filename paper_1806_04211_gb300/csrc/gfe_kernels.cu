@@ -316,33 +316,29 @@ template <int W> __device__ __forceinline__ void wxor(uint64_t (&a)[W], int i, u
 }
 
 template <int W, typename T>
-__global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, const T *H, int64_t ldh,
-                                                          int32_t *info, T *Mo, int64_t ldm, T *Ko,
-                                                          int64_t ldk, T *Ro, int64_t ldr, T one) {
+__global__ void __launch_bounds__(256, 1) k_ech_leaf_gf2(int alpha, int beta, const T *H, int64_t ldh,
+                                                         int32_t *info, T *Mo, int64_t ldm, T *Ko,
+                                                         int64_t ldk, T *Ro, int64_t ldr, T one) {
+    // 256 threads; thread t owns rows t, t + 256, t + 512, t + 768
+    constexpr int NT = 256, RPT = 4, NW = NT / 32;
+    static_assert(W == 4, "one bitmask byte per lane in the load");
     extern __shared__ uint64_t smw[];
     uint64_t *hw = smw;                 // [1024][W] rows after elimination
     uint64_t *tw = smw + 1024 * W;      // [1024][W] slot coefficients
-    __shared__ uint64_t wbuf[3][32][2 * W];
+    __shared__ uint64_t wbuf[3][NW][2 * W];
     __shared__ int best[3];
     __shared__ uint8_t piv[1024];
     __shared__ int16_t slotOf[1024], pivpos[1024];
     __shared__ int16_t slotRow[64 * W], slotCol[64 * W], sortedSlot[64 * W], nonCol[64 * W];
-    __shared__ int wsum[32];
-    const int y = threadIdx.x, lane = y & 31, warp = y >> 5;
-    uint64_t h[W], t[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        h[w] = 0;
-        t[w] = 0;
-    }
-    // coalesced load: warp w reads its 32 rows one at a time, lane l the 8
-    // columns 8l..8l+7, and stores their non-zero pattern as byte l of the
-    // row's bitmask (W = 4 words = 32 bytes)
+    __shared__ int wsum[NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // coalesced load: warp w reads rows 128w..128w+127 one at a time, lane l
+    // the 8 columns 8l..8l+7, stored as byte l of the row's 32-byte bitmask
     {
-        static_assert(W == 4, "one bitmask byte per lane");
         uint8_t *hb = (uint8_t *)hw;
-        for (int rr = 0; rr < 32; ++rr) {
-            const int row = warp * 32 + rr;
+        for (int rr = 0; rr < 128; ++rr) {
+            const int row = warp * 128 + rr;
             uint32_t mask = 0;
             if (row < alpha) {
                 const T *rp = H + (int64_t)row * ldh + 8 * lane;
@@ -351,95 +347,139 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
                     if constexpr (sizeof(T) == 1) {
                         const uint2 v = *(const uint2 *)rp;
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            mask |= ((v.x >> (8 * b)) & 0xFF) ? 1u << b : 0u;
-                            mask |= ((v.y >> (8 * b)) & 0xFF) ? 1u << (4 + b) : 0u;
+                        for (int q = 0; q < 4; ++q) {
+                            mask |= ((v.x >> (8 * q)) & 0xFF) ? 1u << q : 0u;
+                            mask |= ((v.y >> (8 * q)) & 0xFF) ? 1u << (4 + q) : 0u;
                         }
                     } else {
                         const uint4 v = *(const uint4 *)rp;
                         const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            mask |= (vv[b] & 0xFFFF) ? 1u << (2 * b) : 0u;
-                            mask |= (vv[b] >> 16) ? 1u << (2 * b + 1) : 0u;
+                        for (int q = 0; q < 4; ++q) {
+                            mask |= (vv[q] & 0xFFFF) ? 1u << (2 * q) : 0u;
+                            mask |= (vv[q] >> 16) ? 1u << (2 * q + 1) : 0u;
                         }
                     }
                 } else {
-                    for (int b = 0; b < 8 && c0 + b < beta; ++b)
-                        if (rp[b]) mask |= 1u << b;
+                    for (int q = 0; q < 8 && c0 + q < beta; ++q)
+                        if (rp[q]) mask |= 1u << q;
                 }
             }
             hb[row * 8 * W + lane] = (uint8_t)mask;
         }
     }
     __syncthreads();
+    uint64_t h[RPT][W], t[RPT][W];
+    bool isp[RPT];
 #pragma unroll
-    for (int w = 0; w < W; ++w) h[w] = hw[y * W + w];
+    for (int k = 0; k < RPT; ++k) {
+        const int row = tid + NT * k;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            h[k][w] = hw[row * W + w];
+            t[k][w] = 0;
+        }
+        isp[k] = false;
+        piv[row] = 0;
+        slotOf[row] = -1;
+    }
+    if (tid < 3) best[tid] = INT_MAX;
     __syncthreads();
-    if (y < 3) best[y] = INT_MAX;
-    piv[y] = 0;
-    slotOf[y] = -1;
-    bool isp = false;
-    __syncthreads();
+
     int ns = 0;
     for (int c = 0; c < beta; ++c) {
         const int b = c % 3;
-        if (y == 0) best[(c + 1) % 3] = INT_MAX;
-        const int cw = c >> 6;
-        const bool hit = (wpick<W>(h, cw) >> (c & 63)) & 1;
-        const bool cand = (y < alpha) && !isp && hit;
-        const unsigned bal = __ballot_sync(0xffffffffu, cand);
-        if (bal && lane == __ffs(bal) - 1) {
+        if (tid == 0) best[(c + 1) % 3] = INT_MAX;
+        const int cw = c >> 6, cb = c & 63;
+        bool hit[RPT];
+        int myc = INT_MAX, myk = 0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                wbuf[b][warp][w] = h[w];
-                wbuf[b][warp][W + w] = t[w];
+        for (int k = 0; k < RPT; ++k) {
+            hit[k] = (wpick<W>(h[k], cw) >> cb) & 1;
+            if (hit[k] && !isp[k] && tid + NT * k < alpha && myc == INT_MAX) {
+                myc = tid + NT * k;
+                myk = k;
             }
-            atomicMin(&best[b], y);
+        }
+        const int wmin = (int)__reduce_min_sync(0xffffffffu, (unsigned)myc);
+        if (wmin != INT_MAX && myc == wmin) {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+                if (k == myk) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        wbuf[b][warp][w] = h[k][w];
+                        wbuf[b][warp][W + w] = t[k][w];
+                    }
+                }
+            atomicMin(&best[b], wmin);
         }
         __syncthreads();
         const int x = best[b];
         if (x == INT_MAX) continue;  // uniform: column c has no pivot
-        const uint64_t *px = wbuf[b][x >> 5];
-        if (y == x) {
-            wxor<W>(t, ns >> 6, (uint64_t)1 << (ns & 63));  // own identity in slot ns
-            isp = true;
-            piv[y] = 1;
-            slotOf[y] = (int16_t)ns;
-            slotRow[ns] = (int16_t)y;
-            slotCol[ns] = (int16_t)c;
-        } else if (hit) {
+        const uint64_t *px = wbuf[b][(x & (NT - 1)) >> 5];
+        const uint64_t own = (uint64_t)1 << (ns & 63);
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                h[w] ^= px[w];
-                t[w] ^= px[W + w];
+        for (int k = 0; k < RPT; ++k) {
+            const int row = tid + NT * k;
+            if (row == x) {
+                wxor<W>(t[k], ns >> 6, own);  // own identity in slot ns
+                isp[k] = true;
+                piv[row] = 1;
+                slotOf[row] = (int16_t)ns;
+                slotRow[ns] = (int16_t)row;
+                slotCol[ns] = (int16_t)c;
+            } else if (hit[k]) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    h[k][w] ^= px[w];
+                    t[k][w] ^= px[W + w];
+                }
+                wxor<W>(t[k], ns >> 6, own);  // the pivot's own identity
             }
-            wxor<W>(t, ns >> 6, (uint64_t)1 << (ns & 63));  // the pivot's own identity
         }
         ++ns;
     }
     const int r = ns;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-        hw[y * W + w] = h[w];
-        tw[y * W + w] = t[w];
-    }
-    unsigned bal = __ballot_sync(0xffffffffu, isp);
-    if (lane == 0) wsum[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0;
-    for (int w = 0; w < warp; ++w) before += wsum[w];
-    before += __popc(bal & ((1u << lane) - 1));
-    if (y < alpha) {
-        if (isp) {
-            pivpos[y] = (int16_t)before;
-            sortedSlot[before] = slotOf[y];
-            info[1 + before] = y;
-        } else {
-            pivpos[y] = (int16_t)(y - before);
+    for (int k = 0; k < RPT; ++k) {
+        const int row = tid + NT * k;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            hw[row * W + w] = h[k][w];
+            tw[row * W + w] = t[k][w];
         }
     }
-    if (y == 0) {
+    __syncthreads();
+    // rank of each row among the pivot rows (ascending) and the other rows:
+    // thread t scans rows 4t..4t+3, then a block-wide exclusive scan
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cnt += (4 * tid + q < alpha) && piv[4 * tid + q];
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int before = incl - cnt;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int row = 4 * tid + q;
+        if (row >= alpha) break;
+        if (piv[row]) {
+            pivpos[row] = (int16_t)before;
+            sortedSlot[before] = slotOf[row];
+            info[1 + before] = row;
+            ++before;
+        } else {
+            pivpos[row] = (int16_t)(row - before);
+        }
+    }
+    if (tid == 0) {
         info[0] = r;
         int j = 0, l = 0;
         for (int c = 0; c < beta; ++c) {
@@ -447,10 +487,10 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
             else nonCol[j++] = (int16_t)c;
         }
     }
-    if (y < r) info[1 + 64 * W + y] = slotCol[y];
+    for (int l = tid; l < r; l += NT) info[1 + 64 * W + l] = slotCol[l];
     __syncthreads();
     // outputs: one row per warp, lanes along the columns (coalesced)
-    for (int l = warp; l < r; l += 32) {
+    for (int l = warp; l < r; l += NW) {
         const uint64_t *tl = tw + slotRow[l] * W;
         for (int s = lane; s < r; s += 32) {
             const int q = sortedSlot[s];
@@ -458,7 +498,7 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         }
     }
     if (r > 0) {
-        for (int row = warp; row < alpha; row += 32) {
+        for (int row = warp; row < alpha; row += NW) {
             if (piv[row]) continue;
             const uint64_t *tr = tw + row * W;
             T *ko = Ko + (int64_t)pivpos[row] * ldk;
@@ -469,7 +509,7 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         }
     }
     const int nr = beta - r;
-    for (int l = warp; l < r; l += 32) {
+    for (int l = warp; l < r; l += NW) {
         const uint64_t *hl = hw + slotRow[l] * W;
         for (int j = lane; j < nr; j += 32) {
             const int c = nonCol[j];
@@ -492,14 +532,14 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
                 cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
                 attr[0] = true;
             }
-            k_ech_leaf_gf2<4, uint8_t><<<1, 1024, smem, L.st>>>((int)alpha, (int)beta, (const uint8_t *)H, ldh, info,
+            k_ech_leaf_gf2<4, uint8_t><<<1, 256, smem, L.st>>>((int)alpha, (int)beta, (const uint8_t *)H, ldh, info,
                 (uint8_t *)M, ldm, (uint8_t *)K, ldk, (uint8_t *)R, ldr, (uint8_t)0x38);
         } else {
             if (!attr[1]) {
                 cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
                 attr[1] = true;
             }
-            k_ech_leaf_gf2<4, uint16_t><<<1, 1024, smem, L.st>>>((int)alpha, (int)beta, (const uint16_t *)H, ldh,
+            k_ech_leaf_gf2<4, uint16_t><<<1, 256, smem, L.st>>>((int)alpha, (int)beta, (const uint16_t *)H, ldh,
                 info, (uint16_t *)M, ldm, (uint16_t *)K, ldk, (uint16_t *)R, ldr, (uint16_t)0x3F80);
         }
         prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta));
@@ -530,26 +570,59 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
 // ---------------------------------------------------------------------------
 // extracts / riffles (jobs REX, RRF, CEX, CRZ, ADI) -- pure data movement
 // ---------------------------------------------------------------------------
+// copy one row segment: 16-byte vectors when both ends allow it
 template <typename T>
-__global__ void k_gather_rows(int64_t nrows, int64_t ncols, T *dst, int64_t ldd, const T *A,
-                              int64_t lda, const T *B, int64_t ldb, const int32_t *map) {
-    for (int64_t row = blockIdx.y; row < nrows; row += gridDim.y) {
-        int32_t s = map[row];
-        const T *src = s >= 0 ? A + (int64_t)s * lda : B + (int64_t)(-1 - s) * ldb;
-        T *d = dst + row * ldd;
-        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += (int64_t)gridDim.x * blockDim.x)
-            d[c] = src[c];
+__device__ __forceinline__ void copy_row(T *d, const T *src, int64_t ncols, int64_t t0, int64_t stride) {
+    const int64_t bytes = ncols * (int64_t)sizeof(T);
+    if ((((uintptr_t)d | (uintptr_t)src) & 15) == 0) {
+        const int64_t nv = bytes >> 4;
+        const uint4 *s4 = (const uint4 *)src;
+        uint4 *d4 = (uint4 *)d;
+        for (int64_t v = t0; v < nv; v += stride) d4[v] = s4[v];
+        for (int64_t c = (nv << 4) / (int64_t)sizeof(T) + t0; c < ncols; c += stride) d[c] = src[c];
+    } else {
+        for (int64_t c = t0; c < ncols; c += stride) d[c] = src[c];
     }
 }
 
 template <typename T>
+__global__ void k_gather_rows(int64_t nrows, int64_t ncols, T *dst, int64_t ldd, const T *A,
+                              int64_t lda, const T *B, int64_t ldb, const int32_t *map) {
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t row = blockIdx.y; row < nrows; row += gridDim.y) {
+        int32_t s = map[row];
+        const T *src = s >= 0 ? A + (int64_t)s * lda : B + (int64_t)(-1 - s) * ldb;
+        copy_row(dst + row * ldd, src, ncols, t0, stride);
+    }
+}
+
+// each thread: 4 consecutive output columns of a set of rows; the map is
+// read once, the 4 results are stored as one vector when aligned
+template <typename T>
 __global__ void k_gather_cols(int64_t nrows, int64_t ncols, T *dst, int64_t ldd, const T *src,
                               int64_t lds, const int32_t *map) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncols) return;
-    int32_t s = map[c];
-    for (int64_t row = blockIdx.y; row < nrows; row += gridDim.y)
-        dst[row * ldd + c] = s >= 0 ? src[row * lds + s] : (T)0;
+    const int64_t c0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (c0 >= ncols) return;
+    const int nc = ncols - c0 < 4 ? (int)(ncols - c0) : 4;
+    int32_t s[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] = q < nc ? map[c0 + q] : -1;
+    const bool vec = nc == 4 && (((uintptr_t)(dst + c0) | (uintptr_t)(ldd * sizeof(T))) & (4 * sizeof(T) - 1)) == 0;
+    for (int64_t row = blockIdx.y; row < nrows; row += gridDim.y) {
+        const T *sr = src + row * lds;
+        T v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = s[q] >= 0 ? sr[s[q]] : (T)0;
+        T *dr = dst + row * ldd + c0;
+        if (vec) {
+            if constexpr (sizeof(T) == 1)
+                *(uint32_t *)dr = (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16) | ((uint32_t)v[3] << 24);
+            else
+                *(uint2 *)dr = make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16), (uint32_t)v[2] | ((uint32_t)v[3] << 16));
+        } else {
+            for (int q = 0; q < nc; ++q) dr[q] = v[q];
+        }
+    }
 }
 
 template <typename T>
@@ -560,9 +633,19 @@ __global__ void k_set_ones(int64_t count, T *V, int64_t ldv, const int32_t *pos,
 
 template <typename T>
 __global__ void k_copy2d(int64_t rows, int64_t cols, T *dst, int64_t ldd, const T *src, int64_t lds) {
-    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
-        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += (int64_t)gridDim.x * blockDim.x)
-            dst[row * ldd + c] = src ? src[row * lds + c] : (T)0;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        T *d = dst + row * ldd;
+        if (src) {
+            copy_row(d, src + row * lds, cols, t0, stride);
+        } else if (((uintptr_t)d & 15) == 0) {
+            const int64_t nv = (cols * (int64_t)sizeof(T)) >> 4;
+            for (int64_t v = t0; v < nv; v += stride) ((uint4 *)d)[v] = make_uint4(0, 0, 0, 0);
+            for (int64_t c = (nv << 4) / (int64_t)sizeof(T) + t0; c < cols; c += stride) d[c] = (T)0;
+        } else {
+            for (int64_t c = t0; c < cols; c += stride) d[c] = (T)0;
+        }
+    }
 }
 
 static dim3 grid_rc(int64_t rows, int64_t cols, int threads) {
@@ -576,14 +659,15 @@ void gather_rows(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64
                  const void *A, int64_t lda, const void *B, int64_t ldb, const int32_t *map) {
     if (nrows <= 0 || ncols <= 0) return;
     // one CTA row per output row (nrows <= 65535 always holds: rows <= blocks)
-    dim3 grid(cdiv(ncols, 256) > 64 ? 64 : cdiv(ncols, 256), (unsigned)(nrows < 65535 ? nrows : 65535));
+    const int64_t vec = (ncols * codec_bytes(L.codec) + 15) / 16;  // 16-byte vectors per row
+    dim3 grid(cdiv(vec, 128) > 32 ? 32 : cdiv(vec, 128), (unsigned)(nrows < 65535 ? nrows : 65535));
     cudaEvent_t ev;
     prof_begin(L, K_ROWS, &ev);
     if (L.codec == CODEC_F8)
-        k_gather_rows<uint8_t><<<grid, 256, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
+        k_gather_rows<uint8_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
             (const uint8_t *)A, lda, (const uint8_t *)B, ldb, map);
     else
-        k_gather_rows<uint16_t><<<grid, 256, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
+        k_gather_rows<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
             (const uint16_t *)A, lda, (const uint16_t *)B, ldb, map);
     prof_end(L, K_ROWS, ev, 0);
 }
@@ -591,7 +675,7 @@ void gather_rows(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64
 void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
                  const void *src, int64_t lds, const int32_t *map) {
     if (nrows <= 0 || ncols <= 0) return;
-    dim3 grid(cdiv(ncols, 128), (unsigned)(nrows < 4096 ? nrows : 4096));
+    dim3 grid(cdiv((ncols + 3) / 4, 128), (unsigned)(nrows < 8192 ? nrows : 8192));
     cudaEvent_t ev;
     prof_begin(L, K_COLS, &ev);
     if (L.codec == CODEC_F8)
@@ -617,7 +701,7 @@ void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const int32_
 void copy2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd, const void *src,
             int64_t lds) {
     if (rows <= 0 || cols <= 0) return;
-    dim3 grid = grid_rc(rows, cols, 256);
+    dim3 grid = grid_rc(rows, (cols * codec_bytes(L.codec) + 15) / 16, 256);
     cudaEvent_t ev;
     prof_begin(L, K_COPY, &ev);
     if (L.codec == CODEC_F8)
