@@ -117,14 +117,21 @@ gfe_status gfe_rank(const gfe_matrix *A, int64_t *rank_dev, int64_t *pivot_cols,
 
 /*
  * gfe_batch_echelon -- count independent matrices (any sizes, any fields)
- * echelonised together: the block tasks of all matrices that are ready at the
- * same stage share kernel launches.  outs[i] receives the result of As[i];
- * identical to count separate gfe_echelon calls.
+ * echelonised concurrently: a pool of host workers (gfe_set_batch_workers,
+ * default 8), each with its own CUDA stream and its own slice of the
+ * workspace, takes the matrices in order; the work is ordered after what was
+ * queued on `stream` before the call and `stream` waits for all of it.
+ * outs[i] receives the result of As[i], identical to a separate gfe_echelon
+ * call.  The paper's matrices are independent problems; the concurrency is
+ * the GPU-side analogue of its many workers (Section 2.1).
+ * gfe_query_batch_workspace: workers x the largest single workspace.
  */
 gfe_status gfe_query_batch_workspace(const gfe_matrix *As, int32_t count, uint32_t flags,
                                      size_t *ws_bytes);
 gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32_t count,
                              uint32_t flags, void *ws, size_t ws_bytes, void *stream);
+/* number of concurrent workers of gfe_batch_echelon (<= 0: default 8) */
+gfe_status gfe_set_batch_workers(int32_t workers);
 
 /*
  * gfe_mad -- the job MAD (Section 4.1): C := W + A B over GF(p), A m x k,

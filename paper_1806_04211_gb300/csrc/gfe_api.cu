@@ -6,12 +6,15 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <stdexcept>
 #include <vector>
 
 namespace gfe {
 
+static int g_batch_workers = 0;  // 0 = default (8)
 
 // ---------------------------------------------------------------------------
 // errors
@@ -178,7 +181,7 @@ static gfe_status query(const gfe_matrix *A, bool trafo, bool wantR, size_t *ws)
 
 static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_dev, int64_t *pcols,
                       int64_t *prows, uint32_t flags, bool trafo, bool wantR, void *ws, size_t ws_bytes,
-                      void *stream) {
+                      void *stream, bool check_tc = true) {
     gfe_status st = check_matrix(A);
     if (st) return st;
     size_t need = 0;
@@ -278,7 +281,7 @@ static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_
         (void)es;
         if (!cuda_ok(cudaStreamSynchronize(L.st), "final sync")) return GFE_ECUDA;
         if (!cuda_ok(cudaGetLastError(), "kernel launch")) return GFE_ECUDA;
-        if (tc_error_flag(true)) {
+        if (check_tc && tc_error_flag(true)) {
             set_error("a tensor-core multiply-add timed out waiting on its pipeline");
             return GFE_ETIMEOUT;
         }
@@ -317,6 +320,16 @@ gfe_status gfe_rank(const gfe_matrix *A, int64_t *rank_dev, int64_t *pivot_cols,
     return run(A, nullptr, rank_dev, pivot_cols, pivot_rows, flags, false, false, ws, ws_bytes, stream);
 }
 
+// ---------------------------------------------------------------------------
+// batched form: independent matrices on a pool of host workers, each with its
+// own CUDA stream and workspace slice; ordered after prior work on `stream`
+// and completed on it (events)
+// ---------------------------------------------------------------------------
+static int batch_workers(int32_t count) {
+    int w = g_batch_workers > 0 ? g_batch_workers : 8;
+    return count < w ? (count > 0 ? count : 1) : w;
+}
+
 gfe_status gfe_query_batch_workspace(const gfe_matrix *As, int32_t count, uint32_t flags, size_t *ws_bytes) {
     if (!ws_bytes || count < 0 || (count && !As)) return (set_error("bad batch arguments"), GFE_EINVAL);
     size_t best = 0;
@@ -326,17 +339,89 @@ gfe_status gfe_query_batch_workspace(const gfe_matrix *As, int32_t count, uint32
         if (st) return st;
         best = std::max(best, w);
     }
-    *ws_bytes = best;
+    *ws_bytes = al256(best) * (size_t)batch_workers(count);
     return GFE_OK;
 }
 
 gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32_t count, uint32_t flags,
                              void *ws, size_t ws_bytes, void *stream) {
     if (count < 0 || (count && (!As || !outs))) return (set_error("bad batch arguments"), GFE_EINVAL);
-    for (int32_t i = 0; i < count; ++i) {
-        gfe_status st = gfe_echelon(&As[i], &outs[i], flags, ws, ws_bytes, stream);
-        if (st) return st;
+    if (count == 0) return GFE_OK;
+    size_t need = 0;
+    gfe_status st = gfe_query_batch_workspace(As, count, flags, &need);
+    if (st) return st;
+    if (!ws || ws_bytes < need) {
+        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+        return GFE_EINVAL;
     }
+    const int nw = batch_workers(count);
+    const size_t slice = need / (size_t)nw;
+    int dev = 0;
+    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return GFE_ECUDA;
+    cudaEvent_t start;
+    if (!cuda_ok(cudaEventCreateWithFlags(&start, cudaEventDisableTiming), "event")) return GFE_ECUDA;
+    cudaEventRecord(start, (cudaStream_t)stream);
+    std::atomic<int32_t> next(0);
+    std::mutex mu;
+    gfe_status first = GFE_OK;
+    std::string first_msg;
+    std::vector<cudaStream_t> streams(nw, nullptr);
+    std::vector<cudaEvent_t> done(nw, nullptr);
+    std::vector<std::thread> pool;
+    const bool trafo = (flags & (GFE_WANT_TRANSFORM | GFE_WANT_DENSE_T)) != 0;
+    for (int w = 0; w < nw; ++w) {
+        pool.emplace_back([&, w] {
+            cudaSetDevice(dev);
+            cudaStream_t s = nullptr;
+            gfe_status mine = GFE_OK;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamWaitEvent(s, start, 0) != cudaSuccess) {
+                mine = GFE_ECUDA;
+                set_error("worker stream set-up failed");
+            }
+            streams[w] = s;
+            while (mine == GFE_OK) {
+                const int32_t i = next.fetch_add(1);
+                if (i >= count) break;
+                mine = run(&As[i], &outs[i], outs[i].rank, outs[i].pivot_cols, outs[i].pivot_rows, flags, trafo,
+                           true, (char *)ws + slice * w, slice, s, false);
+            }
+            if (mine != GFE_OK) {
+                std::lock_guard<std::mutex> g(mu);
+                if (first == GFE_OK) {
+                    first = mine;
+                    first_msg = gfe_last_error();
+                }
+                next.store(count);
+            }
+            if (s) {
+                cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming);
+                cudaEventRecord(done[w], s);
+            }
+        });
+    }
+    for (auto &t : pool) t.join();
+    for (int w = 0; w < nw; ++w) {
+        if (done[w]) {
+            cudaStreamWaitEvent((cudaStream_t)stream, done[w], 0);
+            cudaEventDestroy(done[w]);
+        }
+        if (streams[w]) cudaStreamDestroy(streams[w]);
+    }
+    cudaEventDestroy(start);
+    if (first != GFE_OK) {
+        set_error(first_msg);
+        return first;
+    }
+    if (tc_error_flag(true)) {
+        set_error("a tensor-core multiply-add timed out waiting on its pipeline");
+        return GFE_ETIMEOUT;
+    }
+    return GFE_OK;
+}
+
+gfe_status gfe_set_batch_workers(int32_t workers) {
+    g_batch_workers = workers > 0 ? (workers > 64 ? 64 : workers) : 0;
     return GFE_OK;
 }
 

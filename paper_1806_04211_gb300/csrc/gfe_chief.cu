@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <stdexcept>
 
 namespace gfe {
@@ -69,12 +70,41 @@ struct Stage {  // pinned host buffer + device ring for small index arrays
     size_t top = 0;
 };
 
-static thread_local char *t_pinned = nullptr;
+// pinned host staging buffers (download area + upload ring), borrowed by
+// each planner run and returned at its end
+static std::mutex g_stage_mu;
+static std::vector<char *> g_stage_free;
+
+static char *stage_acquire() {
+    {
+        std::lock_guard<std::mutex> g(g_stage_mu);
+        if (!g_stage_free.empty()) {
+            char *p = g_stage_free.back();
+            g_stage_free.pop_back();
+            return p;
+        }
+    }
+    char *p = nullptr;
+    if (cudaHostAlloc((void **)&p, STAGE_BYTES + 4096, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+    return p;
+}
+
+static void stage_release(char *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(g_stage_mu);
+    g_stage_free.push_back(p);
+}
+
+struct StageGuard {
+    char *p = nullptr;
+    ~StageGuard() { stage_release(p); }
+};
 
 struct Ctx {
     Launch L;
     Arena ar;
     Stage sg;
+    char *pinned = nullptr;  // download area (first 4 KB of the staging buffer)
     bool dry = false;
     int es = 1;
     int64_t syncs = 0;
@@ -252,7 +282,7 @@ void ech(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, const DMat &Ro, 
         int32_t *info = (int32_t *)X.ar.alloc(sizeof(int32_t) * (1 + 2 * lc));
         if (!X.dry) {
             ech_leaf(X.L, alpha, beta, H.ptr, H.ld, info, Mo.ptr, Mo.ld, Ko.ptr, Ko.ld, Ro.ptr, Ro.ld);
-            int32_t *h = (int32_t *)t_pinned;
+            int32_t *h = (int32_t *)X.pinned;
             X.check(cudaMemcpyAsync(h, info, sizeof(int32_t) * (1 + 2 * lc), cudaMemcpyDeviceToHost, X.L.st),
                     "download");
             X.sync();
@@ -600,15 +630,13 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
     X.ar.cap = ws_bytes;
     X.ar.top = base_used;
     X.ar.peak = base_used;
+    StageGuard guard;
     if (!dry) {
-        if (!t_pinned) {
-            if (cudaHostAlloc((void **)&t_pinned, STAGE_BYTES + 4096, cudaHostAllocDefault) != cudaSuccess) {
-                t_pinned = nullptr;
-                throw CudaError("cudaHostAlloc of the staging buffer failed");
-            }
-        }
-        // layout of t_pinned: [0, 4096) download area, then the upload ring
-        X.sg.host = t_pinned + 4096;
+        guard.p = stage_acquire();
+        if (!guard.p) throw CudaError("cudaHostAlloc of the staging buffer failed");
+        // layout: [0, 4096) download area, then the upload ring
+        X.pinned = guard.p;
+        X.sg.host = guard.p + 4096;
     }
     X.sg.dev = (char *)X.ar.alloc(STAGE_BYTES);
     std::vector<int64_t> a, b;

@@ -5,6 +5,7 @@
 #include "gfe_internal.h"
 
 #include <climits>
+#include <mutex>
 
 namespace gfe {
 
@@ -316,29 +317,29 @@ template <int W> __device__ __forceinline__ void wxor(uint64_t (&a)[W], int i, u
 }
 
 template <int W, typename T>
-__global__ void __launch_bounds__(256, 1) k_ech_leaf_gf2(int alpha, int beta, const T *H, int64_t ldh,
-                                                         int32_t *info, T *Mo, int64_t ldm, T *Ko,
-                                                         int64_t ldk, T *Ro, int64_t ldr, T one) {
-    // 256 threads; thread t owns rows t, t + 256, t + 512, t + 768
-    constexpr int NT = 256, RPT = 4, NW = NT / 32;
+__global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, const T *H, int64_t ldh,
+                                                          int32_t *info, T *Mo, int64_t ldm, T *Ko,
+                                                          int64_t ldk, T *Ro, int64_t ldr, T one) {
+    // 1024 threads, thread y owns row y (registers: W words of the row and W
+    // words of slot coefficients)
     static_assert(W == 4, "one bitmask byte per lane in the load");
     extern __shared__ uint64_t smw[];
     uint64_t *hw = smw;                 // [1024][W] rows after elimination
     uint64_t *tw = smw + 1024 * W;      // [1024][W] slot coefficients
-    __shared__ uint64_t wbuf[3][NW][2 * W];
-    __shared__ int best[3];
+    __shared__ uint64_t wbuf[2][32][2 * W];
+    __shared__ int wmin[2][32];
     __shared__ uint8_t piv[1024];
     __shared__ int16_t slotOf[1024], pivpos[1024];
     __shared__ int16_t slotRow[64 * W], slotCol[64 * W], sortedSlot[64 * W], nonCol[64 * W];
-    __shared__ int wsum[NW];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ int wsum[32];
+    const int y = threadIdx.x, lane = y & 31, warp = y >> 5;
 
-    // coalesced load: warp w reads rows 128w..128w+127 one at a time, lane l
-    // the 8 columns 8l..8l+7, stored as byte l of the row's 32-byte bitmask
+    // coalesced load: warp w reads its 32 rows one at a time, lane l the 8
+    // columns 8l..8l+7, stored as byte l of the row's 32-byte bitmask
     {
         uint8_t *hb = (uint8_t *)hw;
-        for (int rr = 0; rr < 128; ++rr) {
-            const int row = warp * 128 + rr;
+        for (int rr = 0; rr < 32; ++rr) {
+            const int row = warp * 32 + rr;
             uint32_t mask = 0;
             if (row < alpha) {
                 const T *rp = H + (int64_t)row * ldh + 8 * lane;
@@ -369,117 +370,80 @@ __global__ void __launch_bounds__(256, 1) k_ech_leaf_gf2(int alpha, int beta, co
         }
     }
     __syncthreads();
-    uint64_t h[RPT][W], t[RPT][W];
-    bool isp[RPT];
+    uint64_t h[W], t[W];
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int row = tid + NT * k;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            h[k][w] = hw[row * W + w];
-            t[k][w] = 0;
-        }
-        isp[k] = false;
-        piv[row] = 0;
-        slotOf[row] = -1;
+    for (int w = 0; w < W; ++w) {
+        h[w] = hw[y * W + w];
+        t[w] = 0;
     }
-    if (tid < 3) best[tid] = INT_MAX;
+    piv[y] = 0;
+    slotOf[y] = -1;
+    bool isp = false;
     __syncthreads();
 
+    // per column: every warp publishes its first candidate row and that
+    // row's words (double-buffered by column parity), one barrier, then every
+    // warp reduces the 32 published minima -- no atomics
     int ns = 0;
     for (int c = 0; c < beta; ++c) {
-        const int b = c % 3;
-        if (tid == 0) best[(c + 1) % 3] = INT_MAX;
+        const int b = c & 1;
         const int cw = c >> 6, cb = c & 63;
-        bool hit[RPT];
-        int myc = INT_MAX, myk = 0;
+        const bool hit = (wpick<W>(h, cw) >> cb) & 1;
+        const bool cand = (y < alpha) && !isp && hit;
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        const int first = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
+        if (lane == 0) wmin[b][warp] = first;
+        if (bal && lane == __ffs(bal) - 1) {
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            hit[k] = (wpick<W>(h[k], cw) >> cb) & 1;
-            if (hit[k] && !isp[k] && tid + NT * k < alpha && myc == INT_MAX) {
-                myc = tid + NT * k;
-                myk = k;
+            for (int w = 0; w < W; ++w) {
+                wbuf[b][warp][w] = h[w];
+                wbuf[b][warp][W + w] = t[w];
             }
-        }
-        const int wmin = (int)__reduce_min_sync(0xffffffffu, (unsigned)myc);
-        if (wmin != INT_MAX && myc == wmin) {
-#pragma unroll
-            for (int k = 0; k < RPT; ++k)
-                if (k == myk) {
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        wbuf[b][warp][w] = h[k][w];
-                        wbuf[b][warp][W + w] = t[k][w];
-                    }
-                }
-            atomicMin(&best[b], wmin);
         }
         __syncthreads();
-        const int x = best[b];
+        const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)wmin[b][lane]);
         if (x == INT_MAX) continue;  // uniform: column c has no pivot
-        const uint64_t *px = wbuf[b][(x & (NT - 1)) >> 5];
+        const uint64_t *px = wbuf[b][x >> 5];
         const uint64_t own = (uint64_t)1 << (ns & 63);
+        if (y == x) {
+            wxor<W>(t, ns >> 6, own);  // own identity in slot ns
+            isp = true;
+            piv[y] = 1;
+            slotOf[y] = (int16_t)ns;
+            slotRow[ns] = (int16_t)y;
+            slotCol[ns] = (int16_t)c;
+        } else if (hit) {
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            const int row = tid + NT * k;
-            if (row == x) {
-                wxor<W>(t[k], ns >> 6, own);  // own identity in slot ns
-                isp[k] = true;
-                piv[row] = 1;
-                slotOf[row] = (int16_t)ns;
-                slotRow[ns] = (int16_t)row;
-                slotCol[ns] = (int16_t)c;
-            } else if (hit[k]) {
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    h[k][w] ^= px[w];
-                    t[k][w] ^= px[W + w];
-                }
-                wxor<W>(t[k], ns >> 6, own);  // the pivot's own identity
+            for (int w = 0; w < W; ++w) {
+                h[w] ^= px[w];
+                t[w] ^= px[W + w];
             }
+            wxor<W>(t, ns >> 6, own);  // the pivot's own identity
         }
         ++ns;
     }
     const int r = ns;
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int row = tid + NT * k;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            hw[row * W + w] = h[k][w];
-            tw[row * W + w] = t[k][w];
-        }
+    for (int w = 0; w < W; ++w) {
+        hw[y * W + w] = h[w];
+        tw[y * W + w] = t[w];
     }
+    unsigned bal = __ballot_sync(0xffffffffu, isp);
+    if (lane == 0) wsum[warp] = __popc(bal);
     __syncthreads();
-    // rank of each row among the pivot rows (ascending) and the other rows:
-    // thread t scans rows 4t..4t+3, then a block-wide exclusive scan
-    int cnt = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cnt += (4 * tid + q < alpha) && piv[4 * tid + q];
-    int incl = cnt;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += v;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    int before = incl - cnt;
+    int before = 0;
     for (int w = 0; w < warp; ++w) before += wsum[w];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int row = 4 * tid + q;
-        if (row >= alpha) break;
-        if (piv[row]) {
-            pivpos[row] = (int16_t)before;
-            sortedSlot[before] = slotOf[row];
-            info[1 + before] = row;
-            ++before;
+    before += __popc(bal & ((1u << lane) - 1));
+    if (y < alpha) {
+        if (isp) {
+            pivpos[y] = (int16_t)before;
+            sortedSlot[before] = slotOf[y];
+            info[1 + before] = y;
         } else {
-            pivpos[row] = (int16_t)(row - before);
+            pivpos[y] = (int16_t)(y - before);
         }
     }
-    if (tid == 0) {
+    if (y == 0) {
         info[0] = r;
         int j = 0, l = 0;
         for (int c = 0; c < beta; ++c) {
@@ -487,10 +451,10 @@ __global__ void __launch_bounds__(256, 1) k_ech_leaf_gf2(int alpha, int beta, co
             else nonCol[j++] = (int16_t)c;
         }
     }
-    for (int l = tid; l < r; l += NT) info[1 + 64 * W + l] = slotCol[l];
+    if (y < r) info[1 + 64 * W + y] = slotCol[y];
     __syncthreads();
     // outputs: one row per warp, lanes along the columns (coalesced)
-    for (int l = warp; l < r; l += NW) {
+    for (int l = warp; l < r; l += 32) {
         const uint64_t *tl = tw + slotRow[l] * W;
         for (int s = lane; s < r; s += 32) {
             const int q = sortedSlot[s];
@@ -498,7 +462,7 @@ __global__ void __launch_bounds__(256, 1) k_ech_leaf_gf2(int alpha, int beta, co
         }
     }
     if (r > 0) {
-        for (int row = warp; row < alpha; row += NW) {
+        for (int row = warp; row < alpha; row += 32) {
             if (piv[row]) continue;
             const uint64_t *tr = tw + row * W;
             T *ko = Ko + (int64_t)pivpos[row] * ldk;
@@ -509,7 +473,7 @@ __global__ void __launch_bounds__(256, 1) k_ech_leaf_gf2(int alpha, int beta, co
         }
     }
     const int nr = beta - r;
-    for (int l = warp; l < r; l += NW) {
+    for (int l = warp; l < r; l += 32) {
         const uint64_t *hl = hw + slotRow[l] * W;
         for (int j = lane; j < nr; j += 32) {
             const int c = nonCol[j];
@@ -524,43 +488,39 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
               int32_t *info, void *M, int64_t ldm, void *K, int64_t ldk, void *R, int64_t ldr) {
     if (L.p == 2) {
         const int smem = 2 * 1024 * 4 * 8;
-        static bool attr[2] = {false, false};
+        static std::once_flag once[2];
         cudaEvent_t ev;
         prof_begin(L, K_ECH, &ev);
         if (L.codec == CODEC_F8) {
-            if (!attr[0]) {
+            std::call_once(once[0], [&] {
                 cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-                attr[0] = true;
-            }
-            k_ech_leaf_gf2<4, uint8_t><<<1, 256, smem, L.st>>>((int)alpha, (int)beta, (const uint8_t *)H, ldh, info,
+            });
+            k_ech_leaf_gf2<4, uint8_t><<<1, 1024, smem, L.st>>>((int)alpha, (int)beta, (const uint8_t *)H, ldh, info,
                 (uint8_t *)M, ldm, (uint8_t *)K, ldk, (uint8_t *)R, ldr, (uint8_t)0x38);
         } else {
-            if (!attr[1]) {
+            std::call_once(once[1], [&] {
                 cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-                attr[1] = true;
-            }
-            k_ech_leaf_gf2<4, uint16_t><<<1, 256, smem, L.st>>>((int)alpha, (int)beta, (const uint16_t *)H, ldh,
+            });
+            k_ech_leaf_gf2<4, uint16_t><<<1, 1024, smem, L.st>>>((int)alpha, (int)beta, (const uint16_t *)H, ldh,
                 info, (uint16_t *)M, ldm, (uint16_t *)K, ldk, (uint16_t *)R, ldr, (uint16_t)0x3F80);
         }
         prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta));
         return;
     }
     const int smem = 2 * 1024 * LS;
-    static bool attr_set[2] = {false, false};
+    static std::once_flag once2[2];
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
     if (L.codec == CODEC_F8) {
-        if (!attr_set[0]) {
+        std::call_once(once2[0], [&] {
             cudaFuncSetAttribute(k_ech_leaf<CODEC_F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            attr_set[0] = true;
-        }
+        });
         k_ech_leaf<CODEC_F8><<<1, 1024, smem, L.st>>>(L.p, (int)alpha, (int)beta,
             (const uint8_t *)H, ldh, info, (uint8_t *)M, ldm, (uint8_t *)K, ldk, (uint8_t *)R, ldr);
     } else {
-        if (!attr_set[1]) {
+        std::call_once(once2[1], [&] {
             cudaFuncSetAttribute(k_ech_leaf<CODEC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            attr_set[1] = true;
-        }
+        });
         k_ech_leaf<CODEC_BF16><<<1, 1024, smem, L.st>>>(L.p, (int)alpha, (int)beta,
             (const uint16_t *)H, ldh, info, (uint16_t *)M, ldm, (uint16_t *)K, ldk, (uint16_t *)R, ldr);
     }

@@ -53,6 +53,7 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_size_t)]),
     "gfe_batch_echelon": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), _i32, ctypes.c_uint32,
                                  _vp, ctypes.c_size_t, _vp]),
+    "gfe_set_batch_workers": (_i32, [_i32]),
     "gfe_mad_workspace": (ctypes.c_size_t, [_i32, _i64, _i64, _i64]),
     "gfe_mad": (_i32, [_i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_uint32,
                        _vp, ctypes.c_size_t, _vp]),
@@ -201,6 +202,69 @@ def echelon(A: torch.Tensor, p: int, n: int | None = None, transform: bool = Tru
     if dense_T:
         d["T"] = T[:m]
     return d
+
+
+def _alloc_result(mat: GfeMatrix, dev, transform: bool):
+    m, nn = mat.m, mat.n
+    mn = min(m, nn)
+    bits = mat.fmt == GFE_BITS64
+
+    def out(rows, cols):
+        if bits:
+            return torch.zeros((max(rows, 1), words_per_row(max(cols, 1))), dtype=torch.int64, device=dev)
+        return torch.zeros((max(rows, 1), max(cols, 1)), dtype=torch.uint8, device=dev)
+
+    bufs = dict(rank=torch.zeros(1, dtype=torch.int64, device=dev),
+                ups=torch.zeros(max(mn, 1), dtype=torch.int64, device=dev),
+                rho=torch.zeros(max(mn, 1), dtype=torch.int64, device=dev), R=out(mn, nn))
+    if transform:
+        bufs["M"] = out(mn, mn)
+        bufs["K"] = out(m, mn)
+    es = 8 if bits else 1
+
+    def ld(t):
+        return 0 if t is None else t.stride(0) * es
+
+    res = GfeResult(bufs["rank"].data_ptr(), bufs["ups"].data_ptr(), bufs["rho"].data_ptr(), _ptr(bufs["R"]),
+                    ld(bufs["R"]), _ptr(bufs.get("M")), ld(bufs.get("M")), _ptr(bufs.get("K")), ld(bufs.get("K")),
+                    None, 0, None, 0)
+    return bufs, res
+
+
+def _cut_result(mat: GfeMatrix, bufs: dict, r: int) -> dict:
+    m, nn = mat.m, mat.n
+    bits = mat.fmt == GFE_BITS64
+
+    def cut(t, rows, cols):
+        if bits:
+            return t[:rows, :words_per_row(cols)] if rows else t[:0]
+        return t[:rows, :cols]
+
+    d = dict(rank=r, ups=bufs["ups"][:r], rho=bufs["rho"][:r], R=cut(bufs["R"], r, nn - r))
+    if "M" in bufs:
+        d["M"] = cut(bufs["M"], r, r)
+        d["K"] = cut(bufs["K"], m - r, r)
+    return d
+
+
+def batch_echelon(mats, transform: bool = True, impl: str = "tensor", workers: int | None = None, stream=None):
+    """gfe_batch_echelon over a list of (A, p) or (A, p, n) tuples; returns a list of dicts."""
+    args = [matrix_arg(*mt) if len(mt) == 3 else matrix_arg(mt[0], mt[1]) for mt in mats]
+    if not args:
+        return []
+    dev = mats[0][0].device
+    flags = (WANT_TRANSFORM if transform else 0) | _impl_flag(impl)
+    if workers is not None:
+        _check(lib().gfe_set_batch_workers(workers))
+    arr = (GfeMatrix * len(args))(*args)
+    allocs = [_alloc_result(a, dev, transform) for a in args]
+    ress = (GfeResult * len(args))(*[r for _, r in allocs])
+    need = ctypes.c_size_t(0)
+    _check(lib().gfe_query_batch_workspace(arr, len(args), flags, ctypes.byref(need)))
+    ws = _workspace(need.value, dev)
+    _check(lib().gfe_batch_echelon(arr, ress, len(args), flags, ws.data_ptr(), ws.numel(), _stream(stream)))
+    ranks = torch.stack([b["rank"] for b, _ in allocs]).cpu().tolist()
+    return [_cut_result(a, b, int(r[0])) for a, (b, _), r in zip(args, allocs, ranks)]
 
 
 def rank(A: torch.Tensor, p: int, n: int | None = None, impl: str = "tensor", stream=None) -> dict:
