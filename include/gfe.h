@@ -25,7 +25,7 @@
  * Memory: every pointer in this header is DEVICE memory unless stated
  * otherwise.  Inputs are never modified.  Outputs and the workspace are
  * owned by the caller; the library keeps no pointer after a call returns
- * except inside a gfe_server (see there).  Calls are asynchronous on the
+ * except for the requests of a gfe_server (see there).  Calls are asynchronous on the
  * given CUDA stream (a cudaStream_t passed as void*; NULL = legacy default
  * stream) EXCEPT that gfe_echelon / gfe_rank synchronise that stream
  * internally once per block echelonisation (the host plans the data-dependent
@@ -132,6 +132,35 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
                              uint32_t flags, void *ws, size_t ws_bytes, void *stream);
 /* number of concurrent workers of gfe_batch_echelon (<= 0: default 8) */
 gfe_status gfe_set_batch_workers(int32_t workers);
+
+/*
+ * Serving form: requests arrive one matrix at a time and are echelonised
+ * concurrently by `workers` host workers with their own CUDA streams.  The
+ * server owns one device arena of hbm_cap_bytes (its HBM admission cap); a
+ * request is admitted when a worker is free and its workspace
+ * (gfe_query_workspace) fits in the arena, and any queued request that fits
+ * may go first, so requests that arrive while others run join as slots and
+ * memory free up and their work overlaps on the GPU.  The result is that of
+ * gfe_echelon on the same matrix (the paper's computation, Section 3).
+ *   gfe_submit: A and out as for gfe_echelon; both must stay valid and
+ *     untouched until the request is done.  The request is ordered after the
+ *     work queued on `stream` before the call.  A request whose workspace
+ *     exceeds the cap fails with GFE_ENOMEM.
+ *   gfe_poll: GFE_EBUSY while pending, else GFE_OK with the request's status.
+ *   gfe_wait: blocks up to timeout_us (< 0: forever); GFE_ETIMEOUT if still
+ *     pending.  When a request is done its outputs are complete on the device.
+ *   gfe_server_latency: submit-to-done time of a finished request in
+ *     microseconds (host clock); release != 0 forgets the ticket.
+ *   gfe_server_destroy: finishes every queued request, then frees the arena.
+ */
+typedef struct gfe_server gfe_server;
+gfe_status gfe_server_create(gfe_server **server, size_t hbm_cap_bytes, int32_t workers, int32_t device);
+gfe_status gfe_submit(gfe_server *server, const gfe_matrix *A, const gfe_result *out, uint32_t flags,
+                      void *stream, uint64_t *ticket);
+gfe_status gfe_poll(gfe_server *server, uint64_t ticket, gfe_status *done_status);
+gfe_status gfe_wait(gfe_server *server, uint64_t ticket, int64_t timeout_us, gfe_status *done_status);
+gfe_status gfe_server_latency(gfe_server *server, uint64_t ticket, double *us, int32_t release);
+gfe_status gfe_server_destroy(gfe_server *server);
 
 /*
  * gfe_mad -- the job MAD (Section 4.1): C := W + A B over GF(p), A m x k,

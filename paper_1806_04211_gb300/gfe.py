@@ -54,6 +54,13 @@ SIGNATURES = {
     "gfe_batch_echelon": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), _i32, ctypes.c_uint32,
                                  _vp, ctypes.c_size_t, _vp]),
     "gfe_set_batch_workers": (_i32, [_i32]),
+    "gfe_server_create": (_i32, [ctypes.POINTER(_vp), ctypes.c_size_t, _i32, _i32]),
+    "gfe_submit": (_i32, [_vp, ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), ctypes.c_uint32, _vp,
+                          ctypes.POINTER(ctypes.c_uint64)]),
+    "gfe_poll": (_i32, [_vp, ctypes.c_uint64, ctypes.POINTER(_i32)]),
+    "gfe_wait": (_i32, [_vp, ctypes.c_uint64, _i64, ctypes.POINTER(_i32)]),
+    "gfe_server_latency": (_i32, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double), _i32]),
+    "gfe_server_destroy": (_i32, [_vp]),
     "gfe_mad_workspace": (ctypes.c_size_t, [_i32, _i64, _i64, _i64]),
     "gfe_mad": (_i32, [_i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_uint32,
                        _vp, ctypes.c_size_t, _vp]),
@@ -329,3 +336,56 @@ def profile_read(reset: bool = True) -> dict:
                 madds={k: pr.madds[i] for i, k in enumerate(KINDS)},
                 timed={k: pr.timed[i] for i, k in enumerate(KINDS)},
                 host_syncs=pr.host_syncs)
+
+
+class Server:
+    """gfe_server: continuous-batching echelonisation service (C ABI)."""
+
+    def __init__(self, hbm_cap_bytes: int, workers: int = 8, device: int = 0):
+        self._h = _vp()
+        _check(lib().gfe_server_create(ctypes.byref(self._h), hbm_cap_bytes, workers, device))
+        self._pending = {}
+
+    def submit(self, A: torch.Tensor, p: int, n: int | None = None, transform: bool = True, impl: str = "tensor",
+               stream=None) -> int:
+        mat = matrix_arg(A, p, n)
+        bufs, res = _alloc_result(mat, A.device, transform)
+        flags = (WANT_TRANSFORM if transform else 0) | _impl_flag(impl)
+        t = ctypes.c_uint64(0)
+        _check(lib().gfe_submit(self._h, ctypes.byref(mat), ctypes.byref(res), flags, _stream(stream),
+                                ctypes.byref(t)))
+        self._pending[t.value] = (A, mat, bufs, res)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        st = _i32(0)
+        rc = lib().gfe_poll(self._h, ticket, ctypes.byref(st))
+        if rc == 4:
+            return False
+        _check(rc)
+        _check(st.value)
+        return True
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> dict:
+        """Result of a request (and its submit-to-done latency in us)."""
+        st = _i32(0)
+        _check(lib().gfe_wait(self._h, ticket, timeout_us, ctypes.byref(st)))
+        _check(st.value)
+        us = ctypes.c_double(0)
+        _check(lib().gfe_server_latency(self._h, ticket, ctypes.byref(us), 1))
+        A, mat, bufs, res = self._pending.pop(ticket)
+        d = _cut_result(mat, bufs, int(bufs["rank"].item()))
+        d["latency_us"] = us.value
+        return d
+
+    def close(self):
+        if self._h:
+            _check(lib().gfe_server_destroy(self._h))
+            self._h = _vp()
+            self._pending.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
