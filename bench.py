@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain CUDA-core comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched (C4) and served (C5) legs")
+    ap.add_argument("--c4", type=int, default=512, help="matrices of the batched leg")
+    ap.add_argument("--c5", type=int, default=120, help="measured requests of the serving leg")
     return ap.parse_args()
 
 
@@ -196,6 +199,128 @@ def cpu_baseline(n):
                       % (ns, ns, dt)}
 
 
+PRIMES = [q for q in range(2, 252) if all(q % d for d in range(2, int(q ** 0.5) + 1))]
+
+
+def c4_matrices(count, seed=1):
+    """Batched workload (C4): m, n log-uniform in [64, 2048] with aspect ratio
+    <= 4, p uniform in {2, 3, 5, 7}, half of them of rank 0.6 * min(m, n)."""
+    import numpy as np
+    rng = np.random.RandomState(seed)
+    out = []
+    while len(out) < count:
+        m, n = (int(round(64 * 32 ** rng.rand())) for _ in range(2))
+        if max(m, n) > 4 * min(m, n):
+            continue
+        p = [2, 3, 5, 7][rng.randint(4)]
+        rk = int(0.6 * min(m, n)) if len(out) % 2 else None
+        out.append((p, m, n, rk))
+    return out
+
+
+def c5_requests(count, seed=1):
+    """Served workload (C5): square n ~ Pareto(1.5) on [256, 16384] (rejection),
+    p uniform over the primes <= 251, 30% of rank 0.6 n."""
+    import numpy as np
+    rng = np.random.RandomState(seed)
+    out = []
+    while len(out) < count:
+        n = 256 * (1 - rng.rand()) ** (-1 / 1.5)
+        if n > 16384:
+            continue
+        n = int(n)
+        p = PRIMES[rng.randint(len(PRIMES))]
+        rk = int(0.6 * n) if rng.rand() < 0.3 else None
+        out.append((p, n, rk))
+    return out
+
+
+def bench_batched(dev, count):
+    """C4 sample: one gfe_batch_echelon call vs the plain per-matrix path."""
+    import torch
+    from paper_1806_04211_gb300 import gfe, synth
+    specs = c4_matrices(count)
+    mats = [(synth.matrix(p, m, n, seed=5000 + i, rank=rk, device=dev), p, n) for i, (p, m, n, rk) in enumerate(specs)]
+    units = float(sum(m * n * min(m, n) for p, m, n, rk in specs))
+    gfe.batch_echelon(mats[:16])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    res = gfe.batch_echelon(mats, workers=16)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t
+    madds = float(sum(m * n * d["rank"] for (p, m, n, rk), d in zip(specs, res)))
+    t = time.perf_counter()
+    for A, p, n in mats:
+        gfe.echelon(A, p, n=n, impl="plain")
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t
+    return {"matrices": count, "of": 4096, "batched_matrices_per_s": count / tb, "plain_matrices_per_s": count / tp,
+            "speedup": tp / tb, "batched_madds_per_s": madds / tb, "workers": 16,
+            "sample": "first %d of the seeded C4 draw (sum m*n*min(m,n) = %.3g)" % (count, units)}
+
+
+def bench_serving(dev, warm, count, cap=120 << 30):
+    """C5: Poisson arrivals at 0.5x and 0.8x the saturated rate; latency =
+    submit to result ready (host clock).  Baseline: the same trace served one
+    request at a time by the plain path (service times measured, queue replayed)."""
+    import numpy as np
+    import torch
+    from paper_1806_04211_gb300 import gfe, synth
+    reqs = c5_requests(warm + count)
+    mats = [(synth.matrix(p, n, n, seed=7000 + i, rank=rk, device=dev), p, n) for i, (p, n, rk) in enumerate(reqs)]
+    torch.cuda.synchronize()
+
+    def serve(rate, order):
+        rng = np.random.RandomState(3)
+        lat, t0 = [], time.perf_counter()
+        with gfe.Server(cap, workers=12) as srv:
+            tickets, nxt = [], t0
+            for i in order:
+                A, p, n = mats[i]
+                now = time.perf_counter()
+                if rate and nxt > now:
+                    time.sleep(nxt - now)
+                tickets.append(srv.submit(A, p, n if p == 2 else None))
+                nxt += rng.exponential(1.0 / rate) if rate else 0.0
+            for t in tickets:
+                lat.append(srv.wait(t)["latency_us"] / 1e3)
+        return lat, time.perf_counter() - t0
+
+    serve(0, range(warm))                                    # warm-up requests
+    meas = list(range(warm, warm + count))
+    _, tsat = serve(0, meas)                                 # saturated: all at once
+    sat = count / tsat
+    out = {"requests": count, "warmup_requests": warm, "saturated_matrices_per_s": sat, "hbm_cap_gb": cap >> 30,
+           "workers": 12}
+    for frac in (0.5, 0.8):
+        lat, tt = serve(frac * sat, meas)
+        out["at_%.1fx" % frac] = {"rate": frac * sat, "matrices_per_s": count / tt,
+                                  "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    # serial plain baseline: service times, then the same arrival trace replayed
+    svc = []
+    for i in meas:
+        A, p, n = mats[i]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        gfe.echelon(A, p, n=n if p == 2 else None, impl="plain")
+        torch.cuda.synchronize()
+        svc.append(time.perf_counter() - t)
+    for frac in (0.5, 0.8):
+        rng = np.random.RandomState(3)
+        rate = frac * sat
+        arr, tcur, lat = 0.0, 0.0, []
+        for k, sv in enumerate(svc):
+            start = max(arr, tcur)
+            tcur = start + sv
+            lat.append((tcur - arr) * 1e3)
+            arr += rng.exponential(1.0 / rate)
+        out["plain_serial_at_%.1fx" % frac] = {"p50_ms": float(np.percentile(lat, 50)),
+                                               "p99_ms": float(np.percentile(lat, 99)),
+                                               "matrices_per_s": count / max(tcur, arr)}
+    out["plain_serial_saturated_matrices_per_s"] = count / sum(svc)
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -328,6 +453,10 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.n)
+    batched = served = None
+    if rank == 0 and not args.no_forms:
+        batched = bench_batched(dev, args.c4)
+        served = bench_serving(dev, 24, args.c5)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "mul-adds/s", "n_gpus": ws, "steps": args.steps,
@@ -341,6 +470,8 @@ def main():
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_units / (e2e_ms * 1e-3), "unit": "mul-adds/s",
                         "h2d_bytes_per_step": h2d // max(args.steps, 1), "d2h_bytes_per_step": d2h // max(args.steps, 1)},
+                "batched_C4": batched,
+                "served_C5": served,
                 "clocks": clk,
                 "gpu_launches": launches,
                 "profile": {"ms": prof["ms"], "launches": prof["launches"], "host_syncs": prof["host_syncs"]}}
