@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched (C4) and served (C5) legs")
     ap.add_argument("--c4", type=int, default=512, help="matrices of the batched leg")
     ap.add_argument("--c5", type=int, default=120, help="measured requests of the serving leg")
+    ap.add_argument("--no-c3", action="store_true", help="skip the C3 tensor-vs-plain leg")
     return ap.parse_args()
 
 
@@ -321,6 +322,32 @@ def bench_serving(dev, warm, count, cap=120 << 30):
     return out
 
 
+def bench_c3(dev):
+    """C3: the exact tensor-core form vs the CUDA-core modular form on the same
+    inputs -- 32768^2 over GF(7) and 20000 x 50000 over GF(251), each uniform
+    and a rank-0.6*min twin (one seed each)."""
+    import torch
+    from paper_1806_04211_gb300 import gfe, synth
+    out = {}
+    for p, m, n in [(7, 32768, 32768), (251, 20000, 50000)]:
+        for rk in (None, int(0.6 * min(m, n))):
+            A = synth.matrix(p, m, n, seed=11, rank=rk, device=dev)
+            row = {}
+            for impl in ("tensor", "plain"):
+                gfe.echelon(A, p, impl=impl) if impl == "tensor" else None
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                d = gfe.echelon(A, p, impl=impl)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t
+                row[impl] = {"seconds": dt, "madds_per_s": m * n * d["rank"] / dt}
+            key = "GF(%d) %dx%d %s" % (p, m, n, "uniform" if rk is None else "rank-%d twin" % rk)
+            row["speedup"] = row["plain"]["seconds"] / row["tensor"]["seconds"]
+            out[key] = row
+            del A
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -453,7 +480,9 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.n)
-    batched = served = None
+    batched = served = c3 = None
+    if rank == 0 and not args.no_c3:
+        c3 = bench_c3(dev)
     if rank == 0 and not args.no_forms:
         batched = bench_batched(dev, args.c4)
         served = bench_serving(dev, 24, args.c5)
@@ -470,6 +499,7 @@ def main():
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_units / (e2e_ms * 1e-3), "unit": "mul-adds/s",
                         "h2d_bytes_per_step": h2d // max(args.steps, 1), "d2h_bytes_per_step": d2h // max(args.steps, 1)},
+                "tensor_vs_plain_C3": c3,
                 "batched_C4": batched,
                 "served_C5": served,
                 "clocks": clk,
