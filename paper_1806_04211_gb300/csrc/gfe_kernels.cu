@@ -167,8 +167,64 @@ void mad(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_
 // ---------------------------------------------------------------------------
 constexpr int LS = 68;  // smem row stride (bytes): 17 words -> conflict-free rows
 
-template <int C>
-__global__ void __launch_bounds__(1024, 1) k_ech_leaf(int p, int alpha, int beta,
+// Packed multiply-add mod p on four residues per 32-bit word.
+//  small p (<= 13): a + g*b stays below 256 in every byte, so it is formed
+//   with plain 32-bit arithmetic; the quotient by p comes from a Barrett step
+//   on the even and odd bytes (two 16-bit lanes each), never too large and at
+//   most one too small, fixed by one byte-wise compare (__vcmpgeu4).
+//  larger p: byte by byte through the float reciprocal (exact below 2^16).
+struct PackedMod {
+    uint32_t p, pp;     // p, and p in every byte
+    uint32_t M, S, QM;  // Barrett multiplier, shift, mask of the quotient bits
+    float invp;
+};
+
+template <bool SMALL>
+__device__ __forceinline__ uint32_t pmadd(uint32_t a, uint32_t g, uint32_t b, const PackedMod &q) {
+    if constexpr (SMALL) {
+        const uint32_t x = a + g * b;
+        const uint32_t lo = x & 0x00FF00FFu, hi = (x >> 8) & 0x00FF00FFu;
+        const uint32_t qq = (((lo * q.M) >> q.S) & q.QM) | ((((hi * q.M) >> q.S) & q.QM) << 8);
+        const uint32_t r = x - qq * q.p;
+        return r - (__vcmpgeu4(r, q.pp) & q.pp);
+    } else {
+        uint32_t r = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int x = (int)((a >> (8 * k)) & 0xFF) + (int)g * (int)((b >> (8 * k)) & 0xFF);
+            r |= (uint32_t)modp16(x, (int)q.p, q.invp) << (8 * k);
+        }
+        return r;
+    }
+}
+
+// register-resident packed rows: word w of a 16-word array, static indices
+#define GFE_CASE16(M)                                                                                     \
+    M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15)
+#define GFE_RCASE16(M)                                                                                    \
+    M(15) M(14) M(13) M(12) M(11) M(10) M(9) M(8) M(7) M(6) M(5) M(4) M(3) M(2) M(1) M(0)
+
+__device__ __forceinline__ uint32_t pick16(const uint32_t (&a)[16], int i) {
+    uint32_t v = a[0];
+#pragma unroll
+    for (int w = 1; w < 16; ++w)
+        if (i == w) v = a[w];
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// leaf echelonisation (job ECH, Remark "echelon") of H over GF(p), p > 2:
+// alpha <= 1024 rows, beta <= 64 columns, one CTA of 1024 threads, thread y
+// owns row y (64 residues + 64 slot coefficients packed in 32 registers).
+// Column-by-column Gauss-Jordan; the pivot of column c is the topmost
+// non-pivot row with a non-zero entry there, which yields the row rank
+// profile and the column rank profile, i.e. the unique result of Eq. (gauss).
+// Slot t = the t-th pivot found (= the t-th pivot column).  Every warp
+// publishes its first candidate row before the column's one barrier; rows
+// add g = v*s times the published (unscaled) pivot row, s = -1/pivot.
+// ---------------------------------------------------------------------------
+template <int C, bool SMALL>
+__global__ void __launch_bounds__(1024, 1) k_ech_leaf(PackedMod pm, int alpha, int beta,
                                                       const typename Cd<C>::T *H, int64_t ldh,
                                                       int32_t *info, typename Cd<C>::T *Mo,
                                                       int64_t ldm, typename Cd<C>::T *Ko,
@@ -176,17 +232,18 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(int p, int alpha, int beta
                                                       int64_t ldr) {
     using D = Cd<C>;
     extern __shared__ uint8_t sm[];
-    uint8_t *S = sm;                           // [1024][LS]  residues of H
-    uint8_t *Tt = sm + 1024 * LS;              // [1024][LS]  slot coefficients
+    uint8_t *S = sm;                           // [1024][LS]  residues of H (load / output)
+    uint8_t *Tt = sm + 1024 * LS;              // [1024][LS]  slot coefficients (output)
     __shared__ uint8_t inv[256];
     __shared__ uint8_t piv[1024];
     __shared__ int16_t slotOf[1024];
-    __shared__ int16_t pivpos[1024];           // rank among pivot / non-pivot rows
+    __shared__ int16_t pivpos[1024];
     __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
-    __shared__ int best[3];
+    __shared__ uint32_t wbuf[2][32][32];
+    __shared__ int wmin[2][32];
     __shared__ int wsum[32];
     const int y = threadIdx.x, lane = y & 31, warp = y >> 5;
-    const float invp = 1.0f / (float)p;
+    const int p = (int)pm.p;
 
     if (y < p) {
         int v = 0;
@@ -194,69 +251,111 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(int p, int alpha, int beta
             if ((y * x) % p == 1) v = x;
         inv[y] = (uint8_t)v;
     }
-    if (y < 3) best[y] = INT_MAX;
     piv[y] = 0;
     slotOf[y] = -1;
     // coalesced load: warp w reads its 32 rows, lane l columns l and l + 32
     for (int rr = 0; rr < 32; ++rr) {
         const int row = warp * 32 + rr;
-        if (row >= alpha) break;
         const typename D::T *hr = H + (int64_t)row * ldh;
-        S[row * LS + lane] = lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
-        S[row * LS + 32 + lane] = 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
-        Tt[row * LS + lane] = 0;
-        Tt[row * LS + 32 + lane] = 0;
+        const bool in = row < alpha;
+        S[row * LS + lane] = in && lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
+        S[row * LS + 32 + lane] = in && 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
     }
+    __syncthreads();
+    uint32_t h[16], t[16];
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        h[w] = *(const uint32_t *)(S + y * LS + 4 * w);
+        t[w] = 0;
+    }
+    bool isp = false;
     __syncthreads();
 
     int ns = 0;
     for (int c = 0; c < beta; ++c) {
-        // three rotating slots: the one reset here was last read two columns
-        // ago, before the barrier every thread has since passed
-        if (y == 0) best[(c + 1) % 3] = INT_MAX;
-        int cand = (y < alpha) && !piv[y] && S[y * LS + c] != 0;
-        unsigned bal = __ballot_sync(0xffffffffu, cand);
-        if (lane == 0 && bal) atomicMin(&best[c % 3], warp * 32 + __ffs(bal) - 1);
-        __syncthreads();
-        const int x = best[c % 3];
-        if (x == INT_MAX) continue;  // uniform: column c has no pivot
-        if (y == x) {
-            int s = p - inv[S[x * LS + c]];  // scale so that the pivot becomes -1
-            if (s == p) s = 0;
-            for (int cc = c; cc < beta; ++cc) S[x * LS + cc] = (uint8_t)modp16(S[x * LS + cc] * s, p, invp);
-            Tt[x * LS + ns] = 1;
-            for (int t = 0; t <= ns; ++t) Tt[x * LS + t] = (uint8_t)modp16(Tt[x * LS + t] * s, p, invp);
-            piv[x] = 1;
-            slotOf[x] = (int16_t)ns;
-            slotRow[ns] = (int16_t)x;
-            slotCol[ns] = (int16_t)c;
+        const int b = c & 1, wc = c >> 2, bc = 8 * (c & 3);
+        const uint32_t v = (pick16(h, wc) >> bc) & 0xFF;
+        const bool cand = (y < alpha) && !isp && v != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0) wmin[b][warp] = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
+        if (bal && lane == __ffs(bal) - 1) {
+#pragma unroll
+            for (int w = 0; w < 16; ++w) {
+                wbuf[b][warp][w] = h[w];
+                wbuf[b][warp][16 + w] = t[w];
+            }
         }
         __syncthreads();
-        if (y < alpha && y != x) {
-            int f = S[y * LS + c];
-            if (f) {
-                const uint8_t *px = S + x * LS;
-                uint8_t *py = S + y * LS;
-                for (int cc = c; cc < beta; ++cc) py[cc] = (uint8_t)modp16(py[cc] + f * px[cc], p, invp);
-                const uint8_t *tx = Tt + x * LS;
-                uint8_t *ty = Tt + y * LS;
-                for (int t = 0; t <= ns; ++t) ty[t] = (uint8_t)modp16(ty[t] + f * tx[t], p, invp);
+        const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)wmin[b][lane]);
+        if (x == INT_MAX) continue;  // uniform: column c has no pivot
+        const uint32_t *px = wbuf[b][x >> 5];
+        const uint32_t pv = (px[wc] >> bc) & 0xFF;
+        uint32_t sc = (uint32_t)(p - inv[pv]);  // scale making the pivot -1
+        if (sc == (uint32_t)p) sc = 0;
+        const int nw = ns >> 2, nb = 8 * (ns & 3);
+        if (y == x) {
+            // own identity in slot ns, then the whole row times sc
+#define GFE_SETID(k) \
+    if (nw == k) t[k] |= 1u << nb;
+            GFE_CASE16(GFE_SETID)
+#undef GFE_SETID
+#pragma unroll
+            for (int w = 0; w < 16; ++w) {
+                h[w] = pmadd<SMALL>(0u, sc, h[w], pm);
+                t[w] = pmadd<SMALL>(0u, sc, t[w], pm);
             }
+            isp = true;
+            piv[y] = 1;
+            slotOf[y] = (int16_t)ns;
+            slotRow[ns] = (int16_t)y;
+            slotCol[ns] = (int16_t)c;
+        } else if (v) {
+            const uint32_t g = (uint32_t)modp16((int)(v * sc), p, pm.invp);
+            // H words from wc on (the pivot row is zero left of column c)
+            switch (wc) {
+#define GFE_HUPD(k)   \
+    case k:           \
+        h[k] = pmadd<SMALL>(h[k], g, px[k], pm);  [[fallthrough]];
+                GFE_CASE16(GFE_HUPD)
+#undef GFE_HUPD
+            default:
+                break;
+            }
+            // slot words up to nw (the pivot row's slots beyond ns - 1 are zero)
+            switch (nw) {
+#define GFE_TUPD(k)   \
+    case k:           \
+        t[k] = pmadd<SMALL>(t[k], g, px[16 + k], pm);  [[fallthrough]];
+                GFE_RCASE16(GFE_TUPD)
+#undef GFE_TUPD
+            default:
+                break;
+            }
+            // slot ns (zero so far in this row) gets g: the pivot's own identity
+#define GFE_SETG(k) \
+    if (nw == k) t[k] |= g << nb;
+            GFE_CASE16(GFE_SETG)
+#undef GFE_SETG
         }
         ++ns;
     }
-    __syncthreads();
     const int r = ns;
+    // rows back to shared memory for the (coalesced) output phase
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        *(uint32_t *)(S + y * LS + 4 * w) = h[w];
+        *(uint32_t *)(Tt + y * LS + 4 * w) = t[w];
+    }
     // rank of each row among pivot rows (ascending) and among non-pivot rows
-    int isp = (y < alpha) && piv[y];
-    unsigned bal = __ballot_sync(0xffffffffu, isp);
+    const int isp_i = (y < alpha) && isp;
+    unsigned bal = __ballot_sync(0xffffffffu, isp_i);
     if (lane == 0) wsum[warp] = __popc(bal);
     __syncthreads();
     int before = 0;
     for (int w = 0; w < warp; ++w) before += wsum[w];
     before += __popc(bal & ((1u << lane) - 1));
     if (y < alpha) {
-        if (isp) {
+        if (isp_i) {
             pivpos[y] = (int16_t)before;
             sortedSlot[before] = slotOf[y];
             info[1 + before] = y;
@@ -292,6 +391,26 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(int p, int alpha, int beta
     for (int l = warp; l < r; l += 32)
         for (int j = lane; j < nr; j += 32)
             Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
+}
+
+static PackedMod packed_mod(int p) {
+    PackedMod q;
+    q.p = (uint32_t)p;
+    q.pp = (uint32_t)p * 0x01010101u;
+    q.invp = 1.0f / (float)p;
+    q.M = q.S = q.QM = 0;
+    if (p <= 13) {
+        // largest S with 255 * floor(2^S / p) < 2^16 and 255 / p < 2^(16 - S)
+        for (uint32_t S = 8; S < 16; ++S) {
+            const uint32_t M = (1u << S) / (uint32_t)p;
+            if (255u * M >= 65536u || (255u / (uint32_t)p) >= (1u << (16 - S))) break;
+            q.S = S;
+            q.M = M;
+        }
+        const uint32_t qm = (1u << (16 - q.S)) - 1;
+        q.QM = qm | (qm << 16);
+    }
+    return q;
 }
 
 // ---------------------------------------------------------------------------
@@ -508,22 +627,27 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
         return;
     }
     const int smem = 2 * 1024 * LS;
-    static std::once_flag once2[2];
+    const PackedMod pm = packed_mod(L.p);
+    const bool small = L.p <= 13;
+    static std::once_flag once2[4];
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
+#define GFE_LEAF(CODEC, T, SM, IDX)                                                                              \
+    do {                                                                                                          \
+        std::call_once(once2[IDX], [&] {                                                                          \
+            cudaFuncSetAttribute(k_ech_leaf<CODEC, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);       \
+        });                                                                                                       \
+        k_ech_leaf<CODEC, SM><<<1, 1024, smem, L.st>>>(pm, (int)alpha, (int)beta, (const T *)H, ldh, info,        \
+                                                     (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);                      \
+    } while (0)
     if (L.codec == CODEC_F8) {
-        std::call_once(once2[0], [&] {
-            cudaFuncSetAttribute(k_ech_leaf<CODEC_F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        });
-        k_ech_leaf<CODEC_F8><<<1, 1024, smem, L.st>>>(L.p, (int)alpha, (int)beta,
-            (const uint8_t *)H, ldh, info, (uint8_t *)M, ldm, (uint8_t *)K, ldk, (uint8_t *)R, ldr);
+        if (small) GFE_LEAF(CODEC_F8, uint8_t, true, 0);
+        else GFE_LEAF(CODEC_F8, uint8_t, false, 1);
     } else {
-        std::call_once(once2[1], [&] {
-            cudaFuncSetAttribute(k_ech_leaf<CODEC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        });
-        k_ech_leaf<CODEC_BF16><<<1, 1024, smem, L.st>>>(L.p, (int)alpha, (int)beta,
-            (const uint16_t *)H, ldh, info, (uint16_t *)M, ldm, (uint16_t *)K, ldk, (uint16_t *)R, ldr);
+        if (small) GFE_LEAF(CODEC_BF16, uint16_t, true, 2);
+        else GFE_LEAF(CODEC_BF16, uint16_t, false, 3);
     }
+#undef GFE_LEAF
     prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta));
 }
 
