@@ -105,6 +105,8 @@ struct Ctx {
     Arena ar;
     Stage sg;
     char *pinned = nullptr;  // download area (first 4 KB of the staging buffer)
+    int32_t *info = nullptr;    // device result word of the leaf ECH
+    cudaEvent_t ev = nullptr;   // marks the download of the leaf's result
     bool dry = false;
     int es = 1;
     int64_t syncs = 0;
@@ -117,6 +119,19 @@ struct Ctx {
         check(cudaStreamSynchronize(L.st), "cudaStreamSynchronize");
         check(cudaGetLastError(), "kernel launch");
         sg.top = 0;
+        ++syncs;
+        prof_count_sync();
+        prof_sync_point();
+    }
+    // wait for the work queued before the last record(); later work keeps
+    // running and the upload ring is not recycled here
+    void record() {
+        if (!dry) check(cudaEventRecord(ev, L.st), "cudaEventRecord");
+    }
+    void wait_event() {
+        if (dry) return;
+        check(cudaEventSynchronize(ev), "cudaEventSynchronize");
+        check(cudaGetLastError(), "kernel launch");
         ++syncs;
         prof_count_sync();
         prof_sync_point();
@@ -270,32 +285,48 @@ static void block_policy(int p, int64_t alpha, int64_t beta, std::vector<int64_t
     for (int64_t x = 0; x < beta; x += cb) b.push_back(std::min(cb, beta - x));
 }
 
-void ech(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, const DMat &Ro, EchRes &out) {
+// ech_start queues the ECH; for a leaf the pivot sets are still on their way
+// to the host (ech_finish waits for them), so independent work can be queued
+// in between.  A larger block runs the Chief, which returns complete.
+static void ech_start(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, const DMat &Ro, EchRes &out,
+                      bool &pending) {
     const int64_t alpha = H.rows, beta = H.cols;
+    pending = false;
     out.r = 0;
     out.rho.clear();
     out.gamma.clear();
     if (alpha == 0 || beta == 0) return;
     const int lc = ech_leaf_cols(X.L.p);
     if (alpha <= ECH_LEAF_ROWS && beta <= lc) {
-        size_t mk = X.ar.mark();
-        int32_t *info = (int32_t *)X.ar.alloc(sizeof(int32_t) * (1 + 2 * lc));
         if (!X.dry) {
-            ech_leaf(X.L, alpha, beta, H.ptr, H.ld, info, Mo.ptr, Mo.ld, Ko.ptr, Ko.ld, Ro.ptr, Ro.ld);
-            int32_t *h = (int32_t *)X.pinned;
-            X.check(cudaMemcpyAsync(h, info, sizeof(int32_t) * (1 + 2 * lc), cudaMemcpyDeviceToHost, X.L.st),
+            ech_leaf(X.L, alpha, beta, H.ptr, H.ld, X.info, Mo.ptr, Mo.ld, Ko.ptr, Ko.ld, Ro.ptr, Ro.ld);
+            X.check(cudaMemcpyAsync(X.pinned, X.info, sizeof(int32_t) * (1 + 2 * lc), cudaMemcpyDeviceToHost,
+                                    X.L.st),
                     "download");
-            X.sync();
-            out.r = h[0];
-            out.rho.assign(h + 1, h + 1 + out.r);
-            out.gamma.assign(h + 1 + lc, h + 1 + lc + out.r);
+            X.record();
+            pending = true;
         }
-        X.ar.release(mk);
         return;
     }
     std::vector<int64_t> a, b;
     block_policy(X.L.p, alpha, beta, a, b);
     chief(X, H, a, b, true, true, Mo, Ko, Ro, out);
+}
+
+static void ech_finish(Ctx &X, EchRes &out, bool pending) {
+    if (!pending) return;
+    const int lc = ech_leaf_cols(X.L.p);
+    X.wait_event();
+    const int32_t *h = (const int32_t *)X.pinned;
+    out.r = h[0];
+    out.rho.assign(h + 1, h + 1 + out.r);
+    out.gamma.assign(h + 1 + lc, h + 1 + lc + out.r);
+}
+
+void ech(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, const DMat &Ro, EchRes &out) {
+    bool pending = false;
+    ech_start(X, H, Mo, Ko, Ro, out, pending);
+    ech_finish(X, out, pending);
 }
 
 // ---------------------------------------------------------------------------
@@ -365,6 +396,8 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
             EchRes e;
             std::vector<int32_t> lam;
             DMat AAv = AA;  // A.A (a gathered copy or a view of C_ij)
+            bool ur1_done = false;                // UpdateRow step (1) already queued
+            std::vector<char> urt1_done(i + 1, 0);  // UpdateRowTrafo step (1) already queued
             if (i == 0) {
                 DMat Rd = DR[j];
                 ech(X, Cij, AM, AK, Rd, e);
@@ -389,8 +422,34 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                 }
                 // (MAD) H := A' + A.A x D.R
                 j_mad(X, al, bj - r, r, &Hh, AAv, DR[j], Hh);
-                // (ECH)
-                ech(X, Hh, AM, AK, Rech, e);
+                // (ECH), and meanwhile the steps (1) of UpdateRow and of
+                // UpdateRowTrafo for h < i, which do not depend on its result
+                bool pending = false;
+                ech_start(X, Hh, AM, AK, Rech, e, pending);
+                const int64_t wc0 = beta - co[j + 1];
+                if (wc0 > 0) {
+                    DMat Z0 = sub(X, H, ro[i], co[j + 1], al, wc0);
+                    j_mad(X, al, wc0, r, &Z0, AAv, Bp[j], Z0);   // UpdateRow (1): Z := C + A.A x B
+                    ur1_done = true;
+                }
+                if (trafo) {
+                    for (int h = 0; h < i; ++h) {
+                        const std::vector<int32_t> &del = Edel[h][j];
+                        const int64_t nc = (int64_t)del.size();
+                        bool nonew = true;
+                        for (int32_t dbit : del) nonew = nonew && dbit == 0;
+                        if (j != 0 && !nonew) continue;             // needs CRZ: done after the ECH
+                        DMat Kih = sub(X, Kp[i], 0, ro[h], al, nc);
+                        DMat Mjh = sub(X, Mp[j], 0, ro[h], r, nc);
+                        if (wM[j][h] != nc) {  // M_jh not stored yet: it is zero
+                            j_zero(X, r, nc, Mjh);
+                            wM[j][h] = nc;
+                        }
+                        j_mad(X, al, nc, r, j == 0 ? nullptr : &Kih, AAv, Mjh, Kih);   // UpdateRowTrafo (1)
+                        urt1_done[h] = 1;
+                    }
+                }
+                ech_finish(X, e, pending);
                 const int64_t rp = e.r;
                 if (rp > 0) {
                     // (CEX) A.E = D.R gamma'^tr, R' = D.R gamma'_bar^tr
@@ -417,7 +476,7 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
             const int64_t wc = beta - co[j + 1];
             DMat Z = sub(X, H, ro[i], co[j + 1], al, wc);
             if (wc > 0) {
-                if (i > 0) j_mad(X, al, wc, r, &Z, AAv, Bp[j], Z);          // (1) Z := C + A.A x B
+                if (i > 0 && !ur1_done) j_mad(X, al, wc, r, &Z, AAv, Bp[j], Z);  // (1) Z := C + A.A x B
                 if (rp > 0) {
                     DMat Vv = V, Ww = W, Xx = Xb;
                     j_rows(X, rp, wc, Vv, Z, nullptr, e.rho);               // (2) REX
@@ -459,7 +518,7 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                         DMat Kold = sub(X, Kp[i], 0, ro[h], al, wK[i][h]);
                         j_cols(X, al, nc, Zz, Kold, crz_map(del));
                     }
-                    if (h != i) j_mad(X, al, nc, r, first_j ? nullptr : &Zz, AAv, Mjh, Zz);
+                    if (h != i && !urt1_done[h]) j_mad(X, al, nc, r, first_j ? nullptr : &Zz, AAv, Mjh, Zz);
                     if (rp == 0) {  // nothing pivotal: K := Z, M unchanged
                         if (!inplace) j_copy(X, al, nc, Kih, Zz);
                         wK[i][h] = nc;
@@ -582,12 +641,24 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
         for (int k = b - 1; k >= 0; --k) {
             const int64_t rk = (int64_t)gam[k].size();
             std::vector<int32_t> ngk = complement(gam[k], bcols[k]);
-            for (int j = 0; j < k; ++j) {  // PreClearUp: (X_jk, R_jk) := CEX(B_jk, D_k.gamma)
-                const int64_t rj = (int64_t)gam[j].size();
-                if (rj == 0) continue;
-                DMat Bjk = sub(X, Bp[j], 0, co[k] - co[j + 1], rj, bcols[k]);
-                j_cols(X, rj, rk, sub(X, Xcat, rowoff[j], 0, rj, rk), Bjk, gam[k]);
-                j_cols(X, rj, bcols[k] - rk, sub(X, Rw, rowoff[j], pad[k], rj, bcols[k] - rk), Bjk, ngk);
+            // PreClearUp for every j < k at once: (X_jk, R_jk) := CEX(B_jk, D_k.gamma);
+            // the rows of B_1k .. B_(k-1)k are addressed through a row-pointer list
+            if (rowoff[k] > 0 && !X.dry) {
+                std::vector<int32_t> rp32(2 * rowoff[k]);
+                for (int j = 0; j < k; ++j) {
+                    const int64_t rj = (int64_t)gam[j].size();
+                    for (int64_t l = 0; l < rj; ++l) {
+                        const uint64_t a = (uint64_t)(uintptr_t)X.at(Bp[j], l, co[k] - co[j + 1]);
+                        rp32[2 * (rowoff[j] + l)] = (int32_t)(uint32_t)(a & 0xFFFFFFFFu);
+                        rp32[2 * (rowoff[j] + l) + 1] = (int32_t)(uint32_t)(a >> 32);
+                    }
+                }
+                const uint64_t *rows = (const uint64_t *)X.put(rp32);
+                if (rk > 0) gather_rowptr(X.L, rowoff[k], rk, Xcat.ptr, Xcat.ld, rows, X.put(gam[k]));
+                if (bcols[k] - rk > 0) {
+                    DMat Rjk = sub(X, Rw, 0, pad[k], rowoff[k], bcols[k] - rk);
+                    gather_rowptr(X.L, rowoff[k], bcols[k] - rk, Rjk.ptr, Rjk.ld, rows, X.put(ngk));
+                }
             }
             if (rk == 0 || rowoff[k] == 0) continue;
             // ClearUp for every j < k at once: R_jl += X_jk R_kl (l >= k), M_j += X_jk M_k
@@ -639,6 +710,17 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
         X.sg.host = guard.p + 4096;
     }
     X.sg.dev = (char *)X.ar.alloc(STAGE_BYTES);
+    X.info = (int32_t *)X.ar.alloc(sizeof(int32_t) * (1 + 2 * ECH_LEAF_COLS_GF2));
+    struct EvGuard {
+        cudaEvent_t e = nullptr;
+        ~EvGuard() {
+            if (e) cudaEventDestroy(e);
+        }
+    } evg;
+    if (!dry) {
+        X.check(cudaEventCreateWithFlags(&evg.e, cudaEventDisableTiming), "cudaEventCreate");
+        X.ev = evg.e;
+    }
     std::vector<int64_t> a, b;
     top_blocks(L.p, H.rows, H.cols, a, b);
     EchRes e;

@@ -75,6 +75,10 @@ void gather_rows(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64
 // dst col t = map[t] >= 0 ? src col map[t] : 0
 void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
                  const void *src, int64_t lds, const int32_t *map);
+// dst[t][c] = map[c] >= 0 ? rows[t][map[c]] : 0, rows[] a device array of row
+// start pointers (gathers from several matrices in one launch)
+void gather_rowptr(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
+                   const uint64_t *rows, const int32_t *map);
 // V[t][pos[t]] := 1 for t < count (job ADI)
 void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const int32_t *pos);
 void copy2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,

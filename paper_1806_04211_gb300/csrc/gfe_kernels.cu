@@ -710,6 +710,16 @@ __global__ void k_gather_cols(int64_t nrows, int64_t ncols, T *dst, int64_t ldd,
 }
 
 template <typename T>
+__global__ void k_gather_rowptr(int64_t nrows, int64_t ncols, T *dst, int64_t ldd, const uint64_t *rows,
+                                const int32_t *map) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const int32_t s = map[c];
+    for (int64_t row = blockIdx.y; row < nrows; row += gridDim.y)
+        dst[row * ldd + c] = s >= 0 ? ((const T *)rows[row])[s] : (T)0;
+}
+
+template <typename T>
 __global__ void k_set_ones(int64_t count, T *V, int64_t ldv, const int32_t *pos, T one) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) V[t * ldv + pos[t]] = one;
@@ -768,6 +778,19 @@ void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64
     else
         k_gather_cols<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
             (const uint16_t *)src, lds, map);
+    prof_end(L, K_COLS, ev, 0);
+}
+
+void gather_rowptr(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd, const uint64_t *rows,
+                   const int32_t *map) {
+    if (nrows <= 0 || ncols <= 0) return;
+    dim3 grid(cdiv(ncols, 128), (unsigned)(nrows < 8192 ? nrows : 8192));
+    cudaEvent_t ev;
+    prof_begin(L, K_COLS, &ev);
+    if (L.codec == CODEC_F8)
+        k_gather_rowptr<uint8_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd, rows, map);
+    else
+        k_gather_rowptr<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd, rows, map);
     prof_end(L, K_COLS, ev, 0);
 }
 

@@ -189,3 +189,17 @@ def test_tensor_path_is_taken_in_echelon():
     assert got["rank"] == 2000
     assert prof["launches"]["mad_tensor"] > 0
     assert prof["madds"]["mad_tensor"] > 10 * prof["madds"]["mad_plain"]
+
+
+@pytest.mark.parametrize("p,m,n,rank", [(2, 4200, 3000, None), (2, 2049, 5000, 1500), (3, 2100, 1400, None),
+                                        (251, 2300, 1100, 700), (7, 1100, 2300, None)])
+def test_parity_default_policy_ragged_top_blocks(p, m, n, rank):
+    """Sizes past the default 2048 threshold: 2048-square top-level blocks
+    with ragged last blocks, each ECH a Chief over leaf blocks."""
+    A = synth.matrix(p, m, n, seed=21, rank=rank)
+    if p == 2:
+        ref = O.echelon_gf2(A.numpy(), m, n)
+        compare_gf2(gfe.echelon(A.to(DEV), 2, n=n), ref, m, n)
+    else:
+        ref = O.echelon(A.numpy(), p)
+        compare_u8(A, p, gfe.echelon(A.to(DEV), p), ref)
