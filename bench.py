@@ -174,7 +174,9 @@ def roofline(prof, codec_bytes):
         return {"kernel": "k_mad_tc<%s> (tcgen05)" % ("e4m3" if codec_bytes == 1 else "bf16"), "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "peak_source": "%s bf16 sustained x %.0f" % (src, ratio),
-                "launches": launches, "avg_launch_ms": ms / launches}
+                "launches": launches, "avg_launch_ms": ms / launches,
+                "algorithmic_flops_per_launch": 2.0 * madds / launches,
+                "algorithmic_bytes_per_launch": prof["bytes"][k] / max(prof["launches"][k], 1)}
     # CUDA-core multiply-add: 2 integer ops (IMAD) per multiply-add; peak =
     # 152 SMs x 128 INT32 lanes x max SM clock
     peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 * 2 / 1e12

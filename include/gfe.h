@@ -216,11 +216,23 @@ typedef struct {
                              /*   extract/riffle (CEX, CRZ), 5 copy/zero/ADI,     */
                              /*   6 convert/assemble, 7 other                     */
     double  madds[8];        /* algorithmic multiply-adds done by the MAD kinds  */
+    double  bytes[8];        /* algorithmic bytes of the tensor-core MAD: A, B,  */
+                             /*   W (if any) read and C written once             */
     int64_t timed[8];        /* launches that were timed                         */
     int64_t host_syncs;      /* stream synchronisations made by the planner      */
 } gfe_profile;
 gfe_status gfe_profile_enable(int32_t mask);
 gfe_status gfe_profile_read(gfe_profile *out, int32_t reset);
+
+/*
+ * Failure-detection self-test: a kernel waits, with the bounded wait every
+ * pipeline wait of the library uses, on an mbarrier phase that nothing
+ * completes; after limit_us microseconds it gives up, records the error and
+ * returns normally.  Returns GFE_ETIMEOUT when the wait gave up as designed
+ * (no fault, no hang, the context stays usable).  No counterpart in the
+ * paper.
+ */
+gfe_status gfe_selftest_wait_timeout(int64_t limit_us, void *stream);
 
 const char *gfe_status_str(gfe_status s);
 const char *gfe_last_error(void);

@@ -63,10 +63,11 @@ void prof_begin(const Launch &L, Kind k, cudaEvent_t *ev0) {
     cudaEventRecord(*ev0, L.st);
 }
 
-void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds) {
+void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds, double bytes) {
     if (!g_prof_on) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof.madds[k] += madds;
+    g_prof.bytes[k] += bytes;
     if (!ev0) return;
     cudaEvent_t e1 = ev_get();
     cudaEventRecord(e1, L.st);
@@ -463,6 +464,16 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block) {
     g_block_threshold = threshold > 0 ? threshold : 2048;
     g_block_big = block > 0 ? block : 2048;
     return GFE_OK;
+}
+
+gfe_status gfe_selftest_wait_timeout(int64_t limit_us, void *stream) {
+    if (limit_us < 1 || limit_us > 10000000) return (set_error("limit_us out of range"), GFE_EINVAL);
+    const int gave_up = wait_selftest((cudaStream_t)stream, limit_us);
+    tc_error_flag(true);  // the self-test's error word is not a real failure
+    if (gave_up < 0) return (set_error("self-test could not run"), GFE_ECUDA);
+    if (!cuda_ok(cudaGetLastError(), "self-test launch")) return GFE_ECUDA;
+    if (gave_up == 1) return (set_error("bounded wait gave up as designed"), GFE_ETIMEOUT);
+    return (set_error("the wait completed although nothing arrived"), GFE_EINTERNAL);
 }
 
 gfe_status gfe_profile_enable(int32_t mask) {

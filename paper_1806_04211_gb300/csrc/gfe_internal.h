@@ -41,7 +41,7 @@ struct Launch {  // per-call launch context
 
 // ---- profiling (gfe_api.cu) ----
 void prof_begin(const Launch &L, Kind k, cudaEvent_t *ev0);
-void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds);
+void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds, double bytes = 0);
 void prof_sync_point();
 void prof_count_sync();
 extern bool g_prof_on;
@@ -59,6 +59,7 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
 // error word of the tensor-core kernel (a bounded wait ran out); read + reset
 int tc_error_flag(bool reset);
 int64_t tc_k_chunk(int p);
+int wait_selftest(cudaStream_t st, int64_t limit_us);
 
 // Leaf echelonisation of H (alpha <= ECH_LEAF_ROWS, beta <= ech_leaf_cols(p)).
 // info[0] = r, info[1..] = rho (r), info[1+cap..] = gamma (r), cap = ech_leaf_cols(p).

@@ -405,6 +405,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
 }
 
+// Failure-detection self-test: waits (with the kernel's bounded-wait helper
+// and a caller-given limit) on an mbarrier phase that nothing completes; the
+// wait gives up, the error word is set and the kernel returns normally.
+__global__ void k_wait_selftest(uint64_t limit_ns, int *err, int *gave_up) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = gtimer();
+        bool ok = false;
+        while (!(ok = mbar_test(&bar, 0)) && gtimer() - t0 < limit_ns) {
+        }
+        if (!ok) {
+            atomicExch(err, 1);
+            *gave_up = 1;
+        }
+    }
+}
+
 // ---- host side ----
 // error word of the kernel: one per device (a module-scope device variable,
 // zero at load); its device address is looked up once per device
@@ -510,7 +532,8 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
         else
             k_mad_tc<false><<<grid, TC_THREADS, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C,
                                                                  ldc, err);
-        prof_end(L, K_MAD_TC, ev, (double)m * (double)n * (double)kk);
+        prof_end(L, K_MAD_TC, ev, (double)m * (double)n * (double)kk,
+                 (double)es * ((double)m * kk + (double)kk * n + (Wk ? 2.0 : 1.0) * (double)m * n));
     }
     return true;
 }
@@ -530,4 +553,18 @@ int tc_error_flag(bool reset) {
     return h;
 }
 
+}  // namespace gfe
+
+namespace gfe {
+// launches the self-test on `st`; returns the device flag set by the wait
+int wait_selftest(cudaStream_t st, int64_t limit_us) {
+    int *d = nullptr, h = 0;
+    if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return -1;
+    cudaMemsetAsync(d, 0, 2 * sizeof(int), st);
+    k_wait_selftest<<<1, 32, 0, st>>>((uint64_t)limit_us * 1000ull, d, d + 1);
+    cudaMemcpyAsync(&h, d + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    cudaFree(d);
+    return h;
+}
 }  // namespace gfe

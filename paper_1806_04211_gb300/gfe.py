@@ -37,7 +37,7 @@ class GfeResult(ctypes.Structure):
 
 class GfeProfile(ctypes.Structure):
     _fields_ = [("launches", _i64 * 8), ("ms", ctypes.c_double * 8), ("madds", ctypes.c_double * 8),
-                ("timed", _i64 * 8), ("host_syncs", _i64)]
+                ("bytes", ctypes.c_double * 8), ("timed", _i64 * 8), ("host_syncs", _i64)]
 
 
 KINDS = ["mad_tensor", "mad_plain", "ech_leaf", "rows", "cols", "copy", "convert", "other"]
@@ -70,6 +70,7 @@ SIGNATURES = {
     "gfe_set_block_policy": (_i32, [_i64, _i64]),
     "gfe_profile_enable": (_i32, [_i32]),
     "gfe_profile_read": (_i32, [ctypes.POINTER(GfeProfile), _i32]),
+    "gfe_selftest_wait_timeout": (_i32, [_i64, _vp]),
     "gfe_status_str": (ctypes.c_char_p, [_i32]),
     "gfe_last_error": (ctypes.c_char_p, []),
     "gfe_version": (ctypes.c_char_p, []),
@@ -334,6 +335,7 @@ def profile_read(reset: bool = True) -> dict:
     return dict(launches={k: pr.launches[i] for i, k in enumerate(KINDS)},
                 ms={k: pr.ms[i] for i, k in enumerate(KINDS)},
                 madds={k: pr.madds[i] for i, k in enumerate(KINDS)},
+                bytes={k: pr.bytes[i] for i, k in enumerate(KINDS)},
                 timed={k: pr.timed[i] for i, k in enumerate(KINDS)},
                 host_syncs=pr.host_syncs)
 
