@@ -201,8 +201,11 @@ gfe_status gfe_mad_noalloc(int32_t p, int64_t m, int64_t n, int64_t k,
  * whose larger side exceeds `threshold` is split into square blocks of side
  * `block`; smaller ones into leaf blocks of at most 1024 rows x 64 columns
  * (256 columns for GF(2)), which the one-CTA ECH kernel echelonises.
- * Defaults: 2048, 2048.  Process
- * wide; values <= 0 restore the defaults.  Results never depend on it.
+ * Defaults: 2048, 2048; a value <= 0 selects its default.  GFE_EINVAL
+ * (policy unchanged) unless block <= threshold.  Blocks that are multiples
+ * of 64 keep every operand aligned for the tensor-core path (others fall
+ * back to the plain multiply-add where misaligned).  Process wide.  Results
+ * never depend on it.
  */
 gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);
 
@@ -220,9 +223,31 @@ typedef struct {
                              /*   W (if any) read and C written once             */
     int64_t timed[8];        /* launches that were timed                         */
     int64_t host_syncs;      /* stream synchronisations made by the planner      */
+    double  host_wait_ms;    /* host time spent blocked in them                  */
+    double  host_ms;         /* host time inside the planner (all calls, summed  */
+                             /*   over threads), waits included                  */
 } gfe_profile;
 gfe_status gfe_profile_enable(int32_t mask);
 gfe_status gfe_profile_read(gfe_profile *out, int32_t reset);
+
+/* Launch trace: while the profile is enabled and the trace holds fewer than
+ * `capacity` records, every timed launch also leaves one record: its kind,
+ * its shape (m x n x k for a multiply-add, rows x cols for the others,
+ * k = 0), the CUDA stream it ran on and its start (relative to the first
+ * traced launch) and duration, both from CUDA events.  gfe_trace_enable(0)
+ * stops tracing and drops the records; gfe_trace_read copies up to `cap`
+ * records to `out` (may be NULL with cap 0), sets *count to the number
+ * held, and drops them all if `reset`. */
+typedef struct {
+    int32_t kind;            /* as gfe_profile's index                          */
+    int32_t pad;
+    int64_t m, n, k;
+    uint64_t stream;         /* the cudaStream_t handle, as an integer          */
+    double  start_ms;
+    double  ms;
+} gfe_trace_record;
+gfe_status gfe_trace_enable(int64_t capacity);
+gfe_status gfe_trace_read(gfe_trace_record *out, int64_t cap, int64_t *count, int32_t reset);
 
 /*
  * Failure-detection self-test: a kernel waits, with the bounded wait every

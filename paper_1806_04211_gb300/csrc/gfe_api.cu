@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <thread>
 #include <stdexcept>
@@ -37,10 +39,15 @@ static gfe_profile g_prof;
 struct Pending {
     int kind;
     cudaEvent_t a, b;
-    double madds;
+    int64_t m, n, k;
+    cudaStream_t st;
 };
 static std::vector<Pending> g_pending;
 static std::vector<cudaEvent_t> g_evpool;
+// launch trace: records of timed launches, start times relative to t0
+static int64_t g_trace_cap = 0;
+static std::vector<gfe_trace_record> g_trace;
+static cudaEvent_t g_trace_t0 = nullptr;
 
 static cudaEvent_t ev_get() {
     if (!g_evpool.empty()) {
@@ -59,11 +66,16 @@ void prof_begin(const Launch &L, Kind k, cudaEvent_t *ev0) {
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof.launches[k] += 1;
     if (!(g_prof_mask & (1 << k))) return;
+    if (g_trace_cap > 0 && !g_trace_t0) {  // the first traced launch starts the clock
+        g_trace_t0 = ev_get();
+        cudaEventRecord(g_trace_t0, L.st);
+    }
     *ev0 = ev_get();
     cudaEventRecord(*ev0, L.st);
 }
 
-void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds, double bytes) {
+void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds, double bytes, int64_t m, int64_t n,
+              int64_t kk) {
     if (!g_prof_on) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof.madds[k] += madds;
@@ -71,7 +83,7 @@ void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds, double byt
     if (!ev0) return;
     cudaEvent_t e1 = ev_get();
     cudaEventRecord(e1, L.st);
-    g_pending.push_back({(int)k, ev0, e1, madds});
+    g_pending.push_back({(int)k, ev0, e1, m, n, kk, L.st});
 }
 
 static void resolve_locked() {
@@ -81,6 +93,19 @@ static void resolve_locked() {
         cudaEventElapsedTime(&ms, p.a, p.b);
         g_prof.ms[p.kind] += ms;
         g_prof.timed[p.kind] += 1;
+        if (g_trace_t0 && (int64_t)g_trace.size() < g_trace_cap) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, g_trace_t0, p.a);
+            gfe_trace_record r{};
+            r.kind = p.kind;
+            r.m = p.m;
+            r.n = p.n;
+            r.k = p.k;
+            r.stream = (uint64_t)(uintptr_t)p.st;
+            r.start_ms = t;
+            r.ms = ms;
+            g_trace.push_back(r);
+        }
         g_evpool.push_back(p.a);
         g_evpool.push_back(p.b);
     }
@@ -93,9 +118,15 @@ void prof_sync_point() {
     if (g_pending.size() > 4096) resolve_locked();
 }
 
-void prof_count_sync() {
+void prof_count_sync(double wait_ms) {
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof.host_syncs += 1;
+    g_prof.host_wait_ms += wait_ms;
+}
+
+void prof_host_ms(double ms) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.host_ms += ms;
 }
 
 // ---------------------------------------------------------------------------
@@ -159,7 +190,23 @@ static void launch_for(const gfe_matrix *A, uint32_t flags, void *stream, Launch
     L.impl = (flags & GFE_IMPL_PLAIN) ? 1 : 0;
 }
 
+// The workspace need depends only on the field (its codec and leaf width),
+// the shape, the two flags and the block policy; the planner's dry run that
+// finds it walks the whole block schedule, so its answers are memoised.
+using QueryKey = std::tuple<int, int64_t, int64_t, bool, bool, int64_t, int64_t>;
+static std::mutex g_query_mu;
+static std::map<QueryKey, size_t> g_query_memo;
+
 static gfe_status query(const gfe_matrix *A, bool trafo, bool wantR, size_t *ws) {
+    const QueryKey key{A->p, A->m, A->n, trafo, wantR, g_block_threshold, g_block_big};
+    {
+        std::lock_guard<std::mutex> g(g_query_mu);
+        auto it = g_query_memo.find(key);
+        if (it != g_query_memo.end()) {
+            *ws = it->second;
+            return GFE_OK;
+        }
+    }
     Layout Lo = layout(A, trafo, wantR);
     Launch L;
     launch_for(A, 0, nullptr, L);
@@ -177,6 +224,9 @@ static gfe_status query(const gfe_matrix *A, bool trafo, bool wantR, size_t *ws)
         return GFE_EINTERNAL;
     }
     *ws = al256(peak) + 4096;
+    std::lock_guard<std::mutex> g(g_query_mu);
+    if (g_query_memo.size() >= 4096) g_query_memo.clear();
+    g_query_memo[key] = *ws;
     return GFE_OK;
 }
 
@@ -461,8 +511,12 @@ gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k, const uint8_t *W,
 }
 
 gfe_status gfe_set_block_policy(int64_t threshold, int64_t block) {
-    g_block_threshold = threshold > 0 ? threshold : 2048;
-    g_block_big = block > 0 ? block : 2048;
+    const int64_t t = threshold > 0 ? threshold : 2048, b = block > 0 ? block : 2048;
+    // a block must itself be echelonised from leaves (b <= t), else the
+    // split would recurse without end
+    if (t < b) return (set_error("block policy needs block <= threshold"), GFE_EINVAL);
+    g_block_threshold = t;
+    g_block_big = b;
     return GFE_OK;
 }
 
@@ -489,6 +543,33 @@ gfe_status gfe_profile_read(gfe_profile *out, int32_t reset) {
     resolve_locked();
     *out = g_prof;
     if (reset) std::memset(&g_prof, 0, sizeof g_prof);
+    return GFE_OK;
+}
+
+gfe_status gfe_trace_enable(int64_t capacity) {
+    if (capacity < 0) return (set_error("capacity < 0"), GFE_EINVAL);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    resolve_locked();
+    g_trace.clear();
+    if (g_trace_t0) g_evpool.push_back(g_trace_t0);
+    g_trace_t0 = nullptr;
+    g_trace_cap = capacity;
+    if (capacity) g_trace.reserve((size_t)std::min<int64_t>(capacity, 1 << 20));
+    return GFE_OK;
+}
+
+gfe_status gfe_trace_read(gfe_trace_record *out, int64_t cap, int64_t *count, int32_t reset) {
+    if (!count || cap < 0 || (cap > 0 && !out)) return (set_error("gfe_trace_read: bad arguments"), GFE_EINVAL);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    resolve_locked();
+    *count = (int64_t)g_trace.size();
+    const int64_t c = std::min<int64_t>(cap, *count);
+    if (c) std::memcpy(out, g_trace.data(), (size_t)c * sizeof(gfe_trace_record));
+    if (reset) {
+        g_trace.clear();
+        if (g_trace_t0) g_evpool.push_back(g_trace_t0);
+        g_trace_t0 = nullptr;
+    }
     return GFE_OK;
 }
 

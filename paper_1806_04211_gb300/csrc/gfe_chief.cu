@@ -30,6 +30,7 @@
 #include "gfe_internal.h"
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 #include <stdexcept>
@@ -100,6 +101,40 @@ struct StageGuard {
     ~StageGuard() { stage_release(p); }
 };
 
+// side streams (non-blocking), borrowed per planner run and returned at its
+// end; a stream belongs to the device that was current when it was made
+static std::mutex g_stream_mu;
+static std::vector<std::pair<int, cudaStream_t>> g_stream_free;
+
+static cudaStream_t stream_acquire(int dev) {
+    {
+        std::lock_guard<std::mutex> g(g_stream_mu);
+        for (size_t q = 0; q < g_stream_free.size(); ++q)
+            if (g_stream_free[q].first == dev) {
+                cudaStream_t s = g_stream_free[q].second;
+                g_stream_free.erase(g_stream_free.begin() + q);
+                return s;
+            }
+    }
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    return s;
+}
+
+static void stream_release(int dev, cudaStream_t s) {
+    if (!s) return;
+    std::lock_guard<std::mutex> g(g_stream_mu);
+    g_stream_free.push_back({dev, s});
+}
+
+// What one level of the Chief runs beside its ClearDown chain: a side stream
+// and the events that order the two (see chief()).
+struct Level {
+    cudaStream_t s1 = nullptr;
+    cudaEvent_t start = nullptr, aa = nullptr, cd = nullptr, b = nullptr, e4[2] = {nullptr, nullptr},
+                join = nullptr;
+};
+
 struct Ctx {
     Launch L;
     Arena ar;
@@ -110,17 +145,63 @@ struct Ctx {
     bool dry = false;
     int es = 1;
     int64_t syncs = 0;
+    int dev = 0;
+    cudaStream_t main_st = nullptr;  // the caller's stream
+    int depth = 0;                 // nesting depth of the Chief being planned
+    std::vector<Level> levels;     // per depth, made on first use
+    std::vector<cudaEvent_t> owned_events;
+
+    ~Ctx() {
+        for (auto &lv : levels) stream_release(dev, lv.s1);
+        for (cudaEvent_t e : owned_events) cudaEventDestroy(e);
+    }
+    cudaEvent_t make_event() {
+        cudaEvent_t e = nullptr;
+        check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        owned_events.push_back(e);
+        return e;
+    }
+    Level &level(int d) {
+        while ((int)levels.size() <= d) levels.emplace_back();
+        Level &lv = levels[d];
+        if (!dry && !lv.s1) {
+            lv.s1 = stream_acquire(dev);
+            if (!lv.s1) throw CudaError("cudaStreamCreate failed");
+            lv.start = make_event();
+            lv.aa = make_event();
+            lv.cd = make_event();
+            lv.b = make_event();
+            lv.e4[0] = make_event();
+            lv.e4[1] = make_event();
+            lv.join = make_event();
+        }
+        return lv;
+    }
+    // event ordering between the current stream and another
+    void signal(cudaEvent_t e) {
+        if (!dry) check(cudaEventRecord(e, L.st), "cudaEventRecord");
+    }
+    void await(cudaEvent_t e) {
+        if (!dry) check(cudaStreamWaitEvent(L.st, e, 0), "cudaStreamWaitEvent");
+    }
 
     void check(cudaError_t e, const char *what) {
         if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
     }
+    static double now_ms() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch())
+            .count();
+    }
     void sync() {
         if (dry) return;
-        check(cudaStreamSynchronize(L.st), "cudaStreamSynchronize");
+        const double t0 = now_ms();
+        check(cudaStreamSynchronize(main_st), "cudaStreamSynchronize");
+        for (auto &lv : levels)
+            if (lv.s1) check(cudaStreamSynchronize(lv.s1), "cudaStreamSynchronize");
         check(cudaGetLastError(), "kernel launch");
         sg.top = 0;
         ++syncs;
-        prof_count_sync();
+        prof_count_sync(now_ms() - t0);
         prof_sync_point();
     }
     // wait for the work queued before the last record(); later work keeps
@@ -130,10 +211,11 @@ struct Ctx {
     }
     void wait_event() {
         if (dry) return;
+        const double t0 = now_ms();
         check(cudaEventSynchronize(ev), "cudaEventSynchronize");
         check(cudaGetLastError(), "kernel launch");
         ++syncs;
-        prof_count_sync();
+        prof_count_sync(now_ms() - t0);
         prof_sync_point();
     }
     // upload an index array; returns its device address
@@ -344,6 +426,32 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     const int64_t maxb = *std::max_element(bcols.begin(), bcols.end());
     const int64_t minab = std::min(maxa, maxb);
 
+    // ---- streams ----
+    // The ClearDown chain is the critical path.  It runs on the caller's
+    // stream s0 together with UpdateRow on the near columns (block column
+    // j+1, which the next ClearDown reads).  UpdateRow on the far columns
+    // (j+2 onwards) and all of UpdateRowTrafo run on the side stream s1
+    // meanwhile.  Events order the two:
+    //   aa       s0 -> s1   A.A of step t is ready (UpdateRow (1) may start)
+    //   cd       s0 -> s1   ClearDown of step t is done (A.M, A.K, A.E)
+    //   b        s1 -> s0   step t's far columns are done; step t+1's near
+    //                       columns are among them
+    //   e4[t&1]  s1 -> s0   step t's UpdateRowTrafo is done; A.A, A.M, A.K
+    //                       and A.E are double-buffered by step parity, so
+    //                       ClearDown of step t+2 may then overwrite them
+    //   join     s1 -> s0   end of Step 1
+    // A nested Chief (the ECH of a large block) runs on s0 with a side stream
+    // of its own and joins it before it returns.
+    const cudaStream_t s0 = X.L.st;
+    const Level lv = X.level(X.depth);
+    const cudaStream_t s1 = lv.s1;
+    ++X.depth;
+    auto on = [&](cudaStream_t s) { X.L.st = s; };
+    X.signal(lv.start);
+    on(s1);
+    X.await(lv.start);
+    on(s0);
+
     // ---- buffers ----
     std::vector<int64_t> cur(arows.begin(), arows.end());  // current rows per block row
     std::vector<DMat> Bp(b);
@@ -362,12 +470,19 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     std::vector<std::vector<int32_t>> gam(b);
     for (int j = 0; j < b; ++j) DR[j] = X.mat(maxb, maxb);
     DMat DRsp = X.mat(maxb, maxb);
-    DMat AA = X.mat(maxa, maxb), AM = X.mat(minab, minab), AK = X.mat(maxa, minab), AE = X.mat(maxb, maxb);
+    DMat AA[2], AM[2], AK[2], AE[2];
+    for (int q = 0; q < 2; ++q) {
+        AA[q] = X.mat(maxa, maxb);
+        AM[q] = X.mat(minab, minab);
+        AK[q] = X.mat(maxa, minab);
+        AE[q] = X.mat(maxb, maxb);
+    }
     DMat Hb = X.mat(maxa, maxb), Rech = X.mat(minab, maxb), Rp = X.mat(maxb, maxb);
-    DMat V = X.mat(minab, std::max<int64_t>(bw, 1)), W = X.mat(maxa, std::max<int64_t>(bw, 1));
-    DMat Xb = X.mat(minab, std::max<int64_t>(bw, 1));
+    // UpdateRow scratch, one set per stream: V stacked on W (one REX gather), X
+    DMat VW0 = X.mat(maxa, maxb), X0 = X.mat(minab, maxb);
+    DMat VW1 = X.mat(maxa, bw), X1 = X.mat(minab, bw);
     std::vector<DMat> Kp(a), Mp(b);
-    DMat Msp, Zt, Vt, Wt, Xt, St;
+    DMat Msp, Zt, VWt, Xt, St;
     // stored widths of K_ih / M_jh; -1 = not stored yet (implicitly zero)
     std::vector<std::vector<int64_t>> wK(a, std::vector<int64_t>(a, 0)), wM(b, std::vector<int64_t>(a, -1));
     if (trafo) {
@@ -377,8 +492,7 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
         for (int j = 0; j < b; ++j) Mp[j] = X.mat(bcap, alpha);
         Msp = X.mat(bcap, alpha);
         Zt = X.mat(maxa, maxa);
-        Vt = X.mat(minab, maxa);
-        Wt = X.mat(maxa, maxa);
+        VWt = X.mat(maxa, maxa);
         Xt = X.mat(minab, maxa);
         St = X.mat(std::min(maxb, alpha), maxa);
     }
@@ -387,20 +501,32 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
         Edel(a, std::vector<std::vector<int32_t>>(b));
 
     // ================= Step 1 =================
+    int64_t t = 0;  // step counter; its parity picks the double buffers
     for (int i = 0; i < a; ++i) {
-        for (int j = 0; j < b; ++j) {
+        for (int j = 0; j < b; ++j, ++t) {
+            const int q = (int)(t & 1);
             const int64_t al = cur[i], bj = bcols[j];
             const int64_t r = (int64_t)gam[j].size();
             DMat Cij = sub(X, H, ro[i], co[j], al, bj);
+            const int64_t wc = beta - co[j + 1];                   // UpdateRow panel width
+            const int64_t wn = j + 1 < b ? bcols[j + 1] : 0;       // near columns (s0)
+            const int64_t wf = wc - wn;                            // far columns (s1)
+            DMat Z = sub(X, H, ro[i], co[j + 1], al, wc);
+            bool near_ready = j == 0;  // step t-1's far columns are another row panel
+            auto need_near = [&]() {
+                if (!near_ready) X.await(lv.b);
+                near_ready = true;
+            };
+            if (t >= 2) X.await(lv.e4[q]);  // step t-2 has let go of this parity's buffers
             // ---------- Task ClearDown ----------
             EchRes e;
             std::vector<int32_t> lam;
-            DMat AAv = AA;  // A.A (a gathered copy or a view of C_ij)
-            bool ur1_done = false;                // UpdateRow step (1) already queued
+            DMat AAv = AA[q];  // A.A (a gathered copy or a view of C_ij)
+            bool ur1_done = false;                  // UpdateRow step (1) already queued
             std::vector<char> urt1_done(i + 1, 0);  // UpdateRowTrafo step (1) already queued
             if (i == 0) {
                 DMat Rd = DR[j];
-                ech(X, Cij, AM, AK, Rd, e);
+                ech(X, Cij, AM[q], AK[q], Rd, e);
                 gam[j] = e.gamma;
                 lam.assign(e.r, 1);
             } else {
@@ -410,29 +536,41 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                 // leading columns 0..r-1 both are column ranges of C: use views
                 // (C_ij is dead after ClearDown; ECH may overwrite A' in place).
                 bool prefix = true;
-                for (int64_t t = 0; t < r && prefix; ++t) prefix = g[t] == t;
+                for (int64_t x = 0; x < r && prefix; ++x) prefix = g[x] == x;
                 DMat Hh;
                 if (prefix && tma_ok(X, Cij)) {
                     AAv = sub(X, Cij, 0, 0, al, r);
                     Hh = sub(X, Cij, 0, r, al, bj - r);
                 } else {
-                    j_cols(X, al, r, AA, Cij, g);
+                    j_cols(X, al, r, AA[q], Cij, g);
                     Hh = sub(X, Hb, 0, 0, al, bj - r);
                     j_cols(X, al, bj - r, Hh, Cij, ng);
                 }
+                X.signal(lv.aa);
                 // (MAD) H := A' + A.A x D.R
                 j_mad(X, al, bj - r, r, &Hh, AAv, DR[j], Hh);
                 // (ECH), and meanwhile the steps (1) of UpdateRow and of
                 // UpdateRowTrafo for h < i, which do not depend on its result
                 bool pending = false;
-                ech_start(X, Hh, AM, AK, Rech, e, pending);
-                const int64_t wc0 = beta - co[j + 1];
-                if (wc0 > 0) {
-                    DMat Z0 = sub(X, H, ro[i], co[j + 1], al, wc0);
-                    j_mad(X, al, wc0, r, &Z0, AAv, Bp[j], Z0);   // UpdateRow (1): Z := C + A.A x B
+                ech_start(X, Hh, AM[q], AK[q], Rech, e, pending);
+                if (wc > 0) {  // UpdateRow (1): Z := C + A.A x B
+                    if (wn > 0) {
+                        need_near();
+                        DMat Zn = sub(X, Z, 0, 0, al, wn);
+                        j_mad(X, al, wn, r, &Zn, AAv, Bp[j], Zn);
+                    }
+                    if (wf > 0) {
+                        on(s1);
+                        X.await(lv.aa);
+                        DMat Zf = sub(X, Z, 0, wn, al, wf);
+                        j_mad(X, al, wf, r, &Zf, AAv, sub(X, Bp[j], 0, wn, r, wf), Zf);
+                        on(s0);
+                    }
                     ur1_done = true;
                 }
                 if (trafo) {
+                    on(s1);
+                    X.await(lv.aa);
                     for (int h = 0; h < i; ++h) {
                         const std::vector<int32_t> &del = Edel[h][j];
                         const int64_t nc = (int64_t)del.size();
@@ -448,16 +586,17 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                         j_mad(X, al, nc, r, j == 0 ? nullptr : &Kih, AAv, Mjh, Kih);   // UpdateRowTrafo (1)
                         urt1_done[h] = 1;
                     }
+                    on(s0);
                 }
                 ech_finish(X, e, pending);
                 const int64_t rp = e.r;
                 if (rp > 0) {
                     // (CEX) A.E = D.R gamma'^tr, R' = D.R gamma'_bar^tr
                     std::vector<int32_t> ngp = complement(e.gamma, bj - r);
-                    j_cols(X, r, rp, AE, DR[j], e.gamma);
+                    j_cols(X, r, rp, AE[q], DR[j], e.gamma);
                     j_cols(X, r, bj - r - rp, Rp, DR[j], ngp);
                     // (MAD) R' := R' + A.E x R
-                    j_mad(X, r, bj - r - rp, rp, &Rp, AE, Rech, Rp);
+                    j_mad(X, r, bj - r - rp, rp, &Rp, AE[q], Rech, Rp);
                     // (UNH) and (RRF)
                     std::vector<int32_t> newg;
                     unh(g, e.gamma, bj, newg, lam);
@@ -469,32 +608,48 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                 }
             }
             const int64_t rp = e.r;
+            X.signal(lv.cd);
             // ---------- Task Extend (UN0 / UNH) ----------
             unh(j == 0 ? std::vector<int32_t>() : Erho[i][j - 1], e.rho, arows[i], Erho[i][j], Edel[i][j]);
             std::vector<int32_t> nrho = complement(e.rho, al);
+            std::vector<int32_t> rex(e.rho);  // REX into V (pivot rows) stacked on W (the others)
+            rex.insert(rex.end(), nrho.begin(), nrho.end());
+            const std::vector<int32_t> lmap = riffle_map(lam);
             // ---------- Task UpdateRow for all k > j at once (row panel) ----------
-            const int64_t wc = beta - co[j + 1];
-            DMat Z = sub(X, H, ro[i], co[j + 1], al, wc);
-            if (wc > 0) {
-                if (i > 0 && !ur1_done) j_mad(X, al, wc, r, &Z, AAv, Bp[j], Z);  // (1) Z := C + A.A x B
-                if (rp > 0) {
-                    DMat Vv = V, Ww = W, Xx = Xb;
-                    j_rows(X, rp, wc, Vv, Z, nullptr, e.rho);               // (2) REX
-                    j_rows(X, al - rp, wc, Ww, Z, nullptr, nrho);
-                    if (i > 0) {
-                        j_mad(X, rp, wc, rp, nullptr, AM, Vv, Xx);          // (3) X := A.M x V
-                        j_mad(X, r, wc, rp, &Bp[j], AE, Xx, Bp[j]);         // (4) S := B + A.E x X
-                        j_rows(X, r + rp, wc, Bsp, Bp[j], &Xx, riffle_map(lam));  // (5) RRF
-                        std::swap(Bp[j], Bsp);
-                    } else {
-                        j_mad(X, rp, wc, rp, nullptr, AM, Vv, Bp[j]);       // (3)+(5) B := A.M x V
-                    }
-                    j_mad(X, al - rp, wc, rp, &Ww, AK, Vv, Z);              // (6) C := W + A.K x V
+            // columns [c0, c0 + w) of the panel, scratch VW / Xs of the stream
+            auto update_row = [&](int64_t c0, int64_t w, const DMat &VW, const DMat &Xs) {
+                if (w <= 0) return;
+                DMat Zc = sub(X, Z, 0, c0, al, w);
+                DMat Bc = sub(X, Bp[j], 0, c0, r, w);
+                if (i > 0 && !ur1_done) j_mad(X, al, w, r, &Zc, AAv, Bc, Zc);  // (1) Z := C + A.A x B
+                if (rp == 0) return;
+                DMat Vv = sub(X, VW, 0, 0, rp, w), Ww = sub(X, VW, rp, 0, al - rp, w);
+                j_rows(X, al, w, VW, Zc, nullptr, rex);                 // (2) REX
+                if (i > 0) {
+                    j_mad(X, rp, w, rp, nullptr, AM[q], Vv, Xs);        // (3) X := A.M x V
+                    j_mad(X, r, w, rp, &Bc, AE[q], Xs, Bc);             // (4) S := B + A.E x X
+                    DMat Bs = sub(X, Bsp, 0, c0, r + rp, w);
+                    j_rows(X, r + rp, w, Bs, Bc, &Xs, lmap);            // (5) RRF
+                } else {
+                    j_mad(X, rp, w, rp, nullptr, AM[q], Vv, Bc);        // (3)+(5) B := A.M x V
                 }
+                j_mad(X, al - rp, w, rp, &Ww, AK[q], Vv, Zc);           // (6) C := W + A.K x V
+            };
+            if (wc > 0) {
+                need_near();
+                update_row(0, wn, VW0, X0);
+                on(s1);
+                X.await(lv.cd);
+                update_row(wn, wf, VW1, X1);
+                X.signal(lv.b);
+                on(s0);
+                if (i > 0 && rp > 0) std::swap(Bp[j], Bsp);
             }
             cur[i] = al - rp;
             rB[j] = r + rp;
-            // ---------- Task UpdateRowTrafo for h = 1..i ----------
+            // ---------- Task UpdateRowTrafo for h = 1..i (side stream) ----------
+            on(s1);
+            X.await(lv.cd);
             if (trafo && (rp > 0 || i > 0)) {
                 for (int h = 0; h <= i; ++h) {
                     const std::vector<int32_t> &del = Edel[h][j];
@@ -526,27 +681,26 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                     }
                     DMat Xx = Xt;
                     if (first_j && h == i) {
-                        j_copy(X, rp, nc, Xx, AM);                        // (3) X := A.M   (V is 1)
-                        j_copy(X, al - rp, nc, Kih, AK);                  // (6) K := A.K   (V is 1, W is 0)
+                        j_copy(X, rp, nc, Xx, AM[q]);                      // (3) X := A.M   (V is 1)
+                        j_copy(X, al - rp, nc, Kih, AK[q]);                // (6) K := A.K   (V is 1, W is 0)
                     } else {
-                        DMat Vv = Vt, Ww = Wt;
-                        j_rows(X, rp, nc, Vv, Zz, nullptr, e.rho);          // (2) REX
-                        j_rows(X, al - rp, nc, Ww, Zz, nullptr, nrho);
-                        if (h == i && !X.dry)                                // (+) ADI
+                        DMat Vv = sub(X, VWt, 0, 0, rp, nc), Ww = sub(X, VWt, rp, 0, al - rp, nc);
+                        j_rows(X, al, nc, VWt, Zz, nullptr, rex);          // (2) REX
+                        if (h == i && !X.dry)                              // (+) ADI
                             set_ones(X.L, rp, Vv.ptr, Vv.ld, X.put(ones_positions(del)));
-                        j_mad(X, rp, nc, rp, nullptr, AM, Vv, Xx);           // (3) X := A.M x V
-                        j_mad(X, al - rp, nc, rp, &Ww, AK, Vv, Kih);         // (6) K := W + A.K x V
+                        j_mad(X, rp, nc, rp, nullptr, AM[q], Vv, Xx);      // (3) X := A.M x V
+                        j_mad(X, al - rp, nc, rp, &Ww, AK[q], Vv, Kih);    // (6) K := W + A.K x V
                     }
                     wK[i][h] = nc;
                     // (4) S and (5) M := RRF(lambda, S, X)
                     DMat Mn = sub(X, Msp, 0, ro[h], r + rp, nc);
                     if (h != i) {
-                        j_mad(X, r, nc, rp, &Mjh, AE, Xx, Mjh);
-                        j_rows(X, r + rp, nc, Mn, Mjh, &Xx, riffle_map(lam));
+                        j_mad(X, r, nc, rp, &Mjh, AE[q], Xx, Mjh);
+                        j_rows(X, r + rp, nc, Mn, Mjh, &Xx, lmap);
                     } else if (i != 0) {
                         DMat Ss = St;
-                        j_mad(X, r, nc, rp, nullptr, AE, Xx, Ss);
-                        j_rows(X, r + rp, nc, Mn, Ss, &Xx, riffle_map(lam));
+                        j_mad(X, r, nc, rp, nullptr, AE[q], Xx, Ss);
+                        j_rows(X, r + rp, nc, Mn, Ss, &Xx, lmap);
                     } else {
                         j_copy(X, rp, nc, Mn, Xx);
                     }
@@ -554,8 +708,15 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                 }
                 if (rp > 0) std::swap(Mp[j], Msp);
             }
+            X.signal(lv.e4[q]);
+            on(s0);
         }
     }
+    on(s1);
+    X.signal(lv.join);
+    on(s0);
+    X.await(lv.join);
+    --X.depth;
 
     // ---- results: rank, Upsilon, varrho, offsets ----
     int64_t rank = 0;
@@ -701,8 +862,10 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
     X.ar.cap = ws_bytes;
     X.ar.top = base_used;
     X.ar.peak = base_used;
+    X.main_st = L.st;
     StageGuard guard;
     if (!dry) {
+        X.check(cudaGetDevice(&X.dev), "cudaGetDevice");
         guard.p = stage_acquire();
         if (!guard.p) throw CudaError("cudaHostAlloc of the staging buffer failed");
         // layout: [0, 4096) download area, then the upload ring
@@ -724,8 +887,12 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
     std::vector<int64_t> a, b;
     top_blocks(L.p, H.rows, H.cols, a, b);
     EchRes e;
+    const double t0 = Ctx::now_ms();
     if (H.rows > 0 && H.cols > 0) chief(X, H, a, b, trafo, wantR, Mo, Ko, Ro, e);
-    if (!dry) X.sync();
+    if (!dry) {
+        X.sync();
+        if (g_prof_on) prof_host_ms(Ctx::now_ms() - t0);
+    }
     res.r = e.r;
     res.rho = e.rho;
     res.gamma = e.gamma;

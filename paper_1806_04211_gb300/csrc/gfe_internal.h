@@ -41,9 +41,11 @@ struct Launch {  // per-call launch context
 
 // ---- profiling (gfe_api.cu) ----
 void prof_begin(const Launch &L, Kind k, cudaEvent_t *ev0);
-void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds, double bytes = 0);
+void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds, double bytes = 0, int64_t m = 0,
+              int64_t n = 0, int64_t kk = 0);
 void prof_sync_point();
-void prof_count_sync();
+void prof_count_sync(double wait_ms);
+void prof_host_ms(double ms);
 extern bool g_prof_on;
 
 // ---- kernels (gfe_kernels.cu); all asynchronous on L.st ----

@@ -145,7 +145,7 @@ void mad_plain(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, 
             k_mad_plain<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, (int)m, (int)n, (int)kk,
                 (const uint16_t *)Wk, ldwk, (const uint16_t *)Ak, lda, (const uint16_t *)Bk, ldb,
                 (uint16_t *)C, ldc);
-        prof_end(L, K_MAD_PLAIN, ev, (double)m * (double)n * (double)kk);
+        prof_end(L, K_MAD_PLAIN, ev, (double)m * (double)n * (double)kk, 0, m, n, kk);
     }
 }
 
@@ -512,11 +512,13 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         const int first = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
         if (lane == 0) wmin[b][warp] = first;
+        const int nw = ns >> 6;  // slot words beyond nw are zero in every row
         if (bal && lane == __ffs(bal) - 1) {
+            // a candidate row is zero left of column c and in slots >= ns
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                wbuf[b][warp][w] = h[w];
-                wbuf[b][warp][W + w] = t[w];
+                if (w >= cw) wbuf[b][warp][w] = h[w];
+                if (w <= nw) wbuf[b][warp][W + w] = t[w];
             }
         }
         __syncthreads();
@@ -525,7 +527,7 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         const uint64_t *px = wbuf[b][x >> 5];
         const uint64_t own = (uint64_t)1 << (ns & 63);
         if (y == x) {
-            wxor<W>(t, ns >> 6, own);  // own identity in slot ns
+            wxor<W>(t, nw, own);  // own identity in slot ns
             isp = true;
             piv[y] = 1;
             slotOf[y] = (int16_t)ns;
@@ -534,10 +536,10 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         } else if (hit) {
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                h[w] ^= px[w];
-                t[w] ^= px[W + w];
+                if (w >= cw) h[w] ^= px[w];
+                if (w <= nw) t[w] ^= px[W + w];
             }
-            wxor<W>(t, ns >> 6, own);  // the pivot's own identity
+            wxor<W>(t, nw, own);  // the pivot's own identity
         }
         ++ns;
     }
@@ -623,7 +625,7 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
             k_ech_leaf_gf2<4, uint16_t><<<1, 1024, smem, L.st>>>((int)alpha, (int)beta, (const uint16_t *)H, ldh,
                 info, (uint16_t *)M, ldm, (uint16_t *)K, ldk, (uint16_t *)R, ldr, (uint16_t)0x3F80);
         }
-        prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta));
+        prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta), 0, alpha, beta);
         return;
     }
     const int smem = 2 * 1024 * LS;
@@ -648,7 +650,7 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
         else GFE_LEAF(CODEC_BF16, uint16_t, false, 3);
     }
 #undef GFE_LEAF
-    prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta));
+    prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta), 0, alpha, beta);
 }
 
 // ---------------------------------------------------------------------------
@@ -763,7 +765,7 @@ void gather_rows(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64
     else
         k_gather_rows<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
             (const uint16_t *)A, lda, (const uint16_t *)B, ldb, map);
-    prof_end(L, K_ROWS, ev, 0);
+    prof_end(L, K_ROWS, ev, 0, 0, nrows, ncols);
 }
 
 void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
@@ -778,7 +780,7 @@ void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64
     else
         k_gather_cols<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
             (const uint16_t *)src, lds, map);
-    prof_end(L, K_COLS, ev, 0);
+    prof_end(L, K_COLS, ev, 0, 0, nrows, ncols);
 }
 
 void gather_rowptr(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd, const uint64_t *rows,
@@ -791,7 +793,7 @@ void gather_rowptr(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int
         k_gather_rowptr<uint8_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd, rows, map);
     else
         k_gather_rowptr<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd, rows, map);
-    prof_end(L, K_COLS, ev, 0);
+    prof_end(L, K_COLS, ev, 0, 0, nrows, ncols);
 }
 
 void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const int32_t *pos) {
@@ -802,7 +804,7 @@ void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const int32_
         k_set_ones<uint8_t><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint8_t *)V, ldv, pos, (uint8_t)0x38);
     else
         k_set_ones<uint16_t><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint16_t *)V, ldv, pos, (uint16_t)0x3F80);
-    prof_end(L, K_COPY, ev, 0);
+    prof_end(L, K_COPY, ev, 0, 0, count, 1);
 }
 
 void copy2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd, const void *src,
@@ -815,7 +817,7 @@ void copy2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
         k_copy2d<uint8_t><<<grid, 256, 0, L.st>>>(rows, cols, (uint8_t *)dst, ldd, (const uint8_t *)src, lds);
     else
         k_copy2d<uint16_t><<<grid, 256, 0, L.st>>>(rows, cols, (uint16_t *)dst, ldd, (const uint16_t *)src, lds);
-    prof_end(L, K_COPY, ev, 0);
+    prof_end(L, K_COPY, ev, 0, 0, rows, cols);
 }
 
 void zero2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd) {
@@ -874,7 +876,7 @@ void import_u8(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t l
         k_import_u8<CODEC_F8><<<grid, 256, 0, L.st>>>(L.p, rows, cols, (uint8_t *)dst, ldd, src, lds);
     else
         k_import_u8<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, rows, cols, (uint16_t *)dst, ldd, src, lds);
-    prof_end(L, K_CONV, ev, 0);
+    prof_end(L, K_CONV, ev, 0, 0, rows, cols);
 }
 
 void import_bits(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
@@ -887,7 +889,7 @@ void import_bits(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t
         k_import_bits<CODEC_F8><<<grid, 256, 0, L.st>>>(rows, cols, (uint8_t *)dst, ldd, src, ldw);
     else
         k_import_bits<CODEC_BF16><<<grid, 256, 0, L.st>>>(rows, cols, (uint16_t *)dst, ldd, src, ldw);
-    prof_end(L, K_CONV, ev, 0);
+    prof_end(L, K_CONV, ev, 0, 0, rows, cols);
 }
 
 void export_u8(const Launch &L, int64_t rows, int64_t cols, uint8_t *dst, int64_t ldd,
@@ -900,7 +902,7 @@ void export_u8(const Launch &L, int64_t rows, int64_t cols, uint8_t *dst, int64_
         k_export_u8<CODEC_F8><<<grid, 256, 0, L.st>>>(L.p, rows, cols, dst, ldd, (const uint8_t *)src, lds);
     else
         k_export_u8<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, rows, cols, dst, ldd, (const uint16_t *)src, lds);
-    prof_end(L, K_CONV, ev, 0);
+    prof_end(L, K_CONV, ev, 0, 0, rows, cols);
 }
 
 void export_bits(const Launch &L, int64_t rows, int64_t cols, uint64_t *dst, int64_t ldw,
@@ -915,7 +917,7 @@ void export_bits(const Launch &L, int64_t rows, int64_t cols, uint64_t *dst, int
         k_export_bits<CODEC_F8><<<grid, 128, 0, L.st>>>(rows, cols, dst, ldw, (const uint8_t *)src, lds);
     else
         k_export_bits<CODEC_BF16><<<grid, 128, 0, L.st>>>(rows, cols, dst, ldw, (const uint16_t *)src, lds);
-    prof_end(L, K_CONV, ev, 0);
+    prof_end(L, K_CONV, ev, 0, 0, rows, cols);
 }
 
 // dense E and T in the API storage
@@ -1009,7 +1011,7 @@ void build_E(const Launch &L, int fmt, int64_t m, int64_t n, int64_t r, void *ds
         k_build_E_u8<CODEC_BF16><<<grid_rc(m, n, 256), 256, 0, L.st>>>(L.p, m, n, r, (uint8_t *)dst, ldd,
                                                                         (const uint16_t *)R, ldr, colmap);
     }
-    prof_end(L, K_CONV, ev, 0);
+    prof_end(L, K_CONV, ev, 0, 0, m, n);
 }
 
 void build_T(const Launch &L, int fmt, int64_t m, int64_t r, void *dst, int64_t ldd, const void *M,
@@ -1032,7 +1034,7 @@ void build_T(const Launch &L, int fmt, int64_t m, int64_t r, void *dst, int64_t 
         k_build_T_u8<CODEC_BF16><<<grid_rc(m, m, 256), 256, 0, L.st>>>(L.p, m, r, (uint8_t *)dst, ldd,
             (const uint16_t *)M, ldm, (const uint16_t *)K, ldk, rowmap);
     }
-    prof_end(L, K_CONV, ev, 0);
+    prof_end(L, K_CONV, ev, 0, 0, m, m);
 }
 
 __global__ void k_write_i64(int64_t *dst, const int32_t *src, int64_t count, int64_t offset) {
@@ -1045,7 +1047,7 @@ void write_i64(const Launch &L, int64_t *dst, const int32_t *src, int64_t count,
     cudaEvent_t ev;
     prof_begin(L, K_OTHER, &ev);
     k_write_i64<<<cdiv(count, 256), 256, 0, L.st>>>(dst, src, count, offset);
-    prof_end(L, K_OTHER, ev, 0);
+    prof_end(L, K_OTHER, ev, 0, 0, count, 1);
 }
 
 }  // namespace gfe

@@ -533,7 +533,7 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
             k_mad_tc<false><<<grid, TC_THREADS, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C,
                                                                  ldc, err);
         prof_end(L, K_MAD_TC, ev, (double)m * (double)n * (double)kk,
-                 (double)es * ((double)m * kk + (double)kk * n + (Wk ? 2.0 : 1.0) * (double)m * n));
+                 (double)es * ((double)m * kk + (double)kk * n + (Wk ? 2.0 : 1.0) * (double)m * n), m, n, kk);
     }
     return true;
 }

@@ -37,7 +37,13 @@ class GfeResult(ctypes.Structure):
 
 class GfeProfile(ctypes.Structure):
     _fields_ = [("launches", _i64 * 8), ("ms", ctypes.c_double * 8), ("madds", ctypes.c_double * 8),
-                ("bytes", ctypes.c_double * 8), ("timed", _i64 * 8), ("host_syncs", _i64)]
+                ("bytes", ctypes.c_double * 8), ("timed", _i64 * 8), ("host_syncs", _i64),
+                ("host_wait_ms", ctypes.c_double), ("host_ms", ctypes.c_double)]
+
+
+class GfeTraceRecord(ctypes.Structure):
+    _fields_ = [("kind", _i32), ("pad", _i32), ("m", _i64), ("n", _i64), ("k", _i64), ("stream", ctypes.c_uint64),
+                ("start_ms", ctypes.c_double), ("ms", ctypes.c_double)]
 
 
 KINDS = ["mad_tensor", "mad_plain", "ech_leaf", "rows", "cols", "copy", "convert", "other"]
@@ -70,6 +76,8 @@ SIGNATURES = {
     "gfe_set_block_policy": (_i32, [_i64, _i64]),
     "gfe_profile_enable": (_i32, [_i32]),
     "gfe_profile_read": (_i32, [ctypes.POINTER(GfeProfile), _i32]),
+    "gfe_trace_enable": (_i32, [_i64]),
+    "gfe_trace_read": (_i32, [ctypes.POINTER(GfeTraceRecord), _i64, ctypes.POINTER(_i64), _i32]),
     "gfe_selftest_wait_timeout": (_i32, [_i64, _vp]),
     "gfe_status_str": (ctypes.c_char_p, [_i32]),
     "gfe_last_error": (ctypes.c_char_p, []),
@@ -337,7 +345,23 @@ def profile_read(reset: bool = True) -> dict:
                 madds={k: pr.madds[i] for i, k in enumerate(KINDS)},
                 bytes={k: pr.bytes[i] for i, k in enumerate(KINDS)},
                 timed={k: pr.timed[i] for i, k in enumerate(KINDS)},
-                host_syncs=pr.host_syncs)
+                host_syncs=pr.host_syncs, host_wait_ms=pr.host_wait_ms, host_ms=pr.host_ms)
+
+
+def trace_enable(capacity: int = 1 << 20):
+    """Keep a per-launch record (kind, shape, stream, start, duration) of up
+    to `capacity` timed launches (gfe_trace_enable); 0 stops and drops them.
+    Records are made only while the profile is enabled."""
+    _check(lib().gfe_trace_enable(capacity))
+
+
+def trace_read(reset: bool = True) -> list:
+    n = ctypes.c_int64(0)
+    _check(lib().gfe_trace_read(None, 0, ctypes.byref(n), 0))
+    buf = (GfeTraceRecord * max(n.value, 1))()
+    _check(lib().gfe_trace_read(buf, n.value, ctypes.byref(n), 1 if reset else 0))
+    return [dict(kind=KINDS[r.kind], m=r.m, n=r.n, k=r.k, stream=r.stream, start_ms=r.start_ms, ms=r.ms)
+            for r in buf[:n.value]]
 
 
 class Server:

@@ -77,3 +77,13 @@ def test_status_strings():
     L = gfe.lib()
     assert L.gfe_status_str(0) == b"ok"
     assert L.gfe_status_str(1) == b"invalid argument"
+
+
+def test_block_policy_validation():
+    """A block wider than the threshold would recurse without end."""
+    for thr, blk in [(1024, 2048), (100, 200)]:
+        with pytest.raises(gfe.GfeError):
+            gfe.set_block_policy(thr, blk)
+    gfe.set_block_policy(4096, 4096)
+    gfe.set_block_policy(40, 16)
+    gfe.set_block_policy()
