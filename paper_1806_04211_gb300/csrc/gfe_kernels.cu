@@ -204,12 +204,16 @@ __device__ __forceinline__ uint32_t pmadd(uint32_t a, uint32_t g, uint32_t b, co
 #define GFE_RCASE16(M)                                                                                    \
     M(15) M(14) M(13) M(12) M(11) M(10) M(9) M(8) M(7) M(6) M(5) M(4) M(3) M(2) M(1) M(0)
 
+// word i of a register array: a select tree of depth 4 (not a chain of 15)
 __device__ __forceinline__ uint32_t pick16(const uint32_t (&a)[16], int i) {
-    uint32_t v = a[0];
+    uint32_t l1[8], l2[4], l3[2];
 #pragma unroll
-    for (int w = 1; w < 16; ++w)
-        if (i == w) v = a[w];
-    return v;
+    for (int w = 0; w < 8; ++w) l1[w] = (i & 1) ? a[2 * w + 1] : a[2 * w];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) l2[w] = (i & 2) ? l1[2 * w + 1] : l1[2 * w];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) l3[w] = (i & 4) ? l2[2 * w + 1] : l2[2 * w];
+    return (i & 8) ? l3[1] : l3[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -232,8 +236,8 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(PackedMod pm, int alpha, i
                                                       int64_t ldr) {
     using D = Cd<C>;
     extern __shared__ uint8_t sm[];
-    uint8_t *S = sm;                           // [1024][LS]  residues of H (load / output)
-    uint8_t *Tt = sm + 1024 * LS;              // [1024][LS]  slot coefficients (output)
+    uint8_t *S = sm;                           // [threads][LS]  residues of H (load / output)
+    uint8_t *Tt = sm + blockDim.x * LS;        // [threads][LS]  slot coefficients (output)
     __shared__ uint8_t inv[256];
     __shared__ uint8_t piv[1024];
     __shared__ int16_t slotOf[1024];
@@ -242,18 +246,20 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(PackedMod pm, int alpha, i
     __shared__ uint32_t wbuf[2][32][32];
     __shared__ int wmin[2][32];
     __shared__ int wsum[32];
-    const int y = threadIdx.x, lane = y & 31, warp = y >> 5;
+    const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
     const int p = (int)pm.p;
 
-    if (y < p) {
+    for (int q = y; q < p; q += blockDim.x) {
         int v = 0;
         for (int x = 1; x < p; ++x)
-            if ((y * x) % p == 1) v = x;
-        inv[y] = (uint8_t)v;
+            if ((q * x) % p == 1) v = x;
+        inv[q] = (uint8_t)v;
     }
+    for (int q = y; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
     piv[y] = 0;
     slotOf[y] = -1;
     // coalesced load: warp w reads its 32 rows, lane l columns l and l + 32
+#pragma unroll 8
     for (int rr = 0; rr < 32; ++rr) {
         const int row = warp * 32 + rr;
         const typename D::T *hr = H + (int64_t)row * ldh;
@@ -375,12 +381,12 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(PackedMod pm, int alpha, i
     __syncthreads();
     // outputs: one row per warp, lanes along the columns (coalesced)
     // M[l][s] = coefficient of pivot row rho_s in echelon row l
-    for (int l = warp; l < r; l += 32)
+    for (int l = warp; l < r; l += nwarp)
         for (int s = lane; s < r; s += 32)
             Mo[(int64_t)l * ldm + s] = D::enc(cen(Tt[slotRow[l] * LS + sortedSlot[s]], p));
     // K[t][s] for the non-pivot rows t
     if (r > 0) {
-        for (int row = warp; row < alpha; row += 32) {
+        for (int row = warp; row < alpha; row += nwarp) {
             if (piv[row]) continue;
             for (int s = lane; s < r; s += 32)
                 Ko[(int64_t)pivpos[row] * ldk + s] = D::enc(cen(Tt[row * LS + sortedSlot[s]], p));
@@ -388,7 +394,180 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(PackedMod pm, int alpha, i
     }
     // R[l][j] = entry of echelon row l in the j-th non-pivot column
     const int nr = beta - r;
-    for (int l = warp; l < r; l += 32)
+    for (int l = warp; l < r; l += nwarp)
+        for (int j = lane; j < nr; j += 32)
+            Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
+}
+
+// Byte-wise reduction mod p of four packed values <= 255 (p <= 13): the
+// Barrett step of pmadd without the multiply-add.
+__device__ __forceinline__ uint32_t preduce(uint32_t x, const PackedMod &q) {
+    const uint32_t lo = x & 0x00FF00FFu, hi = (x >> 8) & 0x00FF00FFu;
+    const uint32_t qq = (((lo * q.M) >> q.S) & q.QM) | ((((hi * q.M) >> q.S) & q.QM) << 8);
+    const uint32_t r = x - qq * q.p;
+    return r - (__vcmpgeu4(r, q.pp) & q.pp);
+}
+
+// ---------------------------------------------------------------------------
+// leaf ECH for small p (3 <= p <= 13) with lazy reduction: the same
+// column-by-column Gauss-Jordan and topmost-row rule as k_ech_leaf, but a
+// row update is one integer multiply-add per packed word, a += v * s with
+// v < p and s < p in every byte, and rows are reduced mod p only every
+// `lazy_k` pivot steps, lazy_k = floor((255 - (p - 1)) / (p - 1)^2), so no
+// byte ever exceeds 255.  The pivot row is published unreduced; every warp
+// reduces it and scales it by -1/pivot lane-parallel (lane w takes word w)
+// and shuffles the words to its lanes.
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void __launch_bounds__(1024, 1) k_ech_leaf_lazy(PackedMod pm, int lazy_k, int alpha, int beta,
+                                                           const typename Cd<C>::T *H, int64_t ldh,
+                                                           int32_t *info, typename Cd<C>::T *Mo,
+                                                           int64_t ldm, typename Cd<C>::T *Ko,
+                                                           int64_t ldk, typename Cd<C>::T *Ro,
+                                                           int64_t ldr) {
+    using D = Cd<C>;
+    extern __shared__ uint8_t sm[];
+    uint8_t *S = sm;                           // [threads][LS]  residues of H (load / output)
+    uint8_t *Tt = sm + blockDim.x * LS;        // [threads][LS]  slot coefficients (output)
+    __shared__ uint8_t inv[16];
+    __shared__ uint8_t piv[1024];
+    __shared__ int16_t slotOf[1024];
+    __shared__ int16_t pivpos[1024];
+    __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
+    __shared__ uint32_t wbuf[2][32][32];
+    __shared__ int wmin[2][32];
+    __shared__ int wsum[32];
+    const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
+    const int p = (int)pm.p;
+    const uint32_t mv = (65536u + (uint32_t)p - 1) / (uint32_t)p;  // v mod p = v - ((v * mv) >> 16) * p, v <= 255
+
+    for (int q = y; q < p; q += blockDim.x) {
+        int v = 0;
+        for (int x = 1; x < p; ++x)
+            if ((q * x) % p == 1) v = x;
+        inv[q] = (uint8_t)v;
+    }
+    for (int q = y; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
+    piv[y] = 0;
+    slotOf[y] = -1;
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+        const int row = warp * 32 + rr;
+        const typename D::T *hr = H + (int64_t)row * ldh;
+        const bool in = row < alpha;
+        S[row * LS + lane] = in && lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
+        S[row * LS + 32 + lane] = in && 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
+    }
+    __syncthreads();
+    uint32_t h[16], t[16];
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        h[w] = *(const uint32_t *)(S + y * LS + 4 * w);
+        t[w] = 0;
+    }
+    bool isp = false;
+    __syncthreads();
+
+    int ns = 0, since = 0;  // pivots so far; pivot steps since the last full reduction
+    for (int c = 0; c < beta; ++c) {
+        const int b = c & 1, wc = c >> 2, bc = 8 * (c & 3);
+        const uint32_t vraw = (pick16(h, wc) >> bc) & 0xFF;
+        const uint32_t v = vraw - ((vraw * mv) >> 16) * (uint32_t)p;
+        const bool cand = (y < alpha) && !isp && v != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0) wmin[b][warp] = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
+        if (bal && lane == __ffs(bal) - 1) {
+#pragma unroll
+            for (int w = 0; w < 16; ++w) {
+                wbuf[b][warp][w] = h[w];
+                wbuf[b][warp][16 + w] = t[w];
+            }
+        }
+        __syncthreads();
+        const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)wmin[b][lane]);
+        if (x == INT_MAX) continue;  // uniform: column c has no pivot
+        // lane w: word w of the pivot row (h words 0..15, then t words),
+        // reduced, with the pivot's own identity in slot ns, times -1/pivot
+        const uint32_t *px = wbuf[b][x >> 5];
+        const uint32_t praw = (px[wc] >> bc) & 0xFF;
+        const uint32_t pv = praw - ((praw * mv) >> 16) * (uint32_t)p;
+        const uint32_t sc = pv ? (uint32_t)p - inv[pv] : 0u;
+        uint32_t wv = preduce(px[lane], pm);
+        if (lane == 16 + (ns >> 2)) wv += 1u << (8 * (ns & 3));
+        wv = preduce(wv * sc, pm);
+        // the pivot row becomes that row; every other row adds v times it
+        const bool me = (y == x);
+        const uint32_t g = me ? 1u : v;
+        if (me) {
+#pragma unroll
+            for (int w = 0; w < 16; ++w) h[w] = t[w] = 0;
+            isp = true;
+            piv[y] = 1;
+            slotOf[y] = (int16_t)ns;
+            slotRow[ns] = (int16_t)y;
+            slotCol[ns] = (int16_t)c;
+        }
+#pragma unroll
+        for (int w = 0; w < 16; ++w) {
+            h[w] += g * __shfl_sync(0xffffffffu, wv, w);
+            t[w] += g * __shfl_sync(0xffffffffu, wv, 16 + w);
+        }
+        ++ns;
+        if (++since == lazy_k) {
+            since = 0;
+#pragma unroll
+            for (int w = 0; w < 16; ++w) {
+                h[w] = preduce(h[w], pm);
+                t[w] = preduce(t[w], pm);
+            }
+        }
+    }
+    const int r = ns;
+    // fully reduced rows back to shared memory for the (coalesced) output phase
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        *(uint32_t *)(S + y * LS + 4 * w) = preduce(h[w], pm);
+        *(uint32_t *)(Tt + y * LS + 4 * w) = preduce(t[w], pm);
+    }
+    // rank of each row among pivot rows (ascending) and among non-pivot rows
+    const int isp_i = (y < alpha) && isp;
+    unsigned bal = __ballot_sync(0xffffffffu, isp_i);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    before += __popc(bal & ((1u << lane) - 1));
+    if (y < alpha) {
+        if (isp_i) {
+            pivpos[y] = (int16_t)before;
+            sortedSlot[before] = slotOf[y];
+            info[1 + before] = y;
+        } else {
+            pivpos[y] = (int16_t)(y - before);
+        }
+    }
+    if (y == 0) {
+        info[0] = r;
+        int j = 0, l = 0;
+        for (int c = 0; c < beta; ++c) {
+            if (l < r && slotCol[l] == c) ++l;
+            else nonCol[j++] = (int16_t)c;
+        }
+    }
+    if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
+    __syncthreads();
+    for (int l = warp; l < r; l += nwarp)
+        for (int s = lane; s < r; s += 32)
+            Mo[(int64_t)l * ldm + s] = D::enc(cen(Tt[slotRow[l] * LS + sortedSlot[s]], p));
+    if (r > 0) {
+        for (int row = warp; row < alpha; row += nwarp) {
+            if (piv[row]) continue;
+            for (int s = lane; s < r; s += 32)
+                Ko[(int64_t)pivpos[row] * ldk + s] = D::enc(cen(Tt[row * LS + sortedSlot[s]], p));
+        }
+    }
+    const int nr = beta - r;
+    for (int l = warp; l < r; l += nwarp)
         for (int j = lane; j < nr; j += 32)
             Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
 }
@@ -443,20 +622,22 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
     // words of slot coefficients)
     static_assert(W == 4, "one bitmask byte per lane in the load");
     extern __shared__ uint64_t smw[];
-    uint64_t *hw = smw;                 // [1024][W] rows after elimination
-    uint64_t *tw = smw + 1024 * W;      // [1024][W] slot coefficients
+    uint64_t *hw = smw;                  // [threads][W] rows after elimination
+    uint64_t *tw = smw + blockDim.x * W; // [threads][W] slot coefficients
     __shared__ uint64_t wbuf[2][32][2 * W];
     __shared__ int wmin[2][32];
     __shared__ uint8_t piv[1024];
     __shared__ int16_t slotOf[1024], pivpos[1024];
     __shared__ int16_t slotRow[64 * W], slotCol[64 * W], sortedSlot[64 * W], nonCol[64 * W];
     __shared__ int wsum[32];
-    const int y = threadIdx.x, lane = y & 31, warp = y >> 5;
+    const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
+    for (int q = y; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
 
     // coalesced load: warp w reads its 32 rows one at a time, lane l the 8
     // columns 8l..8l+7, stored as byte l of the row's 32-byte bitmask
     {
         uint8_t *hb = (uint8_t *)hw;
+#pragma unroll 8
         for (int rr = 0; rr < 32; ++rr) {
             const int row = warp * 32 + rr;
             uint32_t mask = 0;
@@ -575,7 +756,7 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
     if (y < r) info[1 + 64 * W + y] = slotCol[y];
     __syncthreads();
     // outputs: one row per warp, lanes along the columns (coalesced)
-    for (int l = warp; l < r; l += 32) {
+    for (int l = warp; l < r; l += nwarp) {
         const uint64_t *tl = tw + slotRow[l] * W;
         for (int s = lane; s < r; s += 32) {
             const int q = sortedSlot[s];
@@ -583,7 +764,7 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         }
     }
     if (r > 0) {
-        for (int row = warp; row < alpha; row += 32) {
+        for (int row = warp; row < alpha; row += nwarp) {
             if (piv[row]) continue;
             const uint64_t *tr = tw + row * W;
             T *ko = Ko + (int64_t)pivpos[row] * ldk;
@@ -594,7 +775,7 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         }
     }
     const int nr = beta - r;
-    for (int l = warp; l < r; l += 32) {
+    for (int l = warp; l < r; l += nwarp) {
         const uint64_t *hl = hw + slotRow[l] * W;
         for (int j = lane; j < nr; j += 32) {
             const int c = nonCol[j];
@@ -607,28 +788,30 @@ int ech_leaf_cols(int p) { return p == 2 ? ECH_LEAF_COLS_GF2 : ECH_LEAF_COLS; }
 
 void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64_t ldh,
               int32_t *info, void *M, int64_t ldm, void *K, int64_t ldk, void *R, int64_t ldr) {
+    // one thread per row: the CTA shrinks with the rows still to eliminate
+    const int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (alpha + 31) / 32 * 32));
     if (L.p == 2) {
-        const int smem = 2 * 1024 * 4 * 8;
+        const int smem_max = 2 * 1024 * 4 * 8, smem = 2 * threads * 4 * 8;
         static std::once_flag once[2];
         cudaEvent_t ev;
         prof_begin(L, K_ECH, &ev);
         if (L.codec == CODEC_F8) {
             std::call_once(once[0], [&] {
-                cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
             });
-            k_ech_leaf_gf2<4, uint8_t><<<1, 1024, smem, L.st>>>((int)alpha, (int)beta, (const uint8_t *)H, ldh, info,
+            k_ech_leaf_gf2<4, uint8_t><<<1, threads, smem, L.st>>>((int)alpha, (int)beta, (const uint8_t *)H, ldh, info,
                 (uint8_t *)M, ldm, (uint8_t *)K, ldk, (uint8_t *)R, ldr, (uint8_t)0x38);
         } else {
             std::call_once(once[1], [&] {
-                cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                cudaFuncSetAttribute(k_ech_leaf_gf2<4, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
             });
-            k_ech_leaf_gf2<4, uint16_t><<<1, 1024, smem, L.st>>>((int)alpha, (int)beta, (const uint16_t *)H, ldh,
+            k_ech_leaf_gf2<4, uint16_t><<<1, threads, smem, L.st>>>((int)alpha, (int)beta, (const uint16_t *)H, ldh,
                 info, (uint16_t *)M, ldm, (uint16_t *)K, ldk, (uint16_t *)R, ldr, (uint16_t)0x3F80);
         }
         prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta), 0, alpha, beta);
         return;
     }
-    const int smem = 2 * 1024 * LS;
+    const int smem_max = 2 * 1024 * LS, smem = 2 * threads * LS;
     const PackedMod pm = packed_mod(L.p);
     const bool small = L.p <= 13;
     static std::once_flag once2[4];
@@ -637,19 +820,30 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
 #define GFE_LEAF(CODEC, T, SM, IDX)                                                                              \
     do {                                                                                                          \
         std::call_once(once2[IDX], [&] {                                                                          \
-            cudaFuncSetAttribute(k_ech_leaf<CODEC, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);       \
+            cudaFuncSetAttribute(k_ech_leaf<CODEC, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);   \
         });                                                                                                       \
-        k_ech_leaf<CODEC, SM><<<1, 1024, smem, L.st>>>(pm, (int)alpha, (int)beta, (const T *)H, ldh, info,        \
+        k_ech_leaf<CODEC, SM><<<1, threads, smem, L.st>>>(pm, (int)alpha, (int)beta, (const T *)H, ldh, info,        \
                                                      (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);                      \
     } while (0)
+#define GFE_LAZY(CODEC, T, IDX)                                                                                  \
+    do {                                                                                                          \
+        std::call_once(once2[IDX], [&] {                                                                          \
+            cudaFuncSetAttribute(k_ech_leaf_lazy<CODEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);  \
+        });                                                                                                       \
+        k_ech_leaf_lazy<CODEC><<<1, threads, smem, L.st>>>(pm, lazy_k, (int)alpha, (int)beta, (const T *)H, ldh,  \
+                                                          info, (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);           \
+    } while (0)
+    // pivot steps between full reductions: (p - 1) + k (p - 1)^2 <= 255
+    const int lazy_k = small ? (255 - (L.p - 1)) / ((L.p - 1) * (L.p - 1)) : 0;
     if (L.codec == CODEC_F8) {
-        if (small) GFE_LEAF(CODEC_F8, uint8_t, true, 0);
+        if (small) GFE_LAZY(CODEC_F8, uint8_t, 0);
         else GFE_LEAF(CODEC_F8, uint8_t, false, 1);
     } else {
-        if (small) GFE_LEAF(CODEC_BF16, uint16_t, true, 2);
+        if (small) GFE_LAZY(CODEC_BF16, uint16_t, 2);
         else GFE_LEAF(CODEC_BF16, uint16_t, false, 3);
     }
 #undef GFE_LEAF
+#undef GFE_LAZY
     prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta), 0, alpha, beta);
 }
 

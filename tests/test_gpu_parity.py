@@ -51,6 +51,7 @@ CASES = [
     (3, 300, 200, None), (5, 257, 513, None), (7, 1500, 700, None), (7, 700, 1500, 300),
     (3, 1000, 1000, None), (3, 1000, 1000, 700), (31, 333, 444, None),
     (37, 200, 300, None), (251, 400, 400, None), (251, 600, 450, 270), (193, 129, 1100, None),
+    (11, 300, 200, None), (13, 200, 300, 150), (5, 1100, 130, None), (13, 1030, 64, None),
 ]
 
 
