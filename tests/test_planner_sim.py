@@ -1,0 +1,173 @@
+"""The planner (Steps 1-3 of the Chief, the recursive ECH, the batch entry
+point) run on the CPU against stand-ins of the CUDA runtime and CPU
+restatements of the jobs (tests/plansim/sim.cpp): its results equal the
+oracle's, every buffer access stays in bounds, and no access of one stream
+is unordered with a conflicting access of another (the two-stream schedule
+of Step 1 is ordered by events alone).  No GPU needed."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import oracle as O
+from paper_1806_04211_gb300 import gfe
+
+CSRC = os.path.join(ROOT, "paper_1806_04211_gb300", "csrc")
+SIMDIR = os.path.join(ROOT, "tests", "plansim")
+LIB = os.path.join(SIMDIR, "_build", "libgfe_plansim.so")
+
+
+def cuda_include():
+    for d in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
+            return os.path.join(d, "include")
+    return None
+
+
+@pytest.fixture(scope="module")
+def sim():
+    inc = cuda_include()
+    if shutil.which("g++") is None or inc is None:
+        pytest.skip("g++ or the CUDA headers are not available")
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    srcs = [os.path.join(CSRC, "gfe_chief.cu"), os.path.join(CSRC, "gfe_api.cu")]
+    cmd = ["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-Wl,-Bsymbolic", "-x", "c++"] + srcs + \
+          ["-x", "none", os.path.join(SIMDIR, "sim.cpp"), "-I", inc, "-I", os.path.join(ROOT, "include"),
+           "-I", CSRC, "-o", LIB, "-lpthread"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    L = ctypes.CDLL(LIB)
+    L.sim_register.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    L.sim_races.restype = ctypes.c_long
+    for name, (res, args) in gfe.SIGNATURES.items():
+        if hasattr(L, name):
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+    yield L
+    L.gfe_set_block_policy(0, 0)
+
+
+def races(L):
+    n = L.sim_races()
+    L.sim_race_reset()
+    return n
+
+
+def run(L, A, p, n=None, flags=1):
+    bits = A.dtype != np.uint8
+    m = A.shape[0]
+    nn = n if bits else A.shape[1]
+    mat = gfe.GfeMatrix(p, m, nn, 1 if bits else 0, A.ctypes.data, A.strides[0])
+    mn = min(m, nn)
+
+    def out(rows, cols):
+        if bits:
+            return np.zeros((max(rows, 1), gfe.words_per_row(max(cols, 1))), np.uint64)
+        return np.zeros((max(rows, 1), max(cols, 1)), np.uint8)
+
+    rank = np.zeros(1, np.int64)
+    pc = np.zeros(max(mn, 1), np.int64)
+    pr = np.zeros(max(mn, 1), np.int64)
+    R, M, K = out(mn, nn), out(mn, mn), out(m, mn)
+    for a in (A, rank, pc, pr, R, M, K):
+        L.sim_register(a.ctypes.data, a.nbytes)
+    res = gfe.GfeResult(rank.ctypes.data, pc.ctypes.data, pr.ctypes.data, R.ctypes.data, R.strides[0],
+                        M.ctypes.data, M.strides[0], K.ctypes.data, K.strides[0], None, 0, None, 0)
+    need = ctypes.c_size_t(0)
+    assert L.gfe_query_workspace(ctypes.byref(mat), flags, ctypes.byref(need)) == 0
+    ws = np.zeros(need.value, np.uint8)
+    L.sim_register(ws.ctypes.data, ws.nbytes)
+    st = L.gfe_echelon(ctypes.byref(mat), ctypes.byref(res), flags, ws.ctypes.data, ws.nbytes, None)
+    assert st == 0, L.gfe_last_error()
+    r = int(rank[0])
+    d = dict(rank=r, rho=pr[:r], ups=pc[:r])
+    if bits:
+        d.update(R=R[:r] if r else R[:0], M=M[:r], K=K[:m - r])
+    else:
+        d.update(R=R[:r, :nn - r], M=M[:r, :r], K=K[:m - r, :r])
+    return d
+
+
+def check(L, A, p):
+    got = run(L, A, p)
+    ref = O.echelon(A, p)
+    assert got["rank"] == ref["rank"]
+    for k in ("rho", "ups", "R", "M", "K"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert races(L) == 0
+
+
+def check_gf2(L, A):
+    m, n = A.shape
+    W = O.pack_bits(A)
+    got = run(L, W, 2, n=n)
+    ref = O.echelon_gf2(W, m, n)
+    r = ref["rank"]
+    assert got["rank"] == r
+    for k in ("rho", "ups"):
+        assert np.array_equal(got[k], ref[k]), k
+    for k, cols in (("R", n - r), ("M", r), ("K", r)):
+        rows = ref[k].shape[0] if ref[k].size else 0
+        if rows and cols:
+            assert np.array_equal(O.unpack_bits(got[k], cols)[:rows], O.unpack_bits(ref[k], cols)), k
+    assert races(L) == 0
+
+
+# (threshold, block): a top-level Chief over small blocks; blocks wider than
+# a leaf (128, 96 > 64 columns for p > 2) make the ECH of each block a Chief
+# of its own, so two levels of side streams run at once
+POLICIES = [(40, 16), (100, 48), (150, 128), (130, 96)]
+
+
+@pytest.mark.parametrize("thr,blk", POLICIES)
+def test_planner_matches_oracle_without_races(sim, thr, blk):
+    assert sim.gfe_set_block_policy(thr, blk) == 0
+    rng = np.random.RandomState(thr + blk)
+    for trial in range(10):
+        p = [3, 5, 7, 2, 13, 251, 31][trial % 7]
+        m, n = rng.randint(1, 200), rng.randint(1, 200)
+        kind = trial % 3
+        if kind == 0:
+            A = rng.randint(0, p, (m, n))
+        elif kind == 1:
+            k = rng.randint(0, min(m, n) + 1)
+            A = (rng.randint(0, p, (m, k)) @ rng.randint(0, p, (k, n))) % p
+        else:
+            A = rng.randint(0, p, (m, n)) * (rng.rand(m, n) < 0.05)
+        A = A.astype(np.uint8)
+        if p == 2:
+            check_gf2(sim, A)
+        else:
+            check(sim, A, p)
+    sim.gfe_set_block_policy(0, 0)
+
+
+def test_planner_sim_detects_a_planted_race(sim):
+    """The checker itself: two copies on different streams with no event
+    between them, writing the same bytes, must be reported."""
+    buf = np.zeros(64, np.uint8)
+    src = np.ones(64, np.uint8)
+    sim.sim_register(buf.ctypes.data, buf.nbytes)
+    sim.sim_register(src.ctypes.data, src.nbytes)
+    s1, s2 = ctypes.c_void_p(), ctypes.c_void_p()
+    sim.cudaStreamCreateWithFlags(ctypes.byref(s1), 1)
+    sim.cudaStreamCreateWithFlags(ctypes.byref(s2), 1)
+    cp = sim.cudaMemcpyAsync
+    cp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]
+    races(sim)
+    cp(buf.ctypes.data, src.ctypes.data, 64, 3, s1)  # device to device
+    cp(buf.ctypes.data, src.ctypes.data, 64, 3, s2)
+    assert races(sim) > 0
+    # ordered by an event: no race
+    ev = ctypes.c_void_p()
+    sim.cudaEventCreate(ctypes.byref(ev))
+    cp(buf.ctypes.data, src.ctypes.data, 64, 3, s1)
+    sim.cudaEventRecord(ev, s1)
+    sim.cudaStreamWaitEvent(s2, ev, 0)
+    cp(buf.ctypes.data, src.ctypes.data, 64, 3, s2)
+    assert races(sim) == 0
