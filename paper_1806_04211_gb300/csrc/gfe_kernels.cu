@@ -593,12 +593,24 @@ static PackedMod packed_mod(int p) {
 }
 
 // ---------------------------------------------------------------------------
-// leaf echelonisation over GF(2): the same column-by-column Gauss-Jordan with
-// the topmost-row rule, but each thread holds its row (<= 256 columns) and
-// its <= 256 slot coefficients as 64-bit words in registers, so eliminating
-// a row is one XOR per word.  The candidate rows of every warp publish their
-// words before the barrier; after it the pivot (the smallest candidate row)
-// is read from its warp's buffer, so each column costs one barrier.
+// leaf echelonisation over GF(2): the same Gauss-Jordan with the topmost-row
+// rule, each thread holding its row (<= 256 columns) and its <= 256 slot
+// coefficients as 64-bit words in registers, taken eight columns at a time:
+//  (A) every warp publishes its rows' bits in the group's columns, one
+//      32-bit word per column (a ballot each);
+//  (B) one finder warp runs the column-by-column elimination on that
+//      1024 x 8 bit slice alone (lane l holds warp l's words), finding the
+//      group's pivot rows x_s in order and, for every row y, the set CM_y of
+//      group pivots whose rows as they stood at the group start make up what
+//      was added to y (also one word per pivot);
+//  (C) the group's pivot rows publish their rows as they stood at the group
+//      start, with the identity of their slot;
+//  (D) all threads tabulate the XOR of every subset of pivots 0..3 and of
+//      pivots 4..7 (two 16-entry tables);
+//  (E) row y adds the two entries that make up CM_y (and a pivot row its
+//      own identity).
+// Rows are linear in the rows they were built from, so (E) reproduces the
+// column-by-column result; four barriers per group instead of one per column.
 // ---------------------------------------------------------------------------
 // register-resident word arrays: select / update word i without local memory
 template <int W> __device__ __forceinline__ uint64_t wpick(const uint64_t (&a)[W], int i) {
@@ -613,6 +625,13 @@ template <int W> __device__ __forceinline__ void wxor(uint64_t (&a)[W], int i, u
     for (int w = 0; w < W; ++w)
         if (i == w) a[w] ^= m;
 }
+// word i of eight, select tree of depth 3
+__device__ __forceinline__ uint32_t sel8(const uint32_t (&a)[8], int i) {
+    const uint32_t l0 = (i & 1) ? a[1] : a[0], l1 = (i & 1) ? a[3] : a[2];
+    const uint32_t l2 = (i & 1) ? a[5] : a[4], l3 = (i & 1) ? a[7] : a[6];
+    const uint32_t m0 = (i & 2) ? l1 : l0, m1 = (i & 2) ? l3 : l2;
+    return (i & 4) ? m1 : m0;
+}
 
 template <int W, typename T>
 __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, const T *H, int64_t ldh,
@@ -624,14 +643,17 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
     extern __shared__ uint64_t smw[];
     uint64_t *hw = smw;                  // [threads][W] rows after elimination
     uint64_t *tw = smw + blockDim.x * W; // [threads][W] slot coefficients
-    __shared__ uint64_t wbuf[2][32][2 * W];
-    __shared__ int wmin[2][32];
+    __shared__ uint64_t orig[8][2 * W];    // the group's pivot rows at the group start
+    __shared__ uint64_t tab[2][2 * W][16]; // XOR of every subset of pivots 0..3 / 4..7 (word-major)
+    __shared__ uint32_t slc[32][8];        // bit q of slc[w][k]: column c0+k of row 32w+q
+    __shared__ uint32_t cms[32][8];        // bit q of cms[w][s]: pivot s in CM of row 32w+q
+    __shared__ int16_t gpr[8], gpc[8];     // the group's pivots: row, column
+    __shared__ int gnp;
     __shared__ uint8_t piv[1024];
     __shared__ int16_t slotOf[1024], pivpos[1024];
     __shared__ int16_t slotRow[64 * W], slotCol[64 * W], sortedSlot[64 * W], nonCol[64 * W];
     __shared__ int wsum[32];
     const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
-    for (int q = y; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
 
     // coalesced load: warp w reads its 32 rows one at a time, lane l the 8
     // columns 8l..8l+7, stored as byte l of the row's 32-byte bitmask
@@ -681,48 +703,117 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
     bool isp = false;
     __syncthreads();
 
-    // per column: every warp publishes its first candidate row and that
-    // row's words (double-buffered by column parity), one barrier, then every
-    // warp reduces the 32 published minima -- no atomics
+    // the finder's state (warp 0): lane l's rows 32l..32l+31 that may still
+    // become pivots
+    uint32_t cand_rows = 0;
+    if (warp == 0 && lane * 32 < alpha) cand_rows = alpha - lane * 32 >= 32 ? 0xffffffffu : (1u << (alpha - lane * 32)) - 1;
     int ns = 0;
-    for (int c = 0; c < beta; ++c) {
-        const int b = c & 1;
-        const int cw = c >> 6, cb = c & 63;
-        const bool hit = (wpick<W>(h, cw) >> cb) & 1;
-        const bool cand = (y < alpha) && !isp && hit;
-        const unsigned bal = __ballot_sync(0xffffffffu, cand);
-        const int first = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
-        if (lane == 0) wmin[b][warp] = first;
-        const int nw = ns >> 6;  // slot words beyond nw are zero in every row
-        if (bal && lane == __ffs(bal) - 1) {
-            // a candidate row is zero left of column c and in slots >= ns
+    for (int c0 = 0; c0 < beta; c0 += 8) {
+        // (A) this warp's rows in columns c0..c0+7 (c0 is a multiple of 8),
+        // one 32-bit word per column
+        {
+            const uint32_t by = (uint32_t)(wpick<W>(h, c0 >> 6) >> (c0 & 63));
+            uint32_t mine = 0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                if (w >= cw) wbuf[b][warp][w] = h[w];
-                if (w <= nw) wbuf[b][warp][W + w] = t[w];
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t b = __ballot_sync(0xffffffffu, (by >> k) & 1u);
+                if (lane == k) mine = b;
             }
+            if (lane < 8) slc[warp][lane] = mine;
         }
         __syncthreads();
-        const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)wmin[b][lane]);
-        if (x == INT_MAX) continue;  // uniform: column c has no pivot
-        const uint64_t *px = wbuf[b][x >> 5];
-        const uint64_t own = (uint64_t)1 << (ns & 63);
-        if (y == x) {
-            wxor<W>(t, nw, own);  // own identity in slot ns
-            isp = true;
-            piv[y] = 1;
-            slotOf[y] = (int16_t)ns;
-            slotRow[ns] = (int16_t)y;
-            slotCol[ns] = (int16_t)c;
-        } else if (hit) {
+        // (B) the finder: elimination on the group's columns only, bit-sliced:
+        // bit q of col[k] is column c0+k of row 32*lane+q, bit q of cmb[s]
+        // says group pivot s is in that row's combination
+        if (warp == 0) {
+            uint32_t col[8], cmb[8];
+            const bool live = lane < nwarp;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                col[k] = live ? slc[lane][k] : 0u;
+                cmb[k] = 0u;
+            }
+            int np = 0;
+            for (int k = 0; k < 8; ++k) {
+                // every lane takes its own first candidate row q and forms that
+                // row's byte and combination; the lowest lane with a candidate
+                // holds the pivot and broadcasts them
+                const uint32_t cand = col[k] & cand_rows;
+                const int q = __ffs(cand) - 1;  // -1: none here
+                uint32_t mine = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    mine |= (((col[u] >> (q & 31)) & 1u) << u) | (((cmb[u] >> (q & 31)) & 1u) << (8 + u));
+                const unsigned bal = __ballot_sync(0xffffffffu, cand != 0u);
+                if (bal == 0u) continue;  // uniform: no pivot in this column
+                const int owner = __ffs(bal) - 1;
+                const uint32_t v = __shfl_sync(0xffffffffu, mine, owner);
+                const uint32_t pb = v & 0xFFu, pc = ((v >> 8) & 0xFFu) ^ (1u << np);
+                // rows with column c0+k set, other than the pivot
+                const uint32_t rows = col[k] & ~(lane == owner ? 1u << q : 0u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    col[u] ^= rows & (0u - ((pb >> u) & 1u));
+                    cmb[u] ^= rows & (0u - ((pc >> u) & 1u));
+                }
+                if (lane == owner) {
+                    cand_rows &= ~(1u << q);
+                    gpr[np] = (int16_t)(lane * 32 + q);
+                    gpc[np] = (int16_t)(c0 + k);
+                }
+                ++np;
+            }
+            if (live) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cms[lane][u] = cmb[u];
+            }
+            if (lane == 0) gnp = np;
+        }
+        __syncthreads();
+        const int np = gnp;
+        if (np == 0) continue;  // uniform
+        // (C) the group's pivot rows as they stand now, with their identity
+        int s_me = -1;
+        for (int u = 0; u < np; ++u)
+            if (gpr[u] == y) s_me = u;
+        if (s_me >= 0) {
+            const int slot = ns + s_me;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                if (w >= cw) h[w] ^= px[w];
-                if (w <= nw) t[w] ^= px[W + w];
+                orig[s_me][w] = h[w];
+                orig[s_me][W + w] = t[w] ^ ((slot >> 6) == w ? (uint64_t)1 << (slot & 63) : 0ull);
             }
-            wxor<W>(t, nw, own);  // the pivot's own identity
+            isp = true;
+            piv[y] = 1;
+            slotOf[y] = (int16_t)slot;
+            slotRow[slot] = (int16_t)y;
+            slotCol[slot] = gpc[s_me];
         }
-        ++ns;
+        __syncthreads();
+        // (D) XOR of every subset of pivots 0..3 and of pivots 4..7
+        for (int e = y; e < 2 * 2 * W * 16; e += blockDim.x) {
+            const int half = e >> 7, w = (e >> 4) & (2 * W - 1), m = e & 15;
+            uint64_t v = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (((m >> u) & 1) && 4 * half + u < np) v ^= orig[4 * half + u][w];
+            tab[half][w][m] = v;
+        }
+        __syncthreads();
+        // (E) add the rows of this row's combination; a pivot row also its identity
+        int m = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m |= (int)((cms[warp][u] >> lane) & 1u) << u;
+        if (m) {
+            const int lo = m & 15, hi = m >> 4;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                h[w] ^= tab[0][w][lo] ^ tab[1][w][hi];
+                t[w] ^= tab[0][W + w][lo] ^ tab[1][W + w][hi];
+            }
+        }
+        if (s_me >= 0) wxor<W>(t, (ns + s_me) >> 6, (uint64_t)1 << ((ns + s_me) & 63));
+        ns += np;
     }
     const int r = ns;
 #pragma unroll
