@@ -742,45 +742,40 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     }
 
     // ================= Step 2: RowLengthen (into the output M) =================
-    if (trafo) {
+    // Block row j of the output M takes, for every h, M_jh widened to
+    // E_hb.rho: MKR marks E_hj.rho inside E_hb.rho, CRZ puts the stored
+    // columns at the marks and zeros elsewhere.  All h at once: one column
+    // gather per j over the full width (-1 = a zero column).
+    if (trafo && rank > 0) {
+        std::vector<int32_t> map(rank);
         for (int j = 0; j < b; ++j) {
             const int64_t rj = (int64_t)gam[j].size();
+            if (rj == 0) continue;
             for (int h = 0; h < a; ++h) {
                 const std::vector<int32_t> &fin = Erho[h][b - 1];
-                const int64_t nf = (int64_t)fin.size();
-                if (rj == 0 || nf == 0) continue;
-                // MKR: 1 at elements of E_hj.rho inside E_hb.rho; CRZ zeros at the 0s
-                std::vector<int32_t> keep(nf, 0);
                 const std::vector<int32_t> &ej = Erho[h][j];
+                const int64_t nf = (int64_t)fin.size();
+                const bool stored = wM[j][h] == (int64_t)ej.size();  // else M_jh = 0
                 size_t q = 0;
-                for (int64_t t = 0; t < nf; ++t)
-                    if (q < ej.size() && ej[q] == fin[t]) {
-                        keep[t] = 1;
-                        ++q;
-                    }
-                std::vector<int32_t> zmask(nf);
-                for (int64_t t = 0; t < nf; ++t) zmask[t] = !keep[t];
-                DMat dst = sub(X, Mo, rowoff[j], rhooff[h], rj, nf);
-                if (wM[j][h] != (int64_t)ej.size()) {  // never stored: M_jh = 0
-                    j_zero(X, rj, nf, dst);
-                    continue;
+                int32_t z = 0;
+                for (int64_t t = 0; t < nf; ++t) {
+                    const bool keep = q < ej.size() && ej[q] == fin[t];
+                    if (keep) ++q;
+                    map[rhooff[h] + t] = (keep && stored) ? (int32_t)(ro[h] + z) : -1;
+                    if (keep) ++z;
                 }
-                DMat src = sub(X, Mp[j], 0, ro[h], rj, wM[j][h]);
-                j_cols(X, rj, nf, dst, src, crz_map(zmask));
             }
+            j_cols(X, rj, rank, sub(X, Mo, rowoff[j], 0, rj, rank), Mp[j], map);
         }
-        // K output: block row i, slot h (h <= i), zeros for h > i
+        // K output: block row i takes slot h's stored columns for h <= i,
+        // zeros for h > i; one column gather per i
         for (int i = 0; i < a; ++i) {
             const int64_t nk = kroff[i + 1] - kroff[i];
             if (nk == 0) continue;
-            for (int h = 0; h <= i; ++h) {
-                const int64_t nf = rhooff[h + 1] - rhooff[h];
-                DMat src = sub(X, Kp[i], 0, ro[h], nk, nf);
-                DMat dst = sub(X, Ko, kroff[i], rhooff[h], nk, nf);
-                j_copy(X, nk, nf, dst, src);
-            }
-            if (rank - rhooff[i + 1] > 0)
-                j_zero(X, nk, rank - rhooff[i + 1], sub(X, Ko, kroff[i], rhooff[i + 1], nk, rank - rhooff[i + 1]));
+            for (int h = 0; h < a; ++h)
+                for (int64_t t = rhooff[h]; t < rhooff[h + 1]; ++t)
+                    map[t] = h <= i ? (int32_t)(ro[h] + t - rhooff[h]) : -1;
+            j_cols(X, nk, rank, sub(X, Ko, kroff[i], 0, nk, rank), Kp[i], map);
         }
     }
 

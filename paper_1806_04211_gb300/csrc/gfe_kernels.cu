@@ -1113,14 +1113,6 @@ void zero2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd)
 // conversions at the API boundary (jobs "pack and partition", output assembly)
 // ---------------------------------------------------------------------------
 template <int C>
-__global__ void k_import_u8(int p, int64_t rows, int64_t cols, typename Cd<C>::T *dst, int64_t ldd,
-                            const uint8_t *src, int64_t lds) {
-    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
-        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += (int64_t)gridDim.x * blockDim.x)
-            dst[row * ldd + c] = Cd<C>::enc(cen(src[row * lds + c], p));
-}
-
-template <int C>
 __global__ void k_import_bits(int64_t rows, int64_t cols, typename Cd<C>::T *dst, int64_t ldd,
                               const uint64_t *src, int64_t ldw) {
     for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
@@ -1128,12 +1120,133 @@ __global__ void k_import_bits(int64_t rows, int64_t cols, typename Cd<C>::T *dst
             dst[row * ldd + c] = Cd<C>::enc((int)((src[row * ldw + (c >> 6)] >> (c & 63)) & 1u));
 }
 
+// GF(2) bits -> e4m3 (0 or 1.0 = 0x38): 16 columns per thread, 16-byte stores
+__global__ void k_import_bits_f8(int64_t rows, int64_t cols, uint8_t *dst, int64_t ldd, const uint64_t *src,
+                                 int64_t ldw) {
+    const int64_t nv = (cols + 15) >> 4;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        const uint64_t *sr = src + row * ldw;
+        uint8_t *dr = dst + row * ldd;
+        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t c0 = v << 4;  // a multiple of 16: inside one source word
+            const uint32_t bits = (uint32_t)(sr[c0 >> 6] >> (c0 & 63)) & 0xFFFFu;
+            uint32_t q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)  // nibble -> one flag per byte -> 0x38 per set byte
+                q[j] = ((((bits >> (4 * j)) & 0xFu) * 0x00204081u) & 0x01010101u) * 0x38u;
+            if (c0 + 16 <= cols && ((uintptr_t)(dr + c0) & 15) == 0) {
+                *(uint4 *)(dr + c0) = make_uint4(q[0], q[1], q[2], q[3]);
+            } else {
+                for (int j = 0; j < 16 && c0 + j < cols; ++j) dr[c0 + j] = (uint8_t)(q[j >> 2] >> (8 * (j & 3)));
+            }
+        }
+    }
+}
+
+// e4m3 GF(2) entries -> bits: a warp takes 512 columns of a row, lane l the
+// 16 bytes at 16 l (one 16-byte load), four lanes make one 64-bit word
+__global__ void k_export_bits_f8(int64_t rows, int64_t cols, uint64_t *dst, int64_t ldw, const uint8_t *src,
+                                 int64_t lds) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t nseg = (cols + 511) >> 9;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        const uint8_t *sr = src + row * lds;
+        for (int64_t seg = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); seg < nseg; seg += warps) {
+            const int64_t c0 = (seg << 9) + 16 * lane;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (c0 + 16 <= cols && ((uintptr_t)(sr + c0) & 15) == 0) {
+                const uint4 v = *(const uint4 *)(sr + c0);
+                w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+            } else {
+                for (int j = 0; j < 16 && c0 + j < cols; ++j) w[j >> 2] |= (uint32_t)sr[c0 + j] << (8 * (j & 3));
+            }
+            uint64_t bits = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {  // non-zero magnitude -> 1 (entries are 0 or 1.0)
+                const uint32_t nz = __vcmpne4(w[j] & 0x7F7F7F7Fu, 0u) & 0x01010101u;
+                bits |= (uint64_t)((nz * 0x10204080u) >> 28) << (4 * j);
+            }
+            bits <<= 16 * (lane & 3);
+            bits |= __shfl_xor_sync(0xffffffffu, bits, 1);
+            bits |= __shfl_xor_sync(0xffffffffu, bits, 2);
+            const int64_t wi = (seg << 3) + (lane >> 2);
+            if ((lane & 3) == 0 && (wi << 6) < cols) dst[row * ldw + wi] = bits;
+        }
+    }
+}
+
+// residues -> codec through a 256-entry table (enc(cen(x)) for every byte
+// value x), 16 bytes per thread
 template <int C>
-__global__ void k_export_u8(int p, int64_t rows, int64_t cols, uint8_t *dst, int64_t ldd,
-                            const typename Cd<C>::T *src, int64_t lds) {
-    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
-        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += (int64_t)gridDim.x * blockDim.x)
-            dst[row * ldd + c] = (uint8_t)res(Cd<C>::dec(src[row * lds + c]), p);
+__global__ void k_import_u8_vec(int p, int64_t rows, int64_t cols, typename Cd<C>::T *dst, int64_t ldd,
+                                const uint8_t *src, int64_t lds) {
+    using T = typename Cd<C>::T;
+    __shared__ T tab[256];
+    for (int x = threadIdx.x; x < 256; x += blockDim.x) tab[x] = Cd<C>::enc(cen(x, p));
+    __syncthreads();
+    const int64_t nv = (cols + 15) >> 4;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        const uint8_t *sr = src + row * lds;
+        T *dr = dst + row * ldd;
+        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t c0 = v << 4;
+            if (c0 + 16 <= cols && ((uintptr_t)(sr + c0) & 15) == 0 && ((uintptr_t)(dr + c0) & 15) == 0) {
+                const uint4 in = *(const uint4 *)(sr + c0);
+                const uint32_t w[4] = {in.x, in.y, in.z, in.w};
+                if constexpr (sizeof(T) == 1) {
+                    uint32_t o[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        o[j] = (uint32_t)tab[w[j] & 0xFF] | ((uint32_t)tab[(w[j] >> 8) & 0xFF] << 8) |
+                               ((uint32_t)tab[(w[j] >> 16) & 0xFF] << 16) | ((uint32_t)tab[w[j] >> 24] << 24);
+                    *(uint4 *)(dr + c0) = make_uint4(o[0], o[1], o[2], o[3]);
+                } else {
+                    uint32_t o[8];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        o[2 * j] = (uint32_t)tab[w[j] & 0xFF] | ((uint32_t)tab[(w[j] >> 8) & 0xFF] << 16);
+                        o[2 * j + 1] = (uint32_t)tab[(w[j] >> 16) & 0xFF] | ((uint32_t)tab[w[j] >> 24] << 16);
+                    }
+                    *(uint4 *)(dr + c0) = make_uint4(o[0], o[1], o[2], o[3]);
+                    *(uint4 *)(dr + c0 + 8) = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+            } else {
+                for (int j = 0; j < 16 && c0 + j < cols; ++j) dr[c0 + j] = tab[sr[c0 + j]];
+            }
+        }
+    }
+}
+
+// codec -> residues [0, p), 16 entries per thread
+template <int C>
+__global__ void k_export_u8_vec(int p, int64_t rows, int64_t cols, uint8_t *dst, int64_t ldd,
+                                const typename Cd<C>::T *src, int64_t lds) {
+    using T = typename Cd<C>::T;
+    const int64_t nv = (cols + 15) >> 4;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        const T *sr = src + row * lds;
+        uint8_t *dr = dst + row * ldd;
+        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t c0 = v << 4;
+            if (c0 + 16 <= cols && ((uintptr_t)(sr + c0) & 15) == 0 && ((uintptr_t)(dr + c0) & 15) == 0) {
+                T e[16];
+#pragma unroll
+                for (int j = 0; j < 16 * (int)sizeof(T); j += 16)
+                    *(uint4 *)((char *)e + j) = *(const uint4 *)((const char *)(sr + c0) + j);
+                uint32_t o[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    o[j] = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) o[j] |= (uint32_t)res(Cd<C>::dec(e[4 * j + b]), p) << (8 * b);
+                }
+                *(uint4 *)(dr + c0) = make_uint4(o[0], o[1], o[2], o[3]);
+            } else {
+                for (int j = 0; j < 16 && c0 + j < cols; ++j) dr[c0 + j] = (uint8_t)res(Cd<C>::dec(sr[c0 + j]), p);
+            }
+        }
+    }
 }
 
 template <int C>
@@ -1154,13 +1267,13 @@ __global__ void k_export_bits(int64_t rows, int64_t cols, uint64_t *dst, int64_t
 void import_u8(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
                const uint8_t *src, int64_t lds) {
     if (rows <= 0 || cols <= 0) return;
-    dim3 grid = grid_rc(rows, cols, 256);
+    const dim3 grid = grid_rc(rows, (cols + 15) / 16, 256);
     cudaEvent_t ev;
     prof_begin(L, K_CONV, &ev);
     if (L.codec == CODEC_F8)
-        k_import_u8<CODEC_F8><<<grid, 256, 0, L.st>>>(L.p, rows, cols, (uint8_t *)dst, ldd, src, lds);
+        k_import_u8_vec<CODEC_F8><<<grid, 256, 0, L.st>>>(L.p, rows, cols, (uint8_t *)dst, ldd, src, lds);
     else
-        k_import_u8<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, rows, cols, (uint16_t *)dst, ldd, src, lds);
+        k_import_u8_vec<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, rows, cols, (uint16_t *)dst, ldd, src, lds);
     prof_end(L, K_CONV, ev, 0, 0, rows, cols);
 }
 
@@ -1171,7 +1284,8 @@ void import_bits(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t
     cudaEvent_t ev;
     prof_begin(L, K_CONV, &ev);
     if (L.codec == CODEC_F8)
-        k_import_bits<CODEC_F8><<<grid, 256, 0, L.st>>>(rows, cols, (uint8_t *)dst, ldd, src, ldw);
+        k_import_bits_f8<<<grid_rc(rows, (cols + 15) / 16, 256), 256, 0, L.st>>>(rows, cols, (uint8_t *)dst, ldd,
+                                                                                 src, ldw);
     else
         k_import_bits<CODEC_BF16><<<grid, 256, 0, L.st>>>(rows, cols, (uint16_t *)dst, ldd, src, ldw);
     prof_end(L, K_CONV, ev, 0, 0, rows, cols);
@@ -1180,13 +1294,13 @@ void import_bits(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t
 void export_u8(const Launch &L, int64_t rows, int64_t cols, uint8_t *dst, int64_t ldd,
                const void *src, int64_t lds) {
     if (rows <= 0 || cols <= 0) return;
-    dim3 grid = grid_rc(rows, cols, 256);
+    const dim3 grid = grid_rc(rows, (cols + 15) / 16, 256);
     cudaEvent_t ev;
     prof_begin(L, K_CONV, &ev);
     if (L.codec == CODEC_F8)
-        k_export_u8<CODEC_F8><<<grid, 256, 0, L.st>>>(L.p, rows, cols, dst, ldd, (const uint8_t *)src, lds);
+        k_export_u8_vec<CODEC_F8><<<grid, 256, 0, L.st>>>(L.p, rows, cols, dst, ldd, (const uint8_t *)src, lds);
     else
-        k_export_u8<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, rows, cols, dst, ldd, (const uint16_t *)src, lds);
+        k_export_u8_vec<CODEC_BF16><<<grid, 256, 0, L.st>>>(L.p, rows, cols, dst, ldd, (const uint16_t *)src, lds);
     prof_end(L, K_CONV, ev, 0, 0, rows, cols);
 }
 
@@ -1199,7 +1313,8 @@ void export_bits(const Launch &L, int64_t rows, int64_t cols, uint64_t *dst, int
     cudaEvent_t ev;
     prof_begin(L, K_CONV, &ev);
     if (L.codec == CODEC_F8)
-        k_export_bits<CODEC_F8><<<grid, 128, 0, L.st>>>(rows, cols, dst, ldw, (const uint8_t *)src, lds);
+        k_export_bits_f8<<<grid_rc(rows, (cols + 511) / 512 * 32, 128), 128, 0, L.st>>>(rows, cols, dst, ldw,
+                                                                                         (const uint8_t *)src, lds);
     else
         k_export_bits<CODEC_BF16><<<grid, 128, 0, L.st>>>(rows, cols, dst, ldw, (const uint16_t *)src, lds);
     prof_end(L, K_CONV, ev, 0, 0, rows, cols);
