@@ -130,9 +130,9 @@ static void stream_release(int dev, cudaStream_t s) {
 // What one level of the Chief runs beside its ClearDown chain: a side stream
 // and the events that order the two (see chief()).
 struct Level {
-    cudaStream_t s1 = nullptr;
+    cudaStream_t s1 = nullptr, s2 = nullptr;
     cudaEvent_t start = nullptr, aa = nullptr, cd = nullptr, b = nullptr, e4[2] = {nullptr, nullptr},
-                join = nullptr;
+                join = nullptr, join2 = nullptr;
 };
 
 struct Ctx {
@@ -152,7 +152,10 @@ struct Ctx {
     std::vector<cudaEvent_t> owned_events;
 
     ~Ctx() {
-        for (auto &lv : levels) stream_release(dev, lv.s1);
+        for (auto &lv : levels) {
+            stream_release(dev, lv.s1);
+            stream_release(dev, lv.s2);
+        }
         for (cudaEvent_t e : owned_events) cudaEventDestroy(e);
     }
     cudaEvent_t make_event() {
@@ -166,7 +169,8 @@ struct Ctx {
         Level &lv = levels[d];
         if (!dry && !lv.s1) {
             lv.s1 = stream_acquire(dev);
-            if (!lv.s1) throw CudaError("cudaStreamCreate failed");
+            lv.s2 = stream_acquire(dev);
+            if (!lv.s1 || !lv.s2) throw CudaError("cudaStreamCreate failed");
             lv.start = make_event();
             lv.aa = make_event();
             lv.cd = make_event();
@@ -174,6 +178,7 @@ struct Ctx {
             lv.e4[0] = make_event();
             lv.e4[1] = make_event();
             lv.join = make_event();
+            lv.join2 = make_event();
         }
         return lv;
     }
@@ -196,8 +201,10 @@ struct Ctx {
         if (dry) return;
         const double t0 = now_ms();
         check(cudaStreamSynchronize(main_st), "cudaStreamSynchronize");
-        for (auto &lv : levels)
+        for (auto &lv : levels) {
             if (lv.s1) check(cudaStreamSynchronize(lv.s1), "cudaStreamSynchronize");
+            if (lv.s2) check(cudaStreamSynchronize(lv.s2), "cudaStreamSynchronize");
+        }
         check(cudaGetLastError(), "kernel launch");
         sg.top = 0;
         ++syncs;
@@ -429,26 +436,29 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     // ---- streams ----
     // The ClearDown chain is the critical path.  It runs on the caller's
     // stream s0 together with UpdateRow on the near columns (block column
-    // j+1, which the next ClearDown reads).  UpdateRow on the far columns
-    // (j+2 onwards) and all of UpdateRowTrafo run on the side stream s1
-    // meanwhile.  Events order the two:
-    //   aa       s0 -> s1   A.A of step t is ready (UpdateRow (1) may start)
-    //   cd       s0 -> s1   ClearDown of step t is done (A.M, A.K, A.E)
-    //   b        s1 -> s0   step t's far columns are done; step t+1's near
-    //                       columns are among them
-    //   e4[t&1]  s1 -> s0   step t's UpdateRowTrafo is done; A.A, A.M, A.K
-    //                       and A.E are double-buffered by step parity, so
-    //                       ClearDown of step t+2 may then overwrite them
-    //   join     s1 -> s0   end of Step 1
-    // A nested Chief (the ECH of a large block) runs on s0 with a side stream
-    // of its own and joins it before it returns.
+    // j+1, which the next ClearDown reads).  Meanwhile UpdateRow on the far
+    // columns (j+2 onwards) runs on side stream s1 and UpdateRowTrafo on
+    // side stream s2 (they share no output).  Events order them:
+    //   aa       s0 -> s1,s2  A.A of step t is ready (steps (1) may start)
+    //   cd       s0 -> s1,s2  ClearDown of step t is done (A.M, A.K, A.E)
+    //   b        s1 -> s0     step t's far columns are done; step t+1's near
+    //                         columns are among them (and s1 is then done
+    //                         with step t-1's copies of A.A, A.M, A.K, A.E)
+    //   e4[t&1]  s2 -> s0     step t's UpdateRowTrafo is done; A.A, A.M, A.K
+    //                         and A.E are double-buffered by step parity, so
+    //                         ClearDown of step t+2 may then overwrite them
+    //   join     s1,s2 -> s0  end of Step 1
+    // A nested Chief (the ECH of a large block) runs on s0 with side streams
+    // of its own and joins them before it returns.
     const cudaStream_t s0 = X.L.st;
     const Level lv = X.level(X.depth);
-    const cudaStream_t s1 = lv.s1;
+    const cudaStream_t s1 = lv.s1, s2 = lv.s2;
     ++X.depth;
     auto on = [&](cudaStream_t s) { X.L.st = s; };
     X.signal(lv.start);
     on(s1);
+    X.await(lv.start);
+    on(s2);
     X.await(lv.start);
     on(s0);
 
@@ -569,7 +579,7 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                     ur1_done = true;
                 }
                 if (trafo) {
-                    on(s1);
+                    on(s2);
                     X.await(lv.aa);
                     for (int h = 0; h < i; ++h) {
                         const std::vector<int32_t> &del = Edel[h][j];
@@ -647,8 +657,8 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
             }
             cur[i] = al - rp;
             rB[j] = r + rp;
-            // ---------- Task UpdateRowTrafo for h = 1..i (side stream) ----------
-            on(s1);
+            // ---------- Task UpdateRowTrafo for h = 1..i (side stream s2) ----------
+            on(s2);
             X.await(lv.cd);
             if (trafo && (rp > 0 || i > 0)) {
                 for (int h = 0; h <= i; ++h) {
@@ -714,8 +724,11 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     }
     on(s1);
     X.signal(lv.join);
+    on(s2);
+    X.signal(lv.join2);
     on(s0);
     X.await(lv.join);
+    X.await(lv.join2);
     --X.depth;
 
     // ---- results: rank, Upsilon, varrho, offsets ----

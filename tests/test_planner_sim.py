@@ -171,3 +171,46 @@ def test_planner_sim_detects_a_planted_race(sim):
     sim.cudaStreamWaitEvent(s2, ev, 0)
     cp(buf.ctypes.data, src.ctypes.data, 64, 3, s2)
     assert races(sim) == 0
+
+
+def test_batch_matches_oracle_without_races(sim):
+    """gfe_batch_echelon: two workers, each on its own stream with its own
+    side streams and workspace slice, fenced to the caller's stream."""
+    assert sim.gfe_set_batch_workers(2) == 0
+    rng = np.random.RandomState(5)
+    mats = [(rng.randint(0, p, (rng.randint(1, 150), rng.randint(1, 150))).astype(np.uint8), p)
+            for p in [3, 5, 7, 251, 2, 3, 11, 13]]
+    args, outs, keep = [], [], []
+    for A, p in mats:
+        m, n = A.shape
+        sim.sim_register(A.ctypes.data, A.nbytes)
+        mn = min(m, n)
+        rank = np.zeros(1, np.int64)
+        pc = np.zeros(max(mn, 1), np.int64)
+        pr = np.zeros(max(mn, 1), np.int64)
+        R = np.zeros((max(mn, 1), max(n, 1)), np.uint8)
+        M = np.zeros((max(mn, 1), max(mn, 1)), np.uint8)
+        K = np.zeros((max(m, 1), max(mn, 1)), np.uint8)
+        for a in (rank, pc, pr, R, M, K):
+            sim.sim_register(a.ctypes.data, a.nbytes)
+        keep.append((rank, pc, pr, R, M, K))
+        args.append(gfe.GfeMatrix(p, m, n, 0, A.ctypes.data, A.strides[0]))
+        outs.append(gfe.GfeResult(rank.ctypes.data, pc.ctypes.data, pr.ctypes.data, R.ctypes.data, R.strides[0],
+                                  M.ctypes.data, M.strides[0], K.ctypes.data, K.strides[0], None, 0, None, 0))
+    arr = (gfe.GfeMatrix * len(args))(*args)
+    res = (gfe.GfeResult * len(args))(*outs)
+    need = ctypes.c_size_t(0)
+    assert sim.gfe_query_batch_workspace(arr, len(args), 1, ctypes.byref(need)) == 0
+    ws = np.zeros(need.value, np.uint8)
+    sim.sim_register(ws.ctypes.data, ws.nbytes)
+    assert sim.gfe_batch_echelon(arr, res, len(args), 1, ws.ctypes.data, ws.nbytes, None) == 0, sim.gfe_last_error()
+    for (A, p), (rank, pc, pr, R, M, K) in zip(mats, keep):
+        ref = O.echelon(A, p)
+        r = ref["rank"]
+        m, n = A.shape
+        assert int(rank[0]) == r
+        assert np.array_equal(pr[:r], ref["rho"]) and np.array_equal(pc[:r], ref["ups"])
+        assert np.array_equal(M[:r, :r], ref["M"]) and np.array_equal(K[:m - r, :r], ref["K"])
+        assert np.array_equal(R[:r, :n - r], ref["R"])
+    assert races(sim) == 0
+    sim.gfe_set_batch_workers(0)
