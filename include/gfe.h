@@ -201,13 +201,22 @@ gfe_status gfe_mad_noalloc(int32_t p, int64_t m, int64_t n, int64_t k,
  * whose larger side exceeds `threshold` is split into square blocks of side
  * `block`; smaller ones into leaf blocks of at most 1024 rows x 64 columns
  * (256 columns for GF(2)), which the one-CTA ECH kernel echelonises.
- * Defaults: 2048, 2048; a value <= 0 selects its default.  GFE_EINVAL
- * (policy unchanged) unless block <= threshold.  Blocks that are multiples
- * of 64 keep every operand aligned for the tensor-core path (others fall
- * back to the plain multiply-add where misaligned).  Process wide.  Results
- * never depend on it.
+ * threshold <= 0 and block <= 0 (the default): both equal gfe_auto_block of
+ * the call's field and shape.  One of them <= 0: it takes the other's value.
+ * GFE_EINVAL (policy unchanged) unless block <= threshold.  Blocks that are
+ * multiples of 64 keep every operand aligned for the tensor-core path
+ * (others fall back to the plain multiply-add where misaligned).  Process
+ * wide.  Results never depend on it.
  */
 gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);
+
+/* The block side the default policy uses for an m x n matrix over GF(p):
+ * a table measured on GB300 (GF(2): 2048 below max(m, n) = 12288, 3072 up to
+ * 65536, 6144 above; p > 2: 2048).  The Python autotuner
+ * (paper_1806_04211_gb300.gfe.autotune_block) times candidates on a seeded
+ * matrix of the caller's shape and sets the winner with
+ * gfe_set_block_policy. */
+int64_t gfe_auto_block(int32_t p, int64_t m, int64_t n);
 
 /* Kernel profile of the calls made since the last reset (all streams).
  * While enabled every launch is counted; launches of the kinds selected by

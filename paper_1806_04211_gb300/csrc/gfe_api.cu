@@ -511,7 +511,11 @@ gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k, const uint8_t *W,
 }
 
 gfe_status gfe_set_block_policy(int64_t threshold, int64_t block) {
-    const int64_t t = threshold > 0 ? threshold : 2048, b = block > 0 ? block : 2048;
+    if (threshold <= 0 && block <= 0) {  // back to the measured table
+        g_block_threshold = g_block_big = 0;
+        return GFE_OK;
+    }
+    const int64_t t = threshold > 0 ? threshold : block, b = block > 0 ? block : threshold;
     // a block must itself be echelonised from leaves (b <= t), else the
     // split would recurse without end
     if (t < b) return (set_error("block policy needs block <= threshold"), GFE_EINVAL);
@@ -519,6 +523,8 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block) {
     g_block_big = b;
     return GFE_OK;
 }
+
+int64_t gfe_auto_block(int32_t p, int64_t m, int64_t n) { return auto_block(p, m, n); }
 
 gfe_status gfe_selftest_wait_timeout(int64_t limit_us, void *stream) {
     if (limit_us < 1 || limit_us > 10000000) return (set_error("limit_us out of range"), GFE_EINVAL);

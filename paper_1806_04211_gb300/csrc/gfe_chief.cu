@@ -146,6 +146,7 @@ struct Ctx {
     int es = 1;
     int64_t syncs = 0;
     int dev = 0;
+    int64_t thr = 2048, blk = 2048;  // block policy of this run
     cudaStream_t main_st = nullptr;  // the caller's stream
     int depth = 0;                 // nesting depth of the Chief being planned
     std::vector<Level> levels;     // per depth, made on first use
@@ -358,15 +359,28 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
 // to the one-CTA kernel; larger blocks are split by the Chief itself, which
 // is the paper's recursive scheme with a general rather than 2-way split.
 // ---------------------------------------------------------------------------
-int64_t g_block_threshold = 2048, g_block_big = 2048;
+// 0, 0: the block side comes from auto_block; otherwise it was fixed by
+// gfe_set_block_policy
+int64_t g_block_threshold = 0, g_block_big = 0;
 
-static void block_policy(int p, int64_t alpha, int64_t beta, std::vector<int64_t> &a, std::vector<int64_t> &b) {
+// Top-level block side (the a_i, b_j of Section 3.1) by field and size,
+// from sweeps of the C2/C3 workloads on GB300: GF(2) is fastest with 3072
+// from n ~ 12288 and 6144 from n ~ 65536, larger p with 2048.  Sides are
+// multiples of the 1024-row leaf; ragged ones (2560, 3584) were slower.
+int64_t auto_block(int p, int64_t m, int64_t n) {
+    const int64_t s = std::max(m, n);
+    if (p == 2) return s >= 65536 ? 6144 : (s >= 12288 ? 3072 : 2048);
+    return 2048;
+}
+
+static void block_policy(const Ctx &X, int64_t alpha, int64_t beta, std::vector<int64_t> &a,
+                         std::vector<int64_t> &b) {
     int64_t ra, cb;
-    if (std::max(alpha, beta) <= g_block_threshold) {
+    if (std::max(alpha, beta) <= X.thr) {
         ra = ECH_LEAF_ROWS;
-        cb = ech_leaf_cols(p);
+        cb = ech_leaf_cols(X.L.p);
     } else {
-        ra = cb = g_block_big;
+        ra = cb = X.blk;
     }
     a.clear();
     b.clear();
@@ -398,7 +412,7 @@ static void ech_start(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, con
         return;
     }
     std::vector<int64_t> a, b;
-    block_policy(X.L.p, alpha, beta, a, b);
+    block_policy(X, alpha, beta, a, b);
     chief(X, H, a, b, true, true, Mo, Ko, Ro, out);
 }
 
@@ -852,9 +866,6 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
 // ---------------------------------------------------------------------------
 // entry used by the C ABI
 // ---------------------------------------------------------------------------
-static void top_blocks(int p, int64_t m, int64_t n, std::vector<int64_t> &a, std::vector<int64_t> &b) {
-    block_policy(p, m, n, a, b);
-}
 
 // Runs the method on the (already imported) internal matrix H.
 // Mo/Ko/Ro sized min(m,n) x min(m,n), m x min(m,n), min(m,n) x n.
@@ -892,8 +903,15 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
         X.check(cudaEventCreateWithFlags(&evg.e, cudaEventDisableTiming), "cudaEventCreate");
         X.ev = evg.e;
     }
+    // one block side for the whole run (nested blocks of that side become leaves)
+    if (g_block_threshold > 0) {
+        X.thr = g_block_threshold;
+        X.blk = g_block_big;
+    } else {
+        X.thr = X.blk = auto_block(L.p, H.rows, H.cols);
+    }
     std::vector<int64_t> a, b;
-    top_blocks(L.p, H.rows, H.cols, a, b);
+    block_policy(X, H.rows, H.cols, a, b);
     EchRes e;
     const double t0 = Ctx::now_ms();
     if (H.rows > 0 && H.cols > 0) chief(X, H, a, b, trafo, wantR, Mo, Ko, Ro, e);

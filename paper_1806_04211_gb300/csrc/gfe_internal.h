@@ -118,6 +118,7 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
                int64_t *syncs);
 
 extern int64_t g_block_threshold, g_block_big;
+int64_t auto_block(int p, int64_t m, int64_t n);
 
 // ---- error state (gfe_api.cu) ----
 void set_error(const std::string &s);

@@ -74,6 +74,7 @@ SIGNATURES = {
     "gfe_mad_noalloc": (_i32, [_i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_uint32,
                                _vp]),
     "gfe_set_block_policy": (_i32, [_i64, _i64]),
+    "gfe_auto_block": (_i64, [_i32, _i64, _i64]),
     "gfe_profile_enable": (_i32, [_i32]),
     "gfe_profile_read": (_i32, [ctypes.POINTER(GfeProfile), _i32]),
     "gfe_trace_enable": (_i32, [_i64]),
@@ -325,8 +326,40 @@ def mad_noalloc(W, A: torch.Tensor, B: torch.Tensor, p: int, out: torch.Tensor, 
 
 
 def set_block_policy(threshold: int = 0, block: int = 0):
-    """Block partition policy (gfe_set_block_policy); 0, 0 = defaults."""
+    """Block partition policy (gfe_set_block_policy); 0, 0 = the measured
+    table (gfe_auto_block)."""
     _check(lib().gfe_set_block_policy(threshold, block))
+
+
+def auto_block(p: int, m: int, n: int) -> int:
+    """Block side the default policy uses for an m x n matrix over GF(p)."""
+    return int(lib().gfe_auto_block(p, m, n))
+
+
+def autotune_block(p: int, m: int, n: int, candidates=(2048, 3072, 4096), rank=None, device="cuda:0",
+                   reps: int = 2, seed: int = 1) -> dict:
+    """Times gfe_echelon on a seeded synthetic m x n matrix over GF(p) (rank
+    `rank`, None = uniform) with each candidate block side, sets the fastest
+    with gfe_set_block_policy and returns {side: seconds}."""
+    import time
+    from . import synth
+    A = synth.matrix(p, m, n, seed=seed, rank=rank, device=device)
+    kw = dict(n=n) if p == 2 else {}
+    times = {}
+    for blk in candidates:
+        set_block_policy(blk, blk)
+        echelon(A, p, **kw)
+        torch.cuda.synchronize(device)
+        best = float("inf")
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            echelon(A, p, **kw)
+            torch.cuda.synchronize(device)
+            best = min(best, time.perf_counter() - t0)
+        times[blk] = best
+    winner = min(times, key=times.get)
+    set_block_policy(winner, winner)
+    return times
 
 
 def profile_enable(on: bool = True, kinds=None):

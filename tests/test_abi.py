@@ -86,4 +86,18 @@ def test_block_policy_validation():
             gfe.set_block_policy(thr, blk)
     gfe.set_block_policy(4096, 4096)
     gfe.set_block_policy(40, 16)
+    gfe.set_block_policy(3072, 0)   # one side given: the other takes its value
     gfe.set_block_policy()
+
+
+def test_auto_block_table():
+    """The default policy's measured table: GF(2) grows with the size, larger
+    fields keep 2048; every side is a multiple of the 1024-row leaf."""
+    assert gfe.auto_block(2, 8192, 8192) == 2048
+    assert gfe.auto_block(2, 32768, 32768) == 3072
+    assert gfe.auto_block(2, 100000, 100000) == 6144
+    assert gfe.auto_block(7, 32768, 32768) == 2048
+    assert gfe.auto_block(251, 20000, 50000) == 2048
+    for p in (2, 3, 251):
+        for n in (100, 5000, 20000, 70000, 200000):
+            assert gfe.auto_block(p, n, n) % 1024 == 0

@@ -88,6 +88,21 @@ def test_parity_recursive_chief(p, m, n, rank):
         compare_u8(A, p, gfe.echelon(A.to(DEV), p), ref)
 
 
+@pytest.mark.parametrize("p,m,n,rank,blk", [(2, 4000, 7000, None, 3072), (2, 7000, 3500, 2500, 3072),
+                                            (7, 3300, 700, None, 3072)])
+def test_parity_block_3072(p, m, n, rank, blk):
+    """The 3072-wide top-level blocks the default policy picks for large GF(2)
+    inputs (three leaf row blocks per block), on sizes the oracle finishes."""
+    gfe.set_block_policy(blk, blk)
+    A = synth.matrix(p, m, n, seed=12, rank=rank)
+    if p == 2:
+        ref = O.echelon_gf2(A.numpy(), m, n)
+        compare_gf2(gfe.echelon(A.to(DEV), 2, n=n), ref, m, n)
+    else:
+        ref = O.echelon(A.numpy(), p)
+        compare_u8(A, p, gfe.echelon(A.to(DEV), p), ref)
+
+
 @pytest.mark.parametrize("p", [3, 251])
 def test_dense_E_T(p):
     A = synth.matrix(p, 150, 170, seed=2, rank=100)
