@@ -218,6 +218,11 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);
  * gfe_set_block_policy. */
 int64_t gfe_auto_block(int32_t p, int64_t m, int64_t n);
 
+/* Rows of a leaf block in the planner's leaf grid (the ECH kernel takes at
+ * most 1024): 1..1024, or 0 for the default (1024).  Process wide.  Results
+ * never depend on it.  GFE_EINVAL outside [0, 1024]. */
+gfe_status gfe_set_leaf_rows(int64_t rows);
+
 /* Kernel profile of the calls made since the last reset (all streams).
  * While enabled every launch is counted; launches of the kinds selected by
  * the mask (bit k = kind k, -1 = all) are also timed with CUDA events

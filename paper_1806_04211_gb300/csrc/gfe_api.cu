@@ -193,12 +193,12 @@ static void launch_for(const gfe_matrix *A, uint32_t flags, void *stream, Launch
 // The workspace need depends only on the field (its codec and leaf width),
 // the shape, the two flags and the block policy; the planner's dry run that
 // finds it walks the whole block schedule, so its answers are memoised.
-using QueryKey = std::tuple<int, int64_t, int64_t, bool, bool, int64_t, int64_t>;
+using QueryKey = std::tuple<int, int64_t, int64_t, bool, bool, int64_t, int64_t, int64_t>;
 static std::mutex g_query_mu;
 static std::map<QueryKey, size_t> g_query_memo;
 
 static gfe_status query(const gfe_matrix *A, bool trafo, bool wantR, size_t *ws) {
-    const QueryKey key{A->p, A->m, A->n, trafo, wantR, g_block_threshold, g_block_big};
+    const QueryKey key{A->p, A->m, A->n, trafo, wantR, g_block_threshold, g_block_big, g_leaf_rows};
     {
         std::lock_guard<std::mutex> g(g_query_mu);
         auto it = g_query_memo.find(key);
@@ -525,6 +525,12 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block) {
 }
 
 int64_t gfe_auto_block(int32_t p, int64_t m, int64_t n) { return auto_block(p, m, n); }
+
+gfe_status gfe_set_leaf_rows(int64_t rows) {
+    if (rows < 0 || rows > ECH_LEAF_ROWS) return (set_error("leaf rows must be in [0, 1024]"), GFE_EINVAL);
+    g_leaf_rows = rows;
+    return GFE_OK;
+}
 
 gfe_status gfe_selftest_wait_timeout(int64_t limit_us, void *stream) {
     if (limit_us < 1 || limit_us > 10000000) return (set_error("limit_us out of range"), GFE_EINVAL);

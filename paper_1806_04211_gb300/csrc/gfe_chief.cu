@@ -147,6 +147,7 @@ struct Ctx {
     int64_t syncs = 0;
     int dev = 0;
     int64_t thr = 2048, blk = 2048;  // block policy of this run
+    int64_t leaf_rows = ECH_LEAF_ROWS;
     cudaStream_t main_st = nullptr;  // the caller's stream
     int depth = 0;                 // nesting depth of the Chief being planned
     std::vector<Level> levels;     // per depth, made on first use
@@ -362,6 +363,15 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
 // 0, 0: the block side comes from auto_block; otherwise it was fixed by
 // gfe_set_block_policy
 int64_t g_block_threshold = 0, g_block_big = 0;
+// rows of a leaf block in the leaf grid; 0: auto_leaf_rows
+int64_t g_leaf_rows = 0;
+
+int64_t auto_leaf_rows(int p, int64_t m, int64_t n) {
+    (void)p;
+    (void)m;
+    (void)n;
+    return ECH_LEAF_ROWS;
+}
 
 // Top-level block side (the a_i, b_j of Section 3.1) by field and size,
 // from sweeps of the C2/C3 workloads on GB300: GF(2) is fastest with 3072
@@ -377,7 +387,7 @@ static void block_policy(const Ctx &X, int64_t alpha, int64_t beta, std::vector<
                          std::vector<int64_t> &b) {
     int64_t ra, cb;
     if (std::max(alpha, beta) <= X.thr) {
-        ra = ECH_LEAF_ROWS;
+        ra = X.leaf_rows;
         cb = ech_leaf_cols(X.L.p);
     } else {
         ra = cb = X.blk;
@@ -910,6 +920,7 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
     } else {
         X.thr = X.blk = auto_block(L.p, H.rows, H.cols);
     }
+    X.leaf_rows = g_leaf_rows > 0 ? g_leaf_rows : auto_leaf_rows(L.p, H.rows, H.cols);
     std::vector<int64_t> a, b;
     block_policy(X, H.rows, H.cols, a, b);
     EchRes e;

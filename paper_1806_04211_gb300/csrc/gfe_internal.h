@@ -117,7 +117,8 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
                const DMat &Mo, const DMat &Ko, const DMat &Ro, TopResult &res, size_t *peak, size_t base_used,
                int64_t *syncs);
 
-extern int64_t g_block_threshold, g_block_big;
+extern int64_t g_block_threshold, g_block_big, g_leaf_rows;
+int64_t auto_leaf_rows(int p, int64_t m, int64_t n);
 int64_t auto_block(int p, int64_t m, int64_t n);
 
 // ---- error state (gfe_api.cu) ----

@@ -75,6 +75,7 @@ SIGNATURES = {
                                _vp]),
     "gfe_set_block_policy": (_i32, [_i64, _i64]),
     "gfe_auto_block": (_i64, [_i32, _i64, _i64]),
+    "gfe_set_leaf_rows": (_i32, [_i64]),
     "gfe_profile_enable": (_i32, [_i32]),
     "gfe_profile_read": (_i32, [ctypes.POINTER(GfeProfile), _i32]),
     "gfe_trace_enable": (_i32, [_i64]),
@@ -329,6 +330,11 @@ def set_block_policy(threshold: int = 0, block: int = 0):
     """Block partition policy (gfe_set_block_policy); 0, 0 = the measured
     table (gfe_auto_block)."""
     _check(lib().gfe_set_block_policy(threshold, block))
+
+
+def set_leaf_rows(rows: int = 0):
+    """Rows of a leaf block in the planner's leaf grid (gfe_set_leaf_rows); 0 = default."""
+    _check(lib().gfe_set_leaf_rows(rows))
 
 
 def auto_block(p: int, m: int, n: int) -> int:
