@@ -86,7 +86,8 @@ static char *stage_acquire() {
         }
     }
     char *p = nullptr;
-    if (cudaHostAlloc((void **)&p, STAGE_BYTES + 4096, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+    // mapped: the leaf ECH writes its pivot sets straight into the first 4 KB
+    if (cudaHostAlloc((void **)&p, STAGE_BYTES + 4096, cudaHostAllocMapped) != cudaSuccess) return nullptr;
     return p;
 }
 
@@ -127,6 +128,33 @@ static void stream_release(int dev, cudaStream_t s) {
     g_stream_free.push_back({dev, s});
 }
 
+// the critical path's stream: the device's highest priority, so its CTAs are
+// scheduled before the side streams' when SMs come free
+static std::vector<std::pair<int, cudaStream_t>> g_hp_free;
+
+static cudaStream_t hp_acquire(int dev) {
+    {
+        std::lock_guard<std::mutex> g(g_stream_mu);
+        for (size_t q = 0; q < g_hp_free.size(); ++q)
+            if (g_hp_free[q].first == dev) {
+                cudaStream_t s = g_hp_free[q].second;
+                g_hp_free.erase(g_hp_free.begin() + q);
+                return s;
+            }
+    }
+    int least = 0, greatest = 0;
+    cudaStream_t s = nullptr;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return nullptr;
+    if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) != cudaSuccess) return nullptr;
+    return s;
+}
+
+static void hp_release(int dev, cudaStream_t s) {
+    if (!s) return;
+    std::lock_guard<std::mutex> g(g_stream_mu);
+    g_hp_free.push_back({dev, s});
+}
+
 // What one level of the Chief runs beside its ClearDown chain: a side stream
 // and the events that order the two (see chief()).
 struct Level {
@@ -140,7 +168,7 @@ struct Ctx {
     Arena ar;
     Stage sg;
     char *pinned = nullptr;  // download area (first 4 KB of the staging buffer)
-    int32_t *info = nullptr;    // device result word of the leaf ECH
+    int32_t *info = nullptr;    // the same area as the device sees it: the leaf ECH's result
     cudaEvent_t ev = nullptr;   // marks the download of the leaf's result
     bool dry = false;
     int es = 1;
@@ -277,15 +305,24 @@ static void j_mad(Ctx &X, int64_t m, int64_t n, int64_t k, const DMat *W, const 
     if (X.dry || m <= 0 || n <= 0) return;
     mad(X.L, m, n, k, W ? W->ptr : nullptr, W ? W->ld : 0, A.ptr, A.ld, B.ptr, B.ld, C.ptr, C.ld);
 }
+// an index array for a launch: short ones go by value with the launch,
+// longer ones through the upload ring
+static IdxMap idx(Ctx &X, const std::vector<int32_t> &v) {
+    IdxMap m;
+    m.n = (int64_t)v.size();
+    if (m.n <= MAP_INLINE) m.host = v.data();
+    else m.dev = X.put(v);
+    return m;
+}
 static void j_rows(Ctx &X, int64_t nrows, int64_t ncols, const DMat &dst, const DMat &A, const DMat *B,
                    const std::vector<int32_t> &map) {
     if (X.dry || nrows <= 0 || ncols <= 0) return;
-    gather_rows(X.L, nrows, ncols, dst.ptr, dst.ld, A.ptr, A.ld, B ? B->ptr : nullptr, B ? B->ld : 0, X.put(map));
+    gather_rows(X.L, nrows, ncols, dst.ptr, dst.ld, A.ptr, A.ld, B ? B->ptr : nullptr, B ? B->ld : 0, idx(X, map));
 }
 static void j_cols(Ctx &X, int64_t nrows, int64_t ncols, const DMat &dst, const DMat &src,
                    const std::vector<int32_t> &map) {
     if (X.dry || nrows <= 0 || ncols <= 0) return;
-    gather_cols(X.L, nrows, ncols, dst.ptr, dst.ld, src.ptr, src.ld, X.put(map));
+    gather_cols(X.L, nrows, ncols, dst.ptr, dst.ld, src.ptr, src.ld, idx(X, map));
 }
 static void j_copy(Ctx &X, int64_t rows, int64_t cols, const DMat &dst, const DMat &src) {
     if (X.dry || rows <= 0 || cols <= 0) return;
@@ -412,10 +449,9 @@ static void ech_start(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, con
     const int lc = ech_leaf_cols(X.L.p);
     if (alpha <= ECH_LEAF_ROWS && beta <= lc) {
         if (!X.dry) {
+            // the kernel writes (r, rho, gamma) into mapped host memory; the
+            // event after it makes them visible to the host
             ech_leaf(X.L, alpha, beta, H.ptr, H.ld, X.info, Mo.ptr, Mo.ld, Ko.ptr, Ko.ld, Ro.ptr, Ro.ld);
-            X.check(cudaMemcpyAsync(X.pinned, X.info, sizeof(int32_t) * (1 + 2 * lc), cudaMemcpyDeviceToHost,
-                                    X.L.st),
-                    "download");
             X.record();
             pending = true;
         }
@@ -478,7 +514,13 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     const Level lv = X.level(X.depth);
     const cudaStream_t s1 = lv.s1, s2 = lv.s2;
     ++X.depth;
-    auto on = [&](cudaStream_t s) { X.L.st = s; };
+    // side-stream multiply-adds take at most SIDE_TILES tiles per CTA, so the
+    // ClearDown chain (on a higher-priority stream) gets SMs as tiles finish
+    constexpr int SIDE_TILES = 4;
+    auto on = [&](cudaStream_t s) {
+        X.L.st = s;
+        X.L.tiles_per_cta = s == s0 ? 0 : SIDE_TILES;
+    };
     X.signal(lv.start);
     on(s1);
     X.await(lv.start);
@@ -720,8 +762,10 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                     } else {
                         DMat Vv = sub(X, VWt, 0, 0, rp, nc), Ww = sub(X, VWt, rp, 0, al - rp, nc);
                         j_rows(X, al, nc, VWt, Zz, nullptr, rex);          // (2) REX
-                        if (h == i && !X.dry)                              // (+) ADI
-                            set_ones(X.L, rp, Vv.ptr, Vv.ld, X.put(ones_positions(del)));
+                        if (h == i && !X.dry) {                            // (+) ADI
+                            const std::vector<int32_t> pos = ones_positions(del);
+                            set_ones(X.L, rp, Vv.ptr, Vv.ld, idx(X, pos));
+                        }
                         j_mad(X, rp, nc, rp, nullptr, AM[q], Vv, Xx);      // (3) X := A.M x V
                         j_mad(X, al - rp, nc, rp, &Ww, AK[q], Vv, Kih);    // (6) K := W + A.K x V
                     }
@@ -902,16 +946,33 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
         X.sg.host = guard.p + 4096;
     }
     X.sg.dev = (char *)X.ar.alloc(STAGE_BYTES);
-    X.info = (int32_t *)X.ar.alloc(sizeof(int32_t) * (1 + 2 * ECH_LEAF_COLS_GF2));
+    if (!dry) {
+        void *dinfo = nullptr;
+        X.check(cudaHostGetDevicePointer(&dinfo, X.pinned, 0), "cudaHostGetDevicePointer");
+        X.info = (int32_t *)dinfo;
+    }
     struct EvGuard {
         cudaEvent_t e = nullptr;
         ~EvGuard() {
             if (e) cudaEventDestroy(e);
         }
     } evg;
+    // the critical path runs on a high-priority stream of our own, after the
+    // work already queued on the caller's stream
+    struct HpGuard {
+        int dev = 0;
+        cudaStream_t s = nullptr;
+        ~HpGuard() { hp_release(dev, s); }
+    } hpg;
     if (!dry) {
         X.check(cudaEventCreateWithFlags(&evg.e, cudaEventDisableTiming), "cudaEventCreate");
         X.ev = evg.e;
+        hpg.dev = X.dev;
+        hpg.s = hp_acquire(X.dev);
+        if (!hpg.s) throw CudaError("cudaStreamCreateWithPriority failed");
+        X.check(cudaEventRecord(X.ev, L.st), "cudaEventRecord");
+        X.check(cudaStreamWaitEvent(hpg.s, X.ev, 0), "cudaStreamWaitEvent");
+        X.L.st = X.main_st = hpg.s;
     }
     // one block side for the whole run (nested blocks of that side become leaves)
     if (g_block_threshold > 0) {

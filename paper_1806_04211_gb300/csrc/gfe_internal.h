@@ -37,6 +37,10 @@ struct Launch {  // per-call launch context
     int p = 0;
     Codec codec = CODEC_F8;
     int impl = 0;  // 0 tensor cores, 1 plain CUDA-core multiply-add
+    // tensor-core multiply-add: 0 = one persistent CTA per SM; k > 0 = enough
+    // CTAs that none takes more than k tiles, so SMs come free for other
+    // (higher-priority) streams every few tiles
+    int tiles_per_cta = 0;
 };
 
 // ---- profiling (gfe_api.cu) ----
@@ -72,18 +76,28 @@ int ech_leaf_cols(int p);
 void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64_t ldh,
               int32_t *info, void *M, int64_t ldm, void *K, int64_t ldk, void *R, int64_t ldr);
 
+// An index array for a gather: a device copy, or, when it has at most
+// MAP_INLINE entries, the host array itself, which is then passed by value
+// with the launch (no separate upload on the stream).
+constexpr int MAP_INLINE = 2048;
+struct IdxMap {
+    const int32_t *dev = nullptr;   // device array (any length)
+    const int32_t *host = nullptr;  // host array, n <= MAP_INLINE (takes precedence)
+    int64_t n = 0;
+};
+
 // dst row t = map[t] >= 0 ? A row map[t] : B row (-1 - map[t])   (B may be null if unused)
 void gather_rows(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
-                 const void *A, int64_t lda, const void *B, int64_t ldb, const int32_t *map);
+                 const void *A, int64_t lda, const void *B, int64_t ldb, const IdxMap &map);
 // dst col t = map[t] >= 0 ? src col map[t] : 0
 void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
-                 const void *src, int64_t lds, const int32_t *map);
+                 const void *src, int64_t lds, const IdxMap &map);
 // dst[t][c] = map[c] >= 0 ? rows[t][map[c]] : 0, rows[] a device array of row
 // start pointers (gathers from several matrices in one launch)
 void gather_rowptr(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
                    const uint64_t *rows, const int32_t *map);
 // V[t][pos[t]] := 1 for t < count (job ADI)
-void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const int32_t *pos);
+void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const IdxMap &pos);
 void copy2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd,
             const void *src, int64_t lds);
 void zero2d(const Launch &L, int64_t rows, int64_t cols, void *dst, int64_t ldd);

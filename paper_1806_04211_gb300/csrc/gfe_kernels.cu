@@ -4,6 +4,9 @@
 // Jobs: arXiv 1806.04211, Section 4.1.
 #include "gfe_internal.h"
 
+#include <cstring>
+#include <type_traits>
+
 #include <climits>
 #include <mutex>
 
@@ -956,9 +959,34 @@ __device__ __forceinline__ void copy_row(T *d, const T *src, int64_t ncols, int6
     }
 }
 
-template <typename T>
+// index arrays as kernel parameters: a device pointer, or the entries by value
+struct MapPtr {
+    const int32_t *p;
+    __device__ __forceinline__ int32_t operator[](int64_t i) const { return p[i]; }
+};
+template <int N> struct MapVal {
+    int32_t v[N];
+    __device__ __forceinline__ int32_t operator[](int64_t i) const { return v[i]; }
+};
+// calls f with the map in the cheapest form: by value (two size classes) or
+// as a device pointer
+template <typename F> static void with_map(const IdxMap &m, F &&f) {
+    if (m.host && m.n <= 256) {
+        MapVal<256> v;
+        std::memcpy(v.v, m.host, sizeof(int32_t) * (size_t)m.n);
+        f(v);
+    } else if (m.host && m.n <= MAP_INLINE) {
+        MapVal<MAP_INLINE> v;
+        std::memcpy(v.v, m.host, sizeof(int32_t) * (size_t)m.n);
+        f(v);
+    } else {
+        f(MapPtr{m.dev});
+    }
+}
+
+template <typename T, typename Map>
 __global__ void k_gather_rows(int64_t nrows, int64_t ncols, T *dst, int64_t ldd, const T *A,
-                              int64_t lda, const T *B, int64_t ldb, const int32_t *map) {
+                              int64_t lda, const T *B, int64_t ldb, const __grid_constant__ Map map) {
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t row = blockIdx.y; row < nrows; row += gridDim.y) {
         int32_t s = map[row];
@@ -969,9 +997,9 @@ __global__ void k_gather_rows(int64_t nrows, int64_t ncols, T *dst, int64_t ldd,
 
 // each thread: 4 consecutive output columns of a set of rows; the map is
 // read once, the 4 results are stored as one vector when aligned
-template <typename T>
+template <typename T, typename Map>
 __global__ void k_gather_cols(int64_t nrows, int64_t ncols, T *dst, int64_t ldd, const T *src,
-                              int64_t lds, const int32_t *map) {
+                              int64_t lds, const __grid_constant__ Map map) {
     const int64_t c0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (c0 >= ncols) return;
     const int nc = ncols - c0 < 4 ? (int)(ncols - c0) : 4;
@@ -1006,8 +1034,8 @@ __global__ void k_gather_rowptr(int64_t nrows, int64_t ncols, T *dst, int64_t ld
         dst[row * ldd + c] = s >= 0 ? ((const T *)rows[row])[s] : (T)0;
 }
 
-template <typename T>
-__global__ void k_set_ones(int64_t count, T *V, int64_t ldv, const int32_t *pos, T one) {
+template <typename T, typename Map>
+__global__ void k_set_ones(int64_t count, T *V, int64_t ldv, const __grid_constant__ Map pos, T one) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) V[t * ldv + pos[t]] = one;
 }
@@ -1037,34 +1065,40 @@ static dim3 grid_rc(int64_t rows, int64_t cols, int threads) {
 }
 
 void gather_rows(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
-                 const void *A, int64_t lda, const void *B, int64_t ldb, const int32_t *map) {
+                 const void *A, int64_t lda, const void *B, int64_t ldb, const IdxMap &map) {
     if (nrows <= 0 || ncols <= 0) return;
     // one CTA row per output row (nrows <= 65535 always holds: rows <= blocks)
     const int64_t vec = (ncols * codec_bytes(L.codec) + 15) / 16;  // 16-byte vectors per row
     dim3 grid(cdiv(vec, 128) > 32 ? 32 : cdiv(vec, 128), (unsigned)(nrows < 65535 ? nrows : 65535));
     cudaEvent_t ev;
     prof_begin(L, K_ROWS, &ev);
-    if (L.codec == CODEC_F8)
-        k_gather_rows<uint8_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
-            (const uint8_t *)A, lda, (const uint8_t *)B, ldb, map);
-    else
-        k_gather_rows<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
-            (const uint16_t *)A, lda, (const uint16_t *)B, ldb, map);
+    with_map(map, [&](const auto &mp) {
+        using M = std::decay_t<decltype(mp)>;
+        if (L.codec == CODEC_F8)
+            k_gather_rows<uint8_t, M><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
+                (const uint8_t *)A, lda, (const uint8_t *)B, ldb, mp);
+        else
+            k_gather_rows<uint16_t, M><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
+                (const uint16_t *)A, lda, (const uint16_t *)B, ldb, mp);
+    });
     prof_end(L, K_ROWS, ev, 0, 0, nrows, ncols);
 }
 
 void gather_cols(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int64_t ldd,
-                 const void *src, int64_t lds, const int32_t *map) {
+                 const void *src, int64_t lds, const IdxMap &map) {
     if (nrows <= 0 || ncols <= 0) return;
     dim3 grid(cdiv((ncols + 3) / 4, 128), (unsigned)(nrows < 8192 ? nrows : 8192));
     cudaEvent_t ev;
     prof_begin(L, K_COLS, &ev);
-    if (L.codec == CODEC_F8)
-        k_gather_cols<uint8_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
-            (const uint8_t *)src, lds, map);
-    else
-        k_gather_cols<uint16_t><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
-            (const uint16_t *)src, lds, map);
+    with_map(map, [&](const auto &mp) {
+        using M = std::decay_t<decltype(mp)>;
+        if (L.codec == CODEC_F8)
+            k_gather_cols<uint8_t, M><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint8_t *)dst, ldd,
+                (const uint8_t *)src, lds, mp);
+        else
+            k_gather_cols<uint16_t, M><<<grid, 128, 0, L.st>>>(nrows, ncols, (uint16_t *)dst, ldd,
+                (const uint16_t *)src, lds, mp);
+    });
     prof_end(L, K_COLS, ev, 0, 0, nrows, ncols);
 }
 
@@ -1081,14 +1115,18 @@ void gather_rowptr(const Launch &L, int64_t nrows, int64_t ncols, void *dst, int
     prof_end(L, K_COLS, ev, 0, 0, nrows, ncols);
 }
 
-void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const int32_t *pos) {
+void set_ones(const Launch &L, int64_t count, void *V, int64_t ldv, const IdxMap &pos) {
     if (count <= 0) return;
     cudaEvent_t ev;
     prof_begin(L, K_COPY, &ev);
-    if (L.codec == CODEC_F8)
-        k_set_ones<uint8_t><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint8_t *)V, ldv, pos, (uint8_t)0x38);
-    else
-        k_set_ones<uint16_t><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint16_t *)V, ldv, pos, (uint16_t)0x3F80);
+    with_map(pos, [&](const auto &mp) {
+        using M = std::decay_t<decltype(mp)>;
+        if (L.codec == CODEC_F8)
+            k_set_ones<uint8_t, M><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint8_t *)V, ldv, mp, (uint8_t)0x38);
+        else
+            k_set_ones<uint16_t, M><<<cdiv(count, 128), 128, 0, L.st>>>(count, (uint16_t *)V, ldv, mp,
+                                                                       (uint16_t)0x3F80);
+    });
     prof_end(L, K_COPY, ev, 0, 0, count, 1);
 }
 

@@ -29,6 +29,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <mutex>
 
 namespace gfe {
@@ -523,7 +524,9 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
         const void *Wk = k0 ? C : W;
         const int64_t ldwk = k0 ? ldc : ldw;
         const int64_t tiles = ((m + TBM - 1) / TBM) * ((n + TBN - 1) / TBN);
-        const unsigned grid = (unsigned)(tiles < g_num_sms ? tiles : g_num_sms);
+        int64_t ctas = g_num_sms;
+        if (L.tiles_per_cta > 0) ctas = std::max<int64_t>(ctas, (tiles + L.tiles_per_cta - 1) / L.tiles_per_cta);
+        const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
         cudaEvent_t ev;
         prof_begin(L, K_MAD_TC, &ev);
         if (f8)

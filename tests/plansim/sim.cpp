@@ -112,6 +112,9 @@ cudaError_t cudaEventElapsedTime(float* ms, cudaEvent_t, cudaEvent_t) { *ms = 0;
 cudaError_t cudaEventCreateWithFlags(cudaEvent_t* e, unsigned int) { return cudaEventCreate(e); }
 cudaError_t cudaEventDestroy(cudaEvent_t) { return cudaSuccess; }
 cudaError_t cudaStreamCreateWithFlags(cudaStream_t* s, unsigned int) { std::lock_guard<std::mutex> g(race::mu); *s = (cudaStream_t)(g_handle++); return cudaSuccess; }
+cudaError_t cudaStreamCreateWithPriority(cudaStream_t* s, unsigned int, int) { std::lock_guard<std::mutex> g(race::mu); *s = (cudaStream_t)(g_handle++); return cudaSuccess; }
+cudaError_t cudaDeviceGetStreamPriorityRange(int* least, int* greatest) { *least = 0; *greatest = -5; return cudaSuccess; }
+cudaError_t cudaHostGetDevicePointer(void** d, void* h, unsigned int) { *d = h; return cudaSuccess; }
 cudaError_t cudaStreamWaitEvent(cudaStream_t s, cudaEvent_t e, unsigned int) { std::lock_guard<std::mutex> g(race::mu); int i = race::id_of((uintptr_t)s); race::svc[i].join(race::host); race::svc[i].join(race::evs[(uintptr_t)e]); return cudaSuccess; }
 cudaError_t cudaStreamDestroy(cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaSetDevice(int) { return cudaSuccess; }
@@ -188,15 +191,17 @@ void ech_leaf(const Launch& L, int64_t alpha, int64_t beta, const void* H, int64
     for (int y = 0; y < alpha; ++y) if (!piv[y]) for (int s2 = 0; s2 < r; ++s2) put(K, pivpos[y] * ldk + s2, cen(T[y][sortedSlot[s2]], p));
     for (int l = 0; l < r; ++l) for (int j = 0; j < beta - r; ++j) put(R, l * ldr + j, cen(S[slotRow[l]][nonCol[j]], p));
 }
-void gather_rows(const Launch& L, int64_t nrows, int64_t ncols, void* dst, int64_t ldd, const void* A, int64_t lda, const void* B, int64_t ldb, const int32_t* map) {
-    setL(L, "gather_rows"); chk(map, 4 * nrows, "map");
+// a map passed by value (host array) has no device memory to check
+static const int32_t* map_of(const IdxMap& m, int64_t n) { if (m.host) return m.host; chk(m.dev, 4 * n, "map"); return m.dev; }
+void gather_rows(const Launch& L, int64_t nrows, int64_t ncols, void* dst, int64_t ldd, const void* A, int64_t lda, const void* B, int64_t ldb, const IdxMap& mp) {
+    setL(L, "gather_rows"); const int32_t* map = map_of(mp, nrows);
     for (int64_t r = 0; r < nrows; ++r) { int32_t s = map[r];
         for (int64_t c = 0; c < ncols; ++c) {
             const char* src = s >= 0 ? (const char*)A + (s * lda + c) * es() : (const char*)B + ((-1 - s) * ldb + c) * es();
             rawcpy((char*)dst + (r * ldd + c) * es(), src); } }
 }
-void gather_cols(const Launch& L, int64_t nrows, int64_t ncols, void* dst, int64_t ldd, const void* src, int64_t lds, const int32_t* map) {
-    setL(L, "gather_cols"); chk(map, 4 * ncols, "map");
+void gather_cols(const Launch& L, int64_t nrows, int64_t ncols, void* dst, int64_t ldd, const void* src, int64_t lds, const IdxMap& mp) {
+    setL(L, "gather_cols"); const int32_t* map = map_of(mp, ncols);
     for (int64_t r = 0; r < nrows; ++r) for (int64_t c = 0; c < ncols; ++c) {
         int32_t s = map[c];
         if (s >= 0) rawcpy((char*)dst + (r * ldd + c) * es(), (const char*)src + (r * lds + s) * es());
@@ -208,7 +213,7 @@ void gather_rowptr(const Launch& L, int64_t nrows, int64_t ncols, void* dst, int
         int32_t s = map[c];
         if (s >= 0) rawcpy((char*)dst + (r * ldd + c) * es(), (const char*)rows[r] + s * es()); else put(dst, r * ldd + c, 0); }
 }
-void set_ones(const Launch& L, int64_t count, void* V, int64_t ldv, const int32_t* pos) { setL(L, "set_ones"); chk(pos, 4 * count, "pos"); for (int64_t t = 0; t < count; ++t) put(V, t * ldv + pos[t], 1); }
+void set_ones(const Launch& L, int64_t count, void* V, int64_t ldv, const IdxMap& mp) { setL(L, "set_ones"); const int32_t* pos = map_of(mp, count); for (int64_t t = 0; t < count; ++t) put(V, t * ldv + pos[t], 1); }
 void copy2d(const Launch& L, int64_t rows, int64_t cols, void* dst, int64_t ldd, const void* src, int64_t lds) {
     setL(L, "copy2d"); for (int64_t r = 0; r < rows; ++r) for (int64_t c = 0; c < cols; ++c) { if (src) rawcpy((char*)dst + (r * ldd + c) * es(), (const char*)src + (r * lds + c) * es()); else put(dst, r * ldd + c, 0); }
 }
