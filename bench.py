@@ -270,7 +270,7 @@ def bench_batched(dev, count):
     gfe.batch_echelon(mats[:16])
     torch.cuda.synchronize()
     t = time.perf_counter()
-    res = gfe.batch_echelon(mats, workers=16)
+    res = gfe.batch_echelon(mats, workers=32)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t
     madds = float(sum(m * n * d["rank"] for (p, m, n, rk), d in zip(specs, res)))
@@ -280,8 +280,11 @@ def bench_batched(dev, count):
     torch.cuda.synchronize()
     tp = time.perf_counter() - t
     return {"matrices": count, "of": 4096, "batched_matrices_per_s": count / tb, "plain_matrices_per_s": count / tp,
-            "speedup": tp / tb, "batched_madds_per_s": madds / tb, "workers": 16,
+            "speedup": tp / tb, "batched_madds_per_s": madds / tb, "workers": 32,
             "sample": "first %d of the seeded C4 draw (sum m*n*min(m,n) = %.3g)" % (count, units)}
+
+
+C5_WORKERS = 12
 
 
 def bench_serving(dev, warm, count, cap=120 << 30):
@@ -298,7 +301,7 @@ def bench_serving(dev, warm, count, cap=120 << 30):
     def serve(rate, order):
         rng = np.random.RandomState(3)
         lat, t0 = [], time.perf_counter()
-        with gfe.Server(cap, workers=12) as srv:
+        with gfe.Server(cap, workers=C5_WORKERS) as srv:
             tickets, nxt = [], t0
             for i in order:
                 A, p, n = mats[i]
@@ -316,7 +319,7 @@ def bench_serving(dev, warm, count, cap=120 << 30):
     _, tsat = serve(0, meas)                                 # saturated: all at once
     sat = count / tsat
     out = {"requests": count, "warmup_requests": warm, "saturated_matrices_per_s": sat, "hbm_cap_gb": cap >> 30,
-           "workers": 12}
+           "workers": C5_WORKERS}
     for frac in (0.5, 0.8):
         lat, tt = serve(frac * sat, meas)
         out["at_%.1fx" % frac] = {"rate": frac * sat, "matrices_per_s": count / tt,

@@ -128,6 +128,30 @@ static void stream_release(int dev, cudaStream_t s) {
     g_stream_free.push_back({dev, s});
 }
 
+// ordering events (no timing), borrowed per planner run: many small calls
+// (the batched form) would otherwise create and destroy several per call
+static std::vector<std::pair<int, cudaEvent_t>> g_event_free;
+
+static cudaEvent_t event_acquire(int dev) {
+    {
+        std::lock_guard<std::mutex> g(g_stream_mu);
+        for (size_t q = g_event_free.size(); q-- > 0;)
+            if (g_event_free[q].first == dev) {
+                cudaEvent_t e = g_event_free[q].second;
+                g_event_free.erase(g_event_free.begin() + q);
+                return e;
+            }
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return e;
+}
+
+static void event_release(int dev, const std::vector<cudaEvent_t> &evs) {
+    std::lock_guard<std::mutex> g(g_stream_mu);
+    for (cudaEvent_t e : evs) g_event_free.push_back({dev, e});
+}
+
 // the critical path's stream: the device's highest priority, so its CTAs are
 // scheduled before the side streams' when SMs come free
 static std::vector<std::pair<int, cudaStream_t>> g_hp_free;
@@ -186,11 +210,11 @@ struct Ctx {
             stream_release(dev, lv.s1);
             stream_release(dev, lv.s2);
         }
-        for (cudaEvent_t e : owned_events) cudaEventDestroy(e);
+        event_release(dev, owned_events);
     }
     cudaEvent_t make_event() {
-        cudaEvent_t e = nullptr;
-        check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        cudaEvent_t e = event_acquire(dev);
+        if (!e) throw CudaError("cudaEventCreate failed");
         owned_events.push_back(e);
         return e;
     }
