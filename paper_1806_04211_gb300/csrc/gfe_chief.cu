@@ -183,7 +183,7 @@ static void hp_release(int dev, cudaStream_t s) {
 // and the events that order the two (see chief()).
 struct Level {
     cudaStream_t s1 = nullptr, s2 = nullptr;
-    cudaEvent_t start = nullptr, aa = nullptr, cd = nullptr, b = nullptr, e4[2] = {nullptr, nullptr},
+    cudaEvent_t start = nullptr, aa = nullptr, cd = nullptr, b = nullptr, e4[4] = {nullptr, nullptr, nullptr, nullptr},
                 join = nullptr, join2 = nullptr;
 };
 
@@ -229,8 +229,7 @@ struct Ctx {
             lv.aa = make_event();
             lv.cd = make_event();
             lv.b = make_event();
-            lv.e4[0] = make_event();
-            lv.e4[1] = make_event();
+            for (auto &e : lv.e4) e = make_event();
             lv.join = make_event();
             lv.join2 = make_event();
         }
@@ -528,9 +527,9 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     //   b        s1 -> s0     step t's far columns are done; step t+1's near
     //                         columns are among them (and s1 is then done
     //                         with step t-1's copies of A.A, A.M, A.K, A.E)
-    //   e4[t&1]  s2 -> s0     step t's UpdateRowTrafo is done; A.A, A.M, A.K
-    //                         and A.E are double-buffered by step parity, so
-    //                         ClearDown of step t+2 may then overwrite them
+    //   e4[t%4]  s2 -> s0     step t's UpdateRowTrafo is done; A.A, A.M, A.K
+    //                         and A.E rotate through four copies, so
+    //                         ClearDown of step t+4 may then overwrite them
     //   join     s1,s2 -> s0  end of Step 1
     // A nested Chief (the ECH of a large block) runs on s0 with side streams
     // of its own and joins them before it returns.
@@ -570,8 +569,11 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     std::vector<std::vector<int32_t>> gam(b);
     for (int j = 0; j < b; ++j) DR[j] = X.mat(maxb, maxb);
     DMat DRsp = X.mat(maxb, maxb);
-    DMat AA[2], AM[2], AK[2], AE[2];
-    for (int q = 0; q < 2; ++q) {
+    // ClearDown outputs rotate through NRING copies: the side streams may
+    // still read step t's while ClearDown runs steps t+1 .. t+NRING-1
+    constexpr int NRING = 4;
+    DMat AA[NRING], AM[NRING], AK[NRING], AE[NRING];
+    for (int q = 0; q < NRING; ++q) {
         AA[q] = X.mat(maxa, maxb);
         AM[q] = X.mat(minab, minab);
         AK[q] = X.mat(maxa, minab);
@@ -601,10 +603,10 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
         Edel(a, std::vector<std::vector<int32_t>>(b));
 
     // ================= Step 1 =================
-    int64_t t = 0;  // step counter; its parity picks the double buffers
+    int64_t t = 0;  // step counter; t % NRING picks the copy of the ClearDown outputs
     for (int i = 0; i < a; ++i) {
         for (int j = 0; j < b; ++j, ++t) {
-            const int q = (int)(t & 1);
+            const int q = (int)(t % NRING);
             const int64_t al = cur[i], bj = bcols[j];
             const int64_t r = (int64_t)gam[j].size();
             DMat Cij = sub(X, H, ro[i], co[j], al, bj);
@@ -617,7 +619,7 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                 if (!near_ready) X.await(lv.b);
                 near_ready = true;
             };
-            if (t >= 2) X.await(lv.e4[q]);  // step t-2 has let go of this parity's buffers
+            if (t >= NRING) X.await(lv.e4[q]);  // step t-NRING has let go of these buffers
             // ---------- Task ClearDown ----------
             EchRes e;
             std::vector<int32_t> lam;
