@@ -219,6 +219,18 @@ __device__ __forceinline__ uint32_t pick16(const uint32_t (&a)[16], int i) {
     return (i & 8) ? l3[1] : l3[0];
 }
 
+// column c's place among the non-pivot columns: slotCol holds the r pivot
+// columns in ascending order (pivots are found column by column)
+__device__ __forceinline__ void place_non_pivot(const int16_t *slotCol, int r, int c, int16_t *nonCol) {
+    int lo = 0, hi = r;  // first index with slotCol[] >= c
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (slotCol[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo >= r || slotCol[lo] != c) nonCol[c - lo] = (int16_t)c;
+}
+
 // ---------------------------------------------------------------------------
 // leaf echelonisation (job ECH, Remark "echelon") of H over GF(p), p > 2:
 // alpha <= 1024 rows, beta <= 64 columns, one CTA of 1024 threads, thread y
@@ -372,14 +384,8 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(PackedMod pm, int alpha, i
             pivpos[y] = (int16_t)(y - before);
         }
     }
-    if (y == 0) {
-        info[0] = r;
-        int j = 0, l = 0;
-        for (int c = 0; c < beta; ++c) {
-            if (l < r && slotCol[l] == c) ++l;
-            else nonCol[j++] = (int16_t)c;
-        }
-    }
+    if (y == 0) info[0] = r;
+    for (int c = y; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
     if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
     __syncthreads();
     // outputs: one row per warp, lanes along the columns (coalesced)
@@ -549,14 +555,8 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_lazy(PackedMod pm, int laz
             pivpos[y] = (int16_t)(y - before);
         }
     }
-    if (y == 0) {
-        info[0] = r;
-        int j = 0, l = 0;
-        for (int c = 0; c < beta; ++c) {
-            if (l < r && slotCol[l] == c) ++l;
-            else nonCol[j++] = (int16_t)c;
-        }
-    }
+    if (y == 0) info[0] = r;
+    for (int c = y; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
     if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
     __syncthreads();
     for (int l = warp; l < r; l += nwarp)
@@ -839,42 +839,60 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
             pivpos[y] = (int16_t)(y - before);
         }
     }
-    if (y == 0) {
-        info[0] = r;
-        int j = 0, l = 0;
-        for (int c = 0; c < beta; ++c) {
-            if (l < r && slotCol[l] == c) ++l;
-            else nonCol[j++] = (int16_t)c;
-        }
-    }
+    if (y == 0) info[0] = r;
+    for (int c = y; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
     if (y < r) info[1 + 64 * W + y] = slotCol[y];
     __syncthreads();
-    // outputs: one row per warp, lanes along the columns (coalesced)
-    for (int l = warp; l < r; l += nwarp) {
-        const uint64_t *tl = tw + slotRow[l] * W;
-        for (int s = lane; s < r; s += 32) {
-            const int q = sortedSlot[s];
-            Mo[(int64_t)l * ldm + s] = ((tl[q >> 6] >> (q & 63)) & 1) ? one : (T)0;
+    // outputs: one row per warp; lane l writes the row's entries 8l .. 8l+7
+    // (r <= 256), picking each from the row's 4 words by a fixed bit index
+    // (the sorted slot for M and K, the non-pivot column for R)
+    const int e0 = 8 * lane;
+    auto emit = [&](const uint64_t *src, const int (&bit)[8], int count, T *out) {
+        const uint64_t w0 = src[0], w1 = src[1], w2 = src[2], w3 = src[3];
+        T v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int q = bit[j] & 255;
+            const uint64_t w = (q & 128) ? ((q & 64) ? w3 : w2) : ((q & 64) ? w1 : w0);
+            v[j] = ((w >> (q & 63)) & 1) ? one : (T)0;
         }
-    }
-    if (r > 0) {
-        for (int row = warp; row < alpha; row += nwarp) {
-            if (piv[row]) continue;
-            const uint64_t *tr = tw + row * W;
-            T *ko = Ko + (int64_t)pivpos[row] * ldk;
-            for (int s = lane; s < r; s += 32) {
-                const int q = sortedSlot[s];
-                ko[s] = ((tr[q >> 6] >> (q & 63)) & 1) ? one : (T)0;
+        if (e0 + 8 <= count && ((uintptr_t)(out + e0) & (8 * sizeof(T) - 1)) == 0) {
+            if constexpr (sizeof(T) == 1) {
+                uint2 pk;
+                pk.x = (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16) | ((uint32_t)v[3] << 24);
+                pk.y = (uint32_t)v[4] | ((uint32_t)v[5] << 8) | ((uint32_t)v[6] << 16) | ((uint32_t)v[7] << 24);
+                *(uint2 *)(out + e0) = pk;
+            } else {
+                uint4 pk;
+                pk.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+                pk.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
+                pk.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
+                pk.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
+                *(uint4 *)(out + e0) = pk;
             }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (e0 + j < count) out[e0 + j] = v[j];
         }
+    };
+    if (e0 < r) {
+        int q[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) q[j] = e0 + j < r ? sortedSlot[e0 + j] : 0;
+        // M[l][s] = coefficient of pivot row rho_s in echelon row l
+        for (int l = warp; l < r; l += nwarp) emit(tw + slotRow[l] * W, q, r, Mo + (int64_t)l * ldm);
+        // K[t][s] for the non-pivot rows t
+        for (int row = warp; row < alpha; row += nwarp)
+            if (!piv[row]) emit(tw + row * W, q, r, Ko + (int64_t)pivpos[row] * ldk);
     }
+    // R[l][j] = entry of echelon row l in the j-th non-pivot column
     const int nr = beta - r;
-    for (int l = warp; l < r; l += nwarp) {
-        const uint64_t *hl = hw + slotRow[l] * W;
-        for (int j = lane; j < nr; j += 32) {
-            const int c = nonCol[j];
-            Ro[(int64_t)l * ldr + j] = ((hl[c >> 6] >> (c & 63)) & 1) ? one : (T)0;
-        }
+    if (e0 < nr) {
+        int c[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) c[j] = e0 + j < nr ? nonCol[e0 + j] : 0;
+        for (int l = warp; l < r; l += nwarp) emit(hw + slotRow[l] * W, c, nr, Ro + (int64_t)l * ldr);
     }
 }
 
