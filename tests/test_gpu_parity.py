@@ -103,6 +103,34 @@ def test_parity_block_3072(p, m, n, rank, blk):
         compare_u8(A, p, gfe.echelon(A.to(DEV), p), ref)
 
 
+@pytest.mark.parametrize("p,m,n,leaf_rows", [(3, 900, 300, 256), (2, 1500, 700, 128), (251, 700, 200, 512)])
+def test_parity_leaf_rows(p, m, n, leaf_rows):
+    """Shorter leaf row blocks (gfe_set_leaf_rows) change the block grid, not
+    the result."""
+    gfe.set_leaf_rows(leaf_rows)
+    try:
+        A = synth.matrix(p, m, n, seed=13)
+        if p == 2:
+            ref = O.echelon_gf2(A.numpy(), m, n)
+            compare_gf2(gfe.echelon(A.to(DEV), 2, n=n), ref, m, n)
+        else:
+            ref = O.echelon(A.numpy(), p)
+            compare_u8(A, p, gfe.echelon(A.to(DEV), p), ref)
+    finally:
+        gfe.set_leaf_rows(0)
+
+
+def test_autotune_block_sets_a_candidate():
+    """The autotuner times every candidate and leaves the fastest in force;
+    results do not depend on the policy it picks."""
+    times = gfe.autotune_block(2, 3000, 3000, candidates=(1024, 2048), reps=1)
+    assert sorted(times) == [1024, 2048] and all(t > 0 for t in times.values())
+    A = synth.matrix(2, 1200, 900, seed=14)
+    ref = O.echelon_gf2(A.numpy(), 1200, 900)
+    compare_gf2(gfe.echelon(A.to(DEV), 2, n=900), ref, 1200, 900)
+    gfe.set_block_policy()
+
+
 @pytest.mark.parametrize("p", [3, 251])
 def test_dense_E_T(p):
     A = synth.matrix(p, 150, 170, seed=2, rank=100)
