@@ -200,7 +200,7 @@ struct Ctx {
     int dev = 0;
     int64_t thr = 2048, blk = 2048;  // block policy of this run
     int64_t leaf_rows = ECH_LEAF_ROWS;
-    cudaStream_t main_st = nullptr;  // the caller's stream
+    cudaStream_t main_st = nullptr;  // the critical path's stream (high priority)
     int depth = 0;                 // nesting depth of the Chief being planned
     std::vector<Level> levels;     // per depth, made on first use
     std::vector<cudaEvent_t> owned_events;
