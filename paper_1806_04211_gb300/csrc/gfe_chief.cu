@@ -517,8 +517,8 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     const int64_t minab = std::min(maxa, maxb);
 
     // ---- streams ----
-    // The ClearDown chain is the critical path.  It runs on the caller's
-    // stream s0 together with UpdateRow on the near columns (block column
+    // The ClearDown chain is the critical path.  It runs on the planner's
+    // high-priority stream s0 together with UpdateRow on the near columns (block column
     // j+1, which the next ClearDown reads).  Meanwhile UpdateRow on the far
     // columns (j+2 onwards) runs on side stream s1 and UpdateRowTrafo on
     // side stream s2 (they share no output).  Events order them:
