@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(PackedMod pm, int alpha, i
     __shared__ int16_t slotOf[1024];
     __shared__ int16_t pivpos[1024];
     __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
-    __shared__ uint32_t wbuf[2][32][32];
+    __shared__ __align__(16) uint32_t wbuf[2][32][32];
     __shared__ int wmin[2][32];
     __shared__ int wsum[32];
     const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
@@ -300,10 +300,11 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf(PackedMod pm, int alpha, i
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         if (lane == 0) wmin[b][warp] = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
         if (bal && lane == __ffs(bal) - 1) {
+            uint4 *dst = (uint4 *)wbuf[b][warp];
 #pragma unroll
-            for (int w = 0; w < 16; ++w) {
-                wbuf[b][warp][w] = h[w];
-                wbuf[b][warp][16 + w] = t[w];
+            for (int w = 0; w < 4; ++w) {
+                dst[w] = make_uint4(h[4 * w], h[4 * w + 1], h[4 * w + 2], h[4 * w + 3]);
+                dst[4 + w] = make_uint4(t[4 * w], t[4 * w + 1], t[4 * w + 2], t[4 * w + 3]);
             }
         }
         __syncthreads();
@@ -425,7 +426,7 @@ __device__ __forceinline__ uint32_t preduce(uint32_t x, const PackedMod &q) {
 // `lazy_k` pivot steps, lazy_k = floor((255 - (p - 1)) / (p - 1)^2), so no
 // byte ever exceeds 255.  The pivot row is published unreduced; every warp
 // reduces it and scales it by -1/pivot lane-parallel (lane w takes word w)
-// and shuffles the words to its lanes.
+// and passes the words to its lanes through a warp-private buffer.
 // ---------------------------------------------------------------------------
 template <int C>
 __global__ void __launch_bounds__(1024, 1) k_ech_leaf_lazy(PackedMod pm, int lazy_k, int alpha, int beta,
@@ -443,7 +444,8 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_lazy(PackedMod pm, int laz
     __shared__ int16_t slotOf[1024];
     __shared__ int16_t pivpos[1024];
     __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
-    __shared__ uint32_t wbuf[2][32][32];
+    __shared__ __align__(16) uint32_t wbuf[2][32][32];
+    __shared__ __align__(16) uint32_t prow[32][32];  // per warp: the reduced, scaled pivot row
     __shared__ int wmin[2][32];
     __shared__ int wsum[32];
     const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
@@ -486,10 +488,11 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_lazy(PackedMod pm, int laz
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         if (lane == 0) wmin[b][warp] = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
         if (bal && lane == __ffs(bal) - 1) {
+            uint4 *dst = (uint4 *)wbuf[b][warp];
 #pragma unroll
-            for (int w = 0; w < 16; ++w) {
-                wbuf[b][warp][w] = h[w];
-                wbuf[b][warp][16 + w] = t[w];
+            for (int w = 0; w < 4; ++w) {
+                dst[w] = make_uint4(h[4 * w], h[4 * w + 1], h[4 * w + 2], h[4 * w + 3]);
+                dst[4 + w] = make_uint4(t[4 * w], t[4 * w + 1], t[4 * w + 2], t[4 * w + 3]);
             }
         }
         __syncthreads();
@@ -516,11 +519,24 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_lazy(PackedMod pm, int laz
             slotRow[ns] = (int16_t)y;
             slotCol[ns] = (int16_t)c;
         }
+        // through this warp's own buffer: one store per lane, eight
+        // broadcast 16-byte loads
+        prow[warp][lane] = wv;
+        __syncwarp();
+        const uint4 *pr = (const uint4 *)prow[warp];
 #pragma unroll
-        for (int w = 0; w < 16; ++w) {
-            h[w] += g * __shfl_sync(0xffffffffu, wv, w);
-            t[w] += g * __shfl_sync(0xffffffffu, wv, 16 + w);
+        for (int w = 0; w < 4; ++w) {
+            const uint4 hv = pr[w], tv = pr[4 + w];
+            h[4 * w] += g * hv.x;
+            h[4 * w + 1] += g * hv.y;
+            h[4 * w + 2] += g * hv.z;
+            h[4 * w + 3] += g * hv.w;
+            t[4 * w] += g * tv.x;
+            t[4 * w + 1] += g * tv.y;
+            t[4 * w + 2] += g * tv.z;
+            t[4 * w + 3] += g * tv.w;
         }
+        __syncwarp();  // the buffer is rewritten at the next pivot
         ++ns;
         if (++since == lazy_k) {
             since = 0;
