@@ -218,9 +218,10 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);
  * gfe_set_block_policy. */
 int64_t gfe_auto_block(int32_t p, int64_t m, int64_t n);
 
-/* Rows of a leaf block in the planner's leaf grid (the ECH kernel takes at
- * most 1024): 1..1024, or 0 for the default (1024).  Process wide.  Results
- * never depend on it.  GFE_EINVAL outside [0, 1024]. */
+/* Rows of a leaf block in the planner's leaf grid: 1..1024, or 0 for the
+ * default, which is the most the field's leaf kernel takes (1024 for
+ * p <= 13, 256 for larger p); larger values are capped at that.  Process
+ * wide.  Results never depend on it.  GFE_EINVAL outside [0, 1024]. */
 gfe_status gfe_set_leaf_rows(int64_t rows);
 
 /* Kernel profile of the calls made since the last reset (all streams).

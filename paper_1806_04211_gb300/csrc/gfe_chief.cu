@@ -427,10 +427,9 @@ int64_t g_block_threshold = 0, g_block_big = 0;
 int64_t g_leaf_rows = 0;
 
 int64_t auto_leaf_rows(int p, int64_t m, int64_t n) {
-    (void)p;
     (void)m;
     (void)n;
-    return ECH_LEAF_ROWS;
+    return ech_leaf_rows(p);
 }
 
 // Top-level block side (the a_i, b_j of Section 3.1) by field and size,
@@ -470,7 +469,7 @@ static void ech_start(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, con
     out.gamma.clear();
     if (alpha == 0 || beta == 0) return;
     const int lc = ech_leaf_cols(X.L.p);
-    if (alpha <= ECH_LEAF_ROWS && beta <= lc) {
+    if (alpha <= ech_leaf_rows(X.L.p) && beta <= lc) {
         if (!X.dry) {
             // the kernel writes (r, rho, gamma) into mapped host memory; the
             // event after it makes them visible to the host
@@ -1007,7 +1006,8 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
     } else {
         X.thr = X.blk = auto_block(L.p, H.rows, H.cols);
     }
-    X.leaf_rows = g_leaf_rows > 0 ? g_leaf_rows : auto_leaf_rows(L.p, H.rows, H.cols);
+    X.leaf_rows = std::min<int64_t>(g_leaf_rows > 0 ? g_leaf_rows : auto_leaf_rows(L.p, H.rows, H.cols),
+                                    ech_leaf_rows(L.p));
     std::vector<int64_t> a, b;
     block_policy(X, H.rows, H.cols, a, b);
     EchRes e;

@@ -70,6 +70,9 @@ int wait_selftest(cudaStream_t st, int64_t limit_us);
 // Leaf echelonisation of H (alpha <= ECH_LEAF_ROWS, beta <= ech_leaf_cols(p)).
 // info[0] = r, info[1..] = rho (r), info[1+cap..] = gamma (r), cap = ech_leaf_cols(p).
 constexpr int ECH_LEAF_ROWS = 1024;
+constexpr int F32_LEAF_ROWS = 256;  // the fp32 leaf for 17 <= p <= 251
+// rows one leaf kernel takes for this field
+inline int ech_leaf_rows(int p) { return (p == 2 || p <= 13) ? ECH_LEAF_ROWS : F32_LEAF_ROWS; }
 constexpr int ECH_LEAF_COLS = 64;       // p > 2: byte rows in shared memory
 constexpr int ECH_LEAF_COLS_GF2 = 256;  // p = 2: 64-bit words in registers
 int ech_leaf_cols(int p);

@@ -206,6 +206,7 @@ __device__ __forceinline__ uint32_t pmadd(uint32_t a, uint32_t g, uint32_t b, co
     M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15)
 #define GFE_RCASE16(M)                                                                                    \
     M(15) M(14) M(13) M(12) M(11) M(10) M(9) M(8) M(7) M(6) M(5) M(4) M(3) M(2) M(1) M(0)
+#define GFE_CASE64(M) M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31) M(32) M(33) M(34) M(35) M(36) M(37) M(38) M(39) M(40) M(41) M(42) M(43) M(44) M(45) M(46) M(47) M(48) M(49) M(50) M(51) M(52) M(53) M(54) M(55) M(56) M(57) M(58) M(59) M(60) M(61) M(62) M(63)
 
 // word i of a register array: a select tree of depth 4 (not a chain of 15)
 __device__ __forceinline__ uint32_t pick16(const uint32_t (&a)[16], int i) {
@@ -553,6 +554,213 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_lazy(PackedMod pm, int laz
     for (int w = 0; w < 16; ++w) {
         *(uint32_t *)(S + y * LS + 4 * w) = preduce(h[w], pm);
         *(uint32_t *)(Tt + y * LS + 4 * w) = preduce(t[w], pm);
+    }
+    // rank of each row among pivot rows (ascending) and among non-pivot rows
+    const int isp_i = (y < alpha) && isp;
+    unsigned bal = __ballot_sync(0xffffffffu, isp_i);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    before += __popc(bal & ((1u << lane) - 1));
+    if (y < alpha) {
+        if (isp_i) {
+            pivpos[y] = (int16_t)before;
+            sortedSlot[before] = slotOf[y];
+            info[1 + before] = y;
+        } else {
+            pivpos[y] = (int16_t)(y - before);
+        }
+    }
+    if (y == 0) info[0] = r;
+    for (int c = y; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
+    if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
+    __syncthreads();
+    for (int l = warp; l < r; l += nwarp)
+        for (int s = lane; s < r; s += 32)
+            Mo[(int64_t)l * ldm + s] = D::enc(cen(Tt[slotRow[l] * LS + sortedSlot[s]], p));
+    if (r > 0) {
+        for (int row = warp; row < alpha; row += nwarp) {
+            if (piv[row]) continue;
+            for (int s = lane; s < r; s += 32)
+                Ko[(int64_t)pivpos[row] * ldk + s] = D::enc(cen(Tt[row * LS + sortedSlot[s]], p));
+        }
+    }
+    const int nr = beta - r;
+    for (int l = warp; l < r; l += nwarp)
+        for (int j = lane; j < nr; j += 32)
+            Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
+}
+
+// x mod p for an integer-valued float 0 <= x < 2^24 (the float reciprocal
+// quotient is at most one off; the remainder is formed exactly by fma)
+__device__ __forceinline__ float fred(float x, float p, float invp) {
+    const float q = floorf(x * invp);
+    float r = fmaf(-q, p, x);
+    r = r < 0.f ? r + p : r;
+    return r >= p ? r - p : r;
+}
+
+// ---------------------------------------------------------------------------
+// leaf ECH for 17 <= p <= 251: the same column-by-column Gauss-Jordan and
+// topmost-row rule, with a row's 64 entries and 64 slot coefficients held as
+// fp32 integers in registers, so an update is one exact fma.  Rows start as
+// residues below p and gain less than p^2 per pivot step, so after the at
+// most 64 steps of a leaf every value is below 64 p^2 + p < 2^24 and no row
+// is reduced before the end.  The published pivot row is reduced and scaled
+// by -1/pivot lane-parallel (lane l takes entries l, l+32, l+64, l+96) into
+// a warp-private buffer; rows then add v times it over the columns >= c and
+// the slots <= the new one only (jump tables into unrolled runs of 4).
+// 128 fp32 registers per row: at most F32_LEAF_ROWS rows.
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void __launch_bounds__(F32_LEAF_ROWS, 1) k_ech_leaf_f32(int p, int alpha, int beta,
+                                                                const typename Cd<C>::T *H, int64_t ldh,
+                                                                int32_t *info, typename Cd<C>::T *Mo,
+                                                                int64_t ldm, typename Cd<C>::T *Ko,
+                                                                int64_t ldk, typename Cd<C>::T *Ro,
+                                                                int64_t ldr) {
+    using D = Cd<C>;
+    extern __shared__ uint8_t sm[];
+    uint8_t *S = sm;                           // [threads][LS]  residues of H (load / output)
+    uint8_t *Tt = sm + blockDim.x * LS;        // [threads][LS]  slot coefficients (output)
+    __shared__ uint8_t inv[256];
+    __shared__ uint8_t piv[F32_LEAF_ROWS];
+    __shared__ int16_t slotOf[F32_LEAF_ROWS];
+    __shared__ int16_t pivpos[F32_LEAF_ROWS];
+    __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
+    __shared__ __align__(16) float wbuf[2][F32_LEAF_ROWS / 32][128];  // per warp: its first candidate row
+    __shared__ __align__(16) float prow[F32_LEAF_ROWS / 32][128];     // per warp: the reduced, scaled pivot row
+    __shared__ int wmin[2][32];
+    __shared__ int wsum[32];
+    const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
+    const float fp = (float)p, invp = 1.0f / (float)p;
+
+    for (int q = y; q < p; q += blockDim.x) {
+        int v = 0;
+        for (int x = 1; x < p; ++x)
+            if ((q * x) % p == 1) v = x;
+        inv[q] = (uint8_t)v;
+    }
+    for (int q = y; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
+    piv[y] = 0;
+    slotOf[y] = -1;
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+        const int row = warp * 32 + rr;
+        const typename D::T *hr = H + (int64_t)row * ldh;
+        const bool in = row < alpha;
+        S[row * LS + lane] = in && lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
+        S[row * LS + 32 + lane] = in && 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
+    }
+    __syncthreads();
+    float h[64], t[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) {
+        h[k] = (float)S[y * LS + k];
+        t[k] = 0.f;
+    }
+    bool isp = false;
+    __syncthreads();
+
+    int ns = 0;
+    for (int c = 0; c < beta; ++c) {
+        const int b = c & 1;
+        float vraw = 0.f;
+        switch (c) {
+#define GFE_PICK(k) \
+    case k:         \
+        vraw = h[k];  \
+        break;
+            GFE_CASE64(GFE_PICK)
+#undef GFE_PICK
+        default:
+            break;
+        }
+        const float v = fred(vraw, fp, invp);
+        const bool cand = (y < alpha) && !isp && v != 0.f;
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0) wmin[b][warp] = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
+        if (bal && lane == __ffs(bal) - 1) {
+            float4 *dst = (float4 *)wbuf[b][warp];
+#pragma unroll
+            for (int w = 0; w < 16; ++w) {
+                dst[w] = make_float4(h[4 * w], h[4 * w + 1], h[4 * w + 2], h[4 * w + 3]);
+                dst[16 + w] = make_float4(t[4 * w], t[4 * w + 1], t[4 * w + 2], t[4 * w + 3]);
+            }
+        }
+        __syncthreads();
+        const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)wmin[b][lane]);
+        if (x == INT_MAX) continue;  // uniform: column c has no pivot
+        const float *px = wbuf[b][x >> 5];
+        const float pv = fred(px[c], fp, invp);
+        const int pvi = (int)pv;
+        const float sc = (float)(pvi ? p - inv[pvi] : 0);  // makes the pivot -1
+        // lane l: entries l, l+32 (columns) and 64+l, 96+l (slots), with the
+        // pivot's own identity in slot ns, times sc
+        float e0 = fred(px[lane], fp, invp), e1 = fred(px[32 + lane], fp, invp);
+        float e2 = fred(px[64 + lane], fp, invp), e3 = fred(px[96 + lane], fp, invp);
+        if (lane == ns) e2 += 1.f;
+        if (lane + 32 == ns) e3 += 1.f;
+        prow[warp][lane] = fred(e0 * sc, fp, invp);
+        prow[warp][32 + lane] = fred(e1 * sc, fp, invp);
+        prow[warp][64 + lane] = fred(e2 * sc, fp, invp);
+        prow[warp][96 + lane] = fred(e3 * sc, fp, invp);
+        __syncwarp();
+        // the pivot row becomes that row; every other row adds v times it
+        const bool me = (y == x);
+        const float g = me ? 1.f : v;
+        if (me) {
+#pragma unroll
+            for (int k = 0; k < 64; ++k) h[k] = t[k] = 0.f;
+            isp = true;
+            piv[y] = 1;
+            slotOf[y] = (int16_t)ns;
+            slotRow[ns] = (int16_t)y;
+            slotCol[ns] = (int16_t)c;
+        }
+        const float4 *pr = (const float4 *)prow[warp];
+        // columns from c's group of four on (the pivot row is zero left of c)
+        switch (c >> 2) {
+#define GFE_HUPD(k)                                     \
+    case k: {                                           \
+        const float4 q4 = pr[k];                        \
+        h[4 * k] = fmaf(g, q4.x, h[4 * k]);             \
+        h[4 * k + 1] = fmaf(g, q4.y, h[4 * k + 1]);     \
+        h[4 * k + 2] = fmaf(g, q4.z, h[4 * k + 2]);     \
+        h[4 * k + 3] = fmaf(g, q4.w, h[4 * k + 3]);     \
+    }                                                   \
+        [[fallthrough]];
+            GFE_CASE16(GFE_HUPD)
+#undef GFE_HUPD
+        default:
+            break;
+        }
+        // slots up to ns's group of four (the pivot row's later slots are zero)
+        switch (ns >> 2) {
+#define GFE_TUPD(k)                                     \
+    case k: {                                           \
+        const float4 q4 = pr[16 + k];                   \
+        t[4 * k] = fmaf(g, q4.x, t[4 * k]);             \
+        t[4 * k + 1] = fmaf(g, q4.y, t[4 * k + 1]);     \
+        t[4 * k + 2] = fmaf(g, q4.z, t[4 * k + 2]);     \
+        t[4 * k + 3] = fmaf(g, q4.w, t[4 * k + 3]);     \
+    }                                                   \
+        [[fallthrough]];
+            GFE_RCASE16(GFE_TUPD)
+#undef GFE_TUPD
+        default:
+            break;
+        }
+        __syncwarp();  // prow is rewritten at the next pivot
+        ++ns;
+    }
+    const int r = ns;
+    // reduced rows back to shared memory for the (coalesced) output phase
+#pragma unroll
+    for (int k = 0; k < 64; ++k) {
+        S[y * LS + k] = (uint8_t)fred(h[k], fp, invp);
+        Tt[y * LS + k] = (uint8_t)fred(t[k], fp, invp);
     }
     // rank of each row among pivot rows (ascending) and among non-pivot rows
     const int isp_i = (y < alpha) && isp;
@@ -961,17 +1169,27 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
         k_ech_leaf_lazy<CODEC><<<1, threads, smem, L.st>>>(pm, lazy_k, (int)alpha, (int)beta, (const T *)H, ldh,  \
                                                           info, (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);           \
     } while (0)
+#define GFE_F32(CODEC, T, IDX)                                                                                   \
+    do {                                                                                                          \
+        std::call_once(once2[IDX], [&] {                                                                          \
+            cudaFuncSetAttribute(k_ech_leaf_f32<CODEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                 2 * F32_LEAF_ROWS * LS);                                                         \
+        });                                                                                                       \
+        k_ech_leaf_f32<CODEC><<<1, threads, smem, L.st>>>(L.p, (int)alpha, (int)beta, (const T *)H, ldh, info,    \
+                                                         (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);                  \
+    } while (0)
     // pivot steps between full reductions: (p - 1) + k (p - 1)^2 <= 255
     const int lazy_k = small ? (255 - (L.p - 1)) / ((L.p - 1) * (L.p - 1)) : 0;
     if (L.codec == CODEC_F8) {
         if (small) GFE_LAZY(CODEC_F8, uint8_t, 0);
-        else GFE_LEAF(CODEC_F8, uint8_t, false, 1);
+        else GFE_F32(CODEC_F8, uint8_t, 1);
     } else {
         if (small) GFE_LAZY(CODEC_BF16, uint16_t, 2);
-        else GFE_LEAF(CODEC_BF16, uint16_t, false, 3);
+        else GFE_F32(CODEC_BF16, uint16_t, 3);
     }
 #undef GFE_LEAF
 #undef GFE_LAZY
+#undef GFE_F32
     prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta), 0, alpha, beta);
 }
 
