@@ -50,14 +50,6 @@ __device__ __forceinline__ int modp(int x, int p) {
     int r = x % p;
     return r < 0 ? r + p : r;
 }
-// x in [0, 2^16): x mod p through a float reciprocal, corrected both ways
-__device__ __forceinline__ int modp16(int x, int p, float invp) {
-    int q = (int)((float)x * invp);
-    int r = x - q * p;
-    if (r < 0) r += p;
-    if (r >= p) r -= p;
-    return r;
-}
 
 static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
@@ -161,45 +153,24 @@ void mad(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_
 
 // ---------------------------------------------------------------------------
 // leaf echelonisation (job ECH, Remark "echelon") of H: alpha x beta with
-// alpha <= 1024, beta <= 64, one CTA of 1024 threads, one thread per row.
-// Column-by-column Gauss-Jordan; the pivot of column c is the topmost
-// non-pivot row with a non-zero entry there, which yields the row rank
-// profile and the column rank profile, i.e. the unique result of Eq. (gauss).
-// The transformation is kept in "slot" space: slot t = the t-th pivot found
-// (= the t-th pivot column), so each row carries <= 64 coefficients.
+// beta <= 64 (256 for GF(2)), one CTA, one thread per row.  Column-by-column
+// Gauss-Jordan; the pivot of column c is the topmost non-pivot row with a
+// non-zero entry there, which yields the row rank profile and the column
+// rank profile, i.e. the unique result of Eq. (gauss).  The transformation
+// is kept in "slot" space: slot t = the t-th pivot found (= the t-th pivot
+// column), so each row carries <= 64 (GF(2): 256) coefficients.
 // ---------------------------------------------------------------------------
 constexpr int LS = 68;  // smem row stride (bytes): 17 words -> conflict-free rows
 
-// Packed multiply-add mod p on four residues per 32-bit word.
-//  small p (<= 13): a + g*b stays below 256 in every byte, so it is formed
-//   with plain 32-bit arithmetic; the quotient by p comes from a Barrett step
-//   on the even and odd bytes (two 16-bit lanes each), never too large and at
-//   most one too small, fixed by one byte-wise compare (__vcmpgeu4).
-//  larger p: byte by byte through the float reciprocal (exact below 2^16).
+// Byte-wise arithmetic mod p (p <= 13) on four residues per 32-bit word:
+// the quotient of each byte (<= 255) comes from a Barrett step on the even
+// and odd bytes (two 16-bit lanes each), never too large and at most one too
+// small, fixed by one byte-wise compare (__vcmpgeu4).
 struct PackedMod {
     uint32_t p, pp;     // p, and p in every byte
     uint32_t M, S, QM;  // Barrett multiplier, shift, mask of the quotient bits
     float invp;
 };
-
-template <bool SMALL>
-__device__ __forceinline__ uint32_t pmadd(uint32_t a, uint32_t g, uint32_t b, const PackedMod &q) {
-    if constexpr (SMALL) {
-        const uint32_t x = a + g * b;
-        const uint32_t lo = x & 0x00FF00FFu, hi = (x >> 8) & 0x00FF00FFu;
-        const uint32_t qq = (((lo * q.M) >> q.S) & q.QM) | ((((hi * q.M) >> q.S) & q.QM) << 8);
-        const uint32_t r = x - qq * q.p;
-        return r - (__vcmpgeu4(r, q.pp) & q.pp);
-    } else {
-        uint32_t r = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int x = (int)((a >> (8 * k)) & 0xFF) + (int)g * (int)((b >> (8 * k)) & 0xFF);
-            r |= (uint32_t)modp16(x, (int)q.p, q.invp) << (8 * k);
-        }
-        return r;
-    }
-}
 
 // register-resident packed rows: word w of a 16-word array, static indices
 #define GFE_CASE16(M)                                                                                     \
@@ -232,186 +203,7 @@ __device__ __forceinline__ void place_non_pivot(const int16_t *slotCol, int r, i
     if (lo >= r || slotCol[lo] != c) nonCol[c - lo] = (int16_t)c;
 }
 
-// ---------------------------------------------------------------------------
-// leaf echelonisation (job ECH, Remark "echelon") of H over GF(p), p > 2:
-// alpha <= 1024 rows, beta <= 64 columns, one CTA of 1024 threads, thread y
-// owns row y (64 residues + 64 slot coefficients packed in 32 registers).
-// Column-by-column Gauss-Jordan; the pivot of column c is the topmost
-// non-pivot row with a non-zero entry there, which yields the row rank
-// profile and the column rank profile, i.e. the unique result of Eq. (gauss).
-// Slot t = the t-th pivot found (= the t-th pivot column).  Every warp
-// publishes its first candidate row before the column's one barrier; rows
-// add g = v*s times the published (unscaled) pivot row, s = -1/pivot.
-// ---------------------------------------------------------------------------
-template <int C, bool SMALL>
-__global__ void __launch_bounds__(1024, 1) k_ech_leaf(PackedMod pm, int alpha, int beta,
-                                                      const typename Cd<C>::T *H, int64_t ldh,
-                                                      int32_t *info, typename Cd<C>::T *Mo,
-                                                      int64_t ldm, typename Cd<C>::T *Ko,
-                                                      int64_t ldk, typename Cd<C>::T *Ro,
-                                                      int64_t ldr) {
-    using D = Cd<C>;
-    extern __shared__ uint8_t sm[];
-    uint8_t *S = sm;                           // [threads][LS]  residues of H (load / output)
-    uint8_t *Tt = sm + blockDim.x * LS;        // [threads][LS]  slot coefficients (output)
-    __shared__ uint8_t inv[256];
-    __shared__ uint8_t piv[1024];
-    __shared__ int16_t slotOf[1024];
-    __shared__ int16_t pivpos[1024];
-    __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
-    __shared__ __align__(16) uint32_t wbuf[2][32][32];
-    __shared__ int wmin[2][32];
-    __shared__ int wsum[32];
-    const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
-    const int p = (int)pm.p;
-
-    for (int q = y; q < p; q += blockDim.x) {
-        int v = 0;
-        for (int x = 1; x < p; ++x)
-            if ((q * x) % p == 1) v = x;
-        inv[q] = (uint8_t)v;
-    }
-    for (int q = y; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
-    piv[y] = 0;
-    slotOf[y] = -1;
-    // coalesced load: warp w reads its 32 rows, lane l columns l and l + 32
-#pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) {
-        const int row = warp * 32 + rr;
-        const typename D::T *hr = H + (int64_t)row * ldh;
-        const bool in = row < alpha;
-        S[row * LS + lane] = in && lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
-        S[row * LS + 32 + lane] = in && 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
-    }
-    __syncthreads();
-    uint32_t h[16], t[16];
-#pragma unroll
-    for (int w = 0; w < 16; ++w) {
-        h[w] = *(const uint32_t *)(S + y * LS + 4 * w);
-        t[w] = 0;
-    }
-    bool isp = false;
-    __syncthreads();
-
-    int ns = 0;
-    for (int c = 0; c < beta; ++c) {
-        const int b = c & 1, wc = c >> 2, bc = 8 * (c & 3);
-        const uint32_t v = (pick16(h, wc) >> bc) & 0xFF;
-        const bool cand = (y < alpha) && !isp && v != 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, cand);
-        if (lane == 0) wmin[b][warp] = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
-        if (bal && lane == __ffs(bal) - 1) {
-            uint4 *dst = (uint4 *)wbuf[b][warp];
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                dst[w] = make_uint4(h[4 * w], h[4 * w + 1], h[4 * w + 2], h[4 * w + 3]);
-                dst[4 + w] = make_uint4(t[4 * w], t[4 * w + 1], t[4 * w + 2], t[4 * w + 3]);
-            }
-        }
-        __syncthreads();
-        const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)wmin[b][lane]);
-        if (x == INT_MAX) continue;  // uniform: column c has no pivot
-        const uint32_t *px = wbuf[b][x >> 5];
-        const uint32_t pv = (px[wc] >> bc) & 0xFF;
-        uint32_t sc = (uint32_t)(p - inv[pv]);  // scale making the pivot -1
-        if (sc == (uint32_t)p) sc = 0;
-        const int nw = ns >> 2, nb = 8 * (ns & 3);
-        if (y == x) {
-            // own identity in slot ns, then the whole row times sc
-#define GFE_SETID(k) \
-    if (nw == k) t[k] |= 1u << nb;
-            GFE_CASE16(GFE_SETID)
-#undef GFE_SETID
-#pragma unroll
-            for (int w = 0; w < 16; ++w) {
-                h[w] = pmadd<SMALL>(0u, sc, h[w], pm);
-                t[w] = pmadd<SMALL>(0u, sc, t[w], pm);
-            }
-            isp = true;
-            piv[y] = 1;
-            slotOf[y] = (int16_t)ns;
-            slotRow[ns] = (int16_t)y;
-            slotCol[ns] = (int16_t)c;
-        } else if (v) {
-            const uint32_t g = (uint32_t)modp16((int)(v * sc), p, pm.invp);
-            // H words from wc on (the pivot row is zero left of column c)
-            switch (wc) {
-#define GFE_HUPD(k)   \
-    case k:           \
-        h[k] = pmadd<SMALL>(h[k], g, px[k], pm);  [[fallthrough]];
-                GFE_CASE16(GFE_HUPD)
-#undef GFE_HUPD
-            default:
-                break;
-            }
-            // slot words up to nw (the pivot row's slots beyond ns - 1 are zero)
-            switch (nw) {
-#define GFE_TUPD(k)   \
-    case k:           \
-        t[k] = pmadd<SMALL>(t[k], g, px[16 + k], pm);  [[fallthrough]];
-                GFE_RCASE16(GFE_TUPD)
-#undef GFE_TUPD
-            default:
-                break;
-            }
-            // slot ns (zero so far in this row) gets g: the pivot's own identity
-#define GFE_SETG(k) \
-    if (nw == k) t[k] |= g << nb;
-            GFE_CASE16(GFE_SETG)
-#undef GFE_SETG
-        }
-        ++ns;
-    }
-    const int r = ns;
-    // rows back to shared memory for the (coalesced) output phase
-#pragma unroll
-    for (int w = 0; w < 16; ++w) {
-        *(uint32_t *)(S + y * LS + 4 * w) = h[w];
-        *(uint32_t *)(Tt + y * LS + 4 * w) = t[w];
-    }
-    // rank of each row among pivot rows (ascending) and among non-pivot rows
-    const int isp_i = (y < alpha) && isp;
-    unsigned bal = __ballot_sync(0xffffffffu, isp_i);
-    if (lane == 0) wsum[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0;
-    for (int w = 0; w < warp; ++w) before += wsum[w];
-    before += __popc(bal & ((1u << lane) - 1));
-    if (y < alpha) {
-        if (isp_i) {
-            pivpos[y] = (int16_t)before;
-            sortedSlot[before] = slotOf[y];
-            info[1 + before] = y;
-        } else {
-            pivpos[y] = (int16_t)(y - before);
-        }
-    }
-    if (y == 0) info[0] = r;
-    for (int c = y; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
-    if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
-    __syncthreads();
-    // outputs: one row per warp, lanes along the columns (coalesced)
-    // M[l][s] = coefficient of pivot row rho_s in echelon row l
-    for (int l = warp; l < r; l += nwarp)
-        for (int s = lane; s < r; s += 32)
-            Mo[(int64_t)l * ldm + s] = D::enc(cen(Tt[slotRow[l] * LS + sortedSlot[s]], p));
-    // K[t][s] for the non-pivot rows t
-    if (r > 0) {
-        for (int row = warp; row < alpha; row += nwarp) {
-            if (piv[row]) continue;
-            for (int s = lane; s < r; s += 32)
-                Ko[(int64_t)pivpos[row] * ldk + s] = D::enc(cen(Tt[row * LS + sortedSlot[s]], p));
-        }
-    }
-    // R[l][j] = entry of echelon row l in the j-th non-pivot column
-    const int nr = beta - r;
-    for (int l = warp; l < r; l += nwarp)
-        for (int j = lane; j < nr; j += 32)
-            Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
-}
-
-// Byte-wise reduction mod p of four packed values <= 255 (p <= 13): the
-// Barrett step of pmadd without the multiply-add.
+// Byte-wise reduction mod p of four packed values <= 255 (p <= 13).
 __device__ __forceinline__ uint32_t preduce(uint32_t x, const PackedMod &q) {
     const uint32_t lo = x & 0x00FF00FFu, hi = (x >> 8) & 0x00FF00FFu;
     const uint32_t qq = (((lo * q.M) >> q.S) & q.QM) | ((((hi * q.M) >> q.S) & q.QM) << 8);
@@ -1153,14 +945,6 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
     static std::once_flag once2[4];
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
-#define GFE_LEAF(CODEC, T, SM, IDX)                                                                              \
-    do {                                                                                                          \
-        std::call_once(once2[IDX], [&] {                                                                          \
-            cudaFuncSetAttribute(k_ech_leaf<CODEC, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);   \
-        });                                                                                                       \
-        k_ech_leaf<CODEC, SM><<<1, threads, smem, L.st>>>(pm, (int)alpha, (int)beta, (const T *)H, ldh, info,        \
-                                                     (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);                      \
-    } while (0)
 #define GFE_LAZY(CODEC, T, IDX)                                                                                  \
     do {                                                                                                          \
         std::call_once(once2[IDX], [&] {                                                                          \
@@ -1187,7 +971,6 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
         if (small) GFE_LAZY(CODEC_BF16, uint16_t, 2);
         else GFE_F32(CODEC_BF16, uint16_t, 3);
     }
-#undef GFE_LEAF
 #undef GFE_LAZY
 #undef GFE_F32
     prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta), 0, alpha, beta);
