@@ -212,7 +212,7 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);
 
 /* The block side the default policy uses for an m x n matrix over GF(p):
  * a table measured on GB300 (GF(2): 2048 below max(m, n) = 12288, 3072 up to
- * 65536, 6144 above; p > 2: 2048).  The Python autotuner
+ * 65536, 6144 above; 3 <= p <= 13: 2048; p > 13: 1024).  The Python autotuner
  * (paper_1806_04211_gb300.gfe.autotune_block) times candidates on a seeded
  * matrix of the caller's shape and sets the winner with
  * gfe_set_block_policy. */

@@ -434,11 +434,13 @@ int64_t auto_leaf_rows(int p, int64_t m, int64_t n) {
 
 // Top-level block side (the a_i, b_j of Section 3.1) by field and size,
 // from sweeps of the C2/C3 workloads on GB300: GF(2) is fastest with 3072
-// from n ~ 12288 and 6144 from n ~ 65536, larger p with 2048.  Sides are
-// multiples of the 1024-row leaf; ragged ones (2560, 3584) were slower.
+// from n ~ 12288 and 6144 from n ~ 65536, 3 <= p <= 13 with 2048 and
+// p > 13 (256-row leaves) with 1024.  Sides are multiples of the 1024-row
+// leaf; ragged ones (2560, 3584) were slower.
 int64_t auto_block(int p, int64_t m, int64_t n) {
     const int64_t s = std::max(m, n);
     if (p == 2) return s >= 65536 ? 6144 : (s >= 12288 ? 3072 : 2048);
+    if (p > 13) return 1024;  // the fp32 leaf takes 256 rows: smaller blocks keep its grid small
     return 2048;
 }
 
@@ -498,6 +500,20 @@ void ech(Ctx &X, const DMat &H, const DMat &Mo, const DMat &Ko, const DMat &Ro, 
     bool pending = false;
     ech_start(X, H, Mo, Ko, Ro, out, pending);
     ech_finish(X, out, pending);
+}
+
+// Is H, larger than a leaf, entirely zero?  One reduction and one wait: far
+// cheaper than the Chief over its leaves discovering rank 0 leaf by leaf
+// (a rank-deficient input leaves whole row blocks zero past its rank).
+static bool block_is_zero(Ctx &X, const DMat &H) {
+    if (X.dry || H.rows == 0 || H.cols == 0) return false;
+    if (H.rows <= ech_leaf_rows(X.L.p) && H.cols <= ech_leaf_cols(X.L.p)) return false;  // a leaf: just run it
+    volatile int32_t *flag = (volatile int32_t *)X.pinned;
+    *flag = 0;
+    any_nonzero(X.L, H.rows, H.cols, H.ptr, H.ld, X.info);
+    X.record();
+    X.wait_event();
+    return *flag == 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -602,6 +618,9 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
         Edel(a, std::vector<std::vector<int32_t>>(b));
 
     // ================= Step 1 =================
+    // block rows whose ECH has found no pivot in some block: their later
+    // blocks are tested for being zero before their ECH
+    std::vector<char> zero_rows(a, 0);
     int64_t t = 0;  // step counter; t % NRING picks the copy of the ClearDown outputs
     for (int i = 0; i < a; ++i) {
         for (int j = 0; j < b; ++j, ++t) {
@@ -627,7 +646,8 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
             std::vector<char> urt1_done(i + 1, 0);  // UpdateRowTrafo step (1) already queued
             if (i == 0) {
                 DMat Rd = DR[j];
-                ech(X, Cij, AM[q], AK[q], Rd, e);
+                if (!(zero_rows[i] && block_is_zero(X, Cij))) ech(X, Cij, AM[q], AK[q], Rd, e);
+                if (e.r == 0 && al > 0 && bj > 0) zero_rows[i] = 1;
                 gam[j] = e.gamma;
                 lam.assign(e.r, 1);
             } else {
@@ -653,7 +673,7 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                 // (ECH), and meanwhile the steps (1) of UpdateRow and of
                 // UpdateRowTrafo for h < i, which do not depend on its result
                 bool pending = false;
-                ech_start(X, Hh, AM[q], AK[q], Rech, e, pending);
+                if (!(zero_rows[i] && block_is_zero(X, Hh))) ech_start(X, Hh, AM[q], AK[q], Rech, e, pending);
                 if (wc > 0) {  // UpdateRow (1): Z := C + A.A x B
                     if (wn > 0) {
                         need_near();
@@ -690,6 +710,7 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
                     on(s0);
                 }
                 ech_finish(X, e, pending);
+                if (e.r == 0 && al > 0 && bj - r > 0) zero_rows[i] = 1;
                 const int64_t rp = e.r;
                 if (rp > 0) {
                     // (CEX) A.E = D.R gamma'^tr, R' = D.R gamma'_bar^tr

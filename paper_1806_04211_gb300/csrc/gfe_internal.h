@@ -121,6 +121,9 @@ void build_E(const Launch &L, int fmt, int64_t m, int64_t n, int64_t r, void *ds
 void build_T(const Launch &L, int fmt, int64_t m, int64_t r, void *dst, int64_t ldd,
              const void *M, int64_t ldm, const void *K, int64_t ldk, const int32_t *rowmap);
 void write_i64(const Launch &L, int64_t *dst, const int32_t *src, int64_t count, int64_t offset);
+// *flag := 1 if A (rows x cols, codec entries) has a non-zero entry; flag is
+// left alone otherwise (the caller zeroes it first)
+void any_nonzero(const Launch &L, int64_t rows, int64_t cols, const void *A, int64_t lda, int32_t *flag);
 
 // ---- the planner (gfe_chief.cu) ----
 struct TopResult {

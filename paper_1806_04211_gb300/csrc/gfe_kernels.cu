@@ -1515,6 +1515,35 @@ __global__ void k_write_i64(int64_t *dst, const int32_t *src, int64_t count, int
     if (t < count) dst[t] = (int64_t)src[t] + offset;
 }
 
+// any non-zero entry (either codec: zero is the all-zero pattern, and -0 is
+// never stored), 16 bytes per thread where aligned
+__global__ void k_any_nonzero(int64_t rows, int64_t bytes, const uint8_t *A, int64_t ldb, int32_t *flag) {
+    bool nz = false;
+    for (int64_t row = blockIdx.y; row < rows && !nz; row += gridDim.y) {
+        const uint8_t *r = A + row * ldb;
+        const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+        if (((uintptr_t)r & 15) == 0) {
+            const int64_t nv = bytes >> 4;
+            for (int64_t v = t0; v < nv && !nz; v += st) {
+                const uint4 q = ((const uint4 *)r)[v];
+                nz = (q.x | q.y | q.z | q.w) != 0;
+            }
+            for (int64_t c = (nv << 4) + t0; c < bytes && !nz; c += st) nz = r[c] != 0;
+        } else {
+            for (int64_t c = t0; c < bytes && !nz; c += st) nz = r[c] != 0;
+        }
+    }
+    if (nz) *flag = 1;
+}
+
+void any_nonzero(const Launch &L, int64_t rows, int64_t cols, const void *A, int64_t lda, int32_t *flag) {
+    if (rows <= 0 || cols <= 0) return;
+    const int es = codec_bytes(L.codec);
+    const int64_t bytes = cols * es;
+    k_any_nonzero<<<grid_rc(rows, (bytes + 15) / 16, 128), 128, 0, L.st>>>(rows, bytes, (const uint8_t *)A,
+                                                                             lda * es, flag);
+}
+
 void write_i64(const Launch &L, int64_t *dst, const int32_t *src, int64_t count, int64_t offset) {
     if (count <= 0) return;
     cudaEvent_t ev;

@@ -244,5 +244,10 @@ void build_T(const Launch& L, int fmt, int64_t m, int64_t r, void* dst, int64_t 
         if (fmt == 1) { uint64_t* w = (uint64_t*)dst + row * (ldd / 8) + (x >> 6); chk(w, 8, "T", true); if (!(x & 63)) *w = 0; *w |= (uint64_t)(v & 1) << (x & 63); }
         else { uint8_t* d = (uint8_t*)dst + row * ldd + x; chk(d, 1, "T", true); *d = (uint8_t)v; } }
 }
+void any_nonzero(const Launch& L, int64_t rows, int64_t cols, const void* A, int64_t lda, int32_t* flag) {
+    setL(L, "any_nonzero");
+    for (int64_t r = 0; r < rows; ++r) for (int64_t c = 0; c < cols; ++c)
+        if (get(A, r * lda + c) != 0) { chk(flag, 4, "flag", true); *flag = 1; return; }
+}
 void write_i64(const Launch&, int64_t* dst, const int32_t* src, int64_t count, int64_t offset) { for (int64_t t = 0; t < count; ++t) dst[t] = src[t] + offset; }
 }

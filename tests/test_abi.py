@@ -97,7 +97,8 @@ def test_auto_block_table():
     assert gfe.auto_block(2, 32768, 32768) == 3072
     assert gfe.auto_block(2, 100000, 100000) == 6144
     assert gfe.auto_block(7, 32768, 32768) == 2048
-    assert gfe.auto_block(251, 20000, 50000) == 2048
+    assert gfe.auto_block(251, 20000, 50000) == 1024
+    assert gfe.auto_block(13, 20000, 20000) == 2048
     for p in (2, 3, 251):
         for n in (100, 5000, 20000, 70000, 200000):
             assert gfe.auto_block(p, n, n) % 1024 == 0

@@ -214,3 +214,19 @@ def test_batch_matches_oracle_without_races(sim):
         assert np.array_equal(R[:r, :n - r], ref["R"])
     assert races(sim) == 0
     sim.gfe_set_batch_workers(0)
+
+
+@pytest.mark.parametrize("p", [7, 251, 2])
+def test_rank_deficient_wide_zero_blocks(sim, p):
+    """Past the rank whole row blocks become zero; the planner tests such
+    blocks (larger than a leaf) for zero before their ECH.  Results and
+    ordering must not change."""
+    assert sim.gfe_set_block_policy(150, 128) == 0
+    rng = np.random.RandomState(p)
+    m, n, k = 300, 700, 40
+    A = ((rng.randint(0, p, (m, k)) @ rng.randint(0, p, (k, n))) % p).astype(np.uint8)
+    if p == 2:
+        check_gf2(sim, A)
+    else:
+        check(sim, A, p)
+    sim.gfe_set_block_policy(0, 0)
