@@ -103,6 +103,23 @@ def test_parity_block_3072(p, m, n, rank, blk):
         compare_u8(A, p, gfe.echelon(A.to(DEV), p), ref)
 
 
+@pytest.mark.parametrize("p,m,n,rank,blk", [(251, 700, 3000, 100, 512), (7, 1500, 4000, 300, 1024),
+                                            (2, 3000, 6000, 500, 1024), (31, 900, 2500, 0, 512)])
+def test_parity_zero_blocks(p, m, n, rank, blk):
+    """Wide rank-deficient inputs (rank 0 included): past the rank whole row
+    blocks are zero and are skipped after one zero test; the fp32 leaf
+    (p > 13) and nested Chiefs over leaves are exercised."""
+    gfe.set_block_policy(blk, blk)
+    A = synth.matrix(p, m, n, seed=15, rank=rank) if rank else torch.zeros((m, n), dtype=torch.uint8)
+    if p == 2:
+        A = synth.matrix(p, m, n, seed=15, rank=rank)
+        ref = O.echelon_gf2(A.numpy(), m, n)
+        compare_gf2(gfe.echelon(A.to(DEV), 2, n=n), ref, m, n)
+    else:
+        ref = O.echelon(A.numpy(), p)
+        compare_u8(A, p, gfe.echelon(A.to(DEV), p), ref)
+
+
 @pytest.mark.parametrize("p,m,n,leaf_rows", [(3, 900, 300, 256), (2, 1500, 700, 128), (251, 700, 200, 512)])
 def test_parity_leaf_rows(p, m, n, leaf_rows):
     """Shorter leaf row blocks (gfe_set_leaf_rows) change the block grid, not
