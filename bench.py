@@ -172,9 +172,10 @@ def union_ms(recs):
 
 def roofline(prof, codec_bytes, trace):
     """Roofline of the dominant kernel kind of the timed region.  The
-    planner runs multiply-adds on two streams at once, so per-launch event
+    planner runs multiply-adds on several streams at once, so per-launch
     times overlap; the rate is the launches' algorithmic flops over the time
-    at least one of them ran (the union of their event intervals)."""
+    at least one of them ran (the union of their intervals, which the
+    tensor-core multiply-add stamps itself with %globaltimer)."""
     pk, src = peaks()
     kinds = ["mad_tensor", "mad_plain"]
     k = max(kinds, key=lambda x: prof["ms"][x])
@@ -193,7 +194,8 @@ def roofline(prof, codec_bytes, trace):
         return {"kernel": "k_mad_tc<%s> (tcgen05)" % ("e4m3" if codec_bytes == 1 else "bf16"), "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "peak_source": "%s bf16 sustained x %.0f" % (src, ratio),
-                "denominator": "union of the launches' event intervals" if um else "sum of launch times",
+                "denominator": ("union of the launches' intervals (%s clock)" % recs[0].get("clock", "event"))
+                if um else "sum of launch times",
                 "union_ms": um, "sum_of_launch_ms": ms,
                 "launches": launches, "avg_launch_ms": ms / launches,
                 "achieved_per_launch_avg": 2.0 * madds / (ms * 1e-3) / 1e12,

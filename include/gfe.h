@@ -248,14 +248,18 @@ gfe_status gfe_profile_read(gfe_profile *out, int32_t reset);
 /* Launch trace: while the profile is enabled and the trace holds fewer than
  * `capacity` records, every timed launch also leaves one record: its kind,
  * its shape (m x n x k for a multiply-add, rows x cols for the others,
- * k = 0), the CUDA stream it ran on and its start (relative to the first
- * traced launch) and duration, both from CUDA events.  gfe_trace_enable(0)
- * stops tracing and drops the records; gfe_trace_read copies up to `cap`
- * records to `out` (may be NULL with cap 0), sets *count to the number
- * held, and drops them all if `reset`. */
+ * k = 0), the CUDA stream it ran on and its start and duration.  The
+ * tensor-core multiply-add times itself on the device (%globaltimer at its
+ * first CTA's start and its last CTA's end, in a device buffer of `capacity`
+ * slots that gfe_trace_enable allocates), so tracing it records no events;
+ * the other kinds are timed with CUDA events.  Starts are relative to the
+ * first traced launch of the same clock (field `clock`).  gfe_trace_enable(0)
+ * stops tracing and drops the records and the buffer; gfe_trace_read waits
+ * for the device, copies up to `cap` records to `out` (may be NULL with cap
+ * 0), sets *count to the number held, and drops them all if `reset`. */
 typedef struct {
     int32_t kind;            /* as gfe_profile's index                          */
-    int32_t pad;
+    int32_t clock;           /* 0: CUDA events, 1: device %globaltimer          */
     int64_t m, n, k;
     uint64_t stream;         /* the cudaStream_t handle, as an integer          */
     double  start_ms;

@@ -48,6 +48,19 @@ static std::vector<cudaEvent_t> g_evpool;
 static int64_t g_trace_cap = 0;
 static std::vector<gfe_trace_record> g_trace;
 static cudaEvent_t g_trace_t0 = nullptr;
+// launches that time themselves on the device: a slot each in a device
+// buffer ({start, end, CTAs in, CTAs out}, %globaltimer ns), read back when
+// the profile or the trace is read
+struct DevSlot {
+    int kind;
+    int64_t m, n, k;
+    cudaStream_t st;
+};
+static uint64_t *g_dslots = nullptr;
+static int64_t g_dcap = 0, g_dnext = 0, g_dresolved = 0;
+static int g_ddev = -1;
+static std::vector<DevSlot> g_dmeta;
+static std::vector<std::pair<uint64_t, uint64_t>> g_dtimes;  // resolved {start, end}
 
 static cudaEvent_t ev_get() {
     if (!g_evpool.empty()) {
@@ -58,6 +71,43 @@ static cudaEvent_t ev_get() {
     cudaEvent_t e = nullptr;
     cudaEventCreate(&e);
     return e;
+}
+
+uint64_t *prof_device_slot(const Launch &L, Kind k, int64_t m, int64_t n, int64_t kk) {
+    if (!g_prof_on) return nullptr;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!(g_prof_mask & (1 << k)) || !g_dslots || g_dnext >= g_dcap) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != g_ddev) return nullptr;
+    g_dmeta.push_back({(int)k, m, n, kk, L.st});
+    return g_dslots + 4 * (g_dnext++);
+}
+
+void prof_count(Kind k) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.launches[k] += 1;
+}
+
+// device-timed launches issued since the last call: wait for the device,
+// fetch their slots, add their times to the profile
+static void resolve_device_locked() {
+    if (!g_dslots || g_dresolved >= g_dnext) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != g_ddev) cudaSetDevice(g_ddev);
+    cudaDeviceSynchronize();
+    std::vector<uint64_t> v((size_t)(g_dnext - g_dresolved) * 4);
+    cudaMemcpy(v.data(), g_dslots + 4 * g_dresolved, v.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (cur != g_ddev) cudaSetDevice(cur);
+    for (int64_t q = g_dresolved; q < g_dnext; ++q) {
+        const uint64_t t0 = v[(size_t)(q - g_dresolved) * 4], t1 = v[(size_t)(q - g_dresolved) * 4 + 1];
+        const DevSlot &d = g_dmeta[(size_t)q];
+        g_prof.ms[d.kind] += t1 > t0 ? (double)(t1 - t0) * 1e-6 : 0.0;
+        g_prof.timed[d.kind] += 1;
+        g_dtimes.push_back({t0, t1});
+    }
+    g_dresolved = g_dnext;
 }
 
 void prof_begin(const Launch &L, Kind k, cudaEvent_t *ev0) {
@@ -553,9 +603,21 @@ gfe_status gfe_profile_read(gfe_profile *out, int32_t reset) {
     if (!out) return (set_error("out is NULL"), GFE_EINVAL);
     std::lock_guard<std::mutex> g(g_prof_mu);
     resolve_locked();
+    resolve_device_locked();
     *out = g_prof;
     if (reset) std::memset(&g_prof, 0, sizeof g_prof);
     return GFE_OK;
+}
+
+static void drop_device_slots_locked() {
+    if (g_dslots) {
+        cudaDeviceSynchronize();
+        cudaFree(g_dslots);
+    }
+    g_dslots = nullptr;
+    g_dcap = g_dnext = g_dresolved = 0;
+    g_dmeta.clear();
+    g_dtimes.clear();
 }
 
 gfe_status gfe_trace_enable(int64_t capacity) {
@@ -566,7 +628,21 @@ gfe_status gfe_trace_enable(int64_t capacity) {
     if (g_trace_t0) g_evpool.push_back(g_trace_t0);
     g_trace_t0 = nullptr;
     g_trace_cap = capacity;
-    if (capacity) g_trace.reserve((size_t)std::min<int64_t>(capacity, 1 << 20));
+    drop_device_slots_locked();
+    if (capacity) {
+        g_trace.reserve((size_t)std::min<int64_t>(capacity, 1 << 20));
+        // device slots for the launches that time themselves (the
+        // tensor-core multiply-add)
+        if (cudaGetDevice(&g_ddev) == cudaSuccess &&
+            cudaMalloc((void **)&g_dslots, (size_t)capacity * 4 * sizeof(uint64_t)) == cudaSuccess &&
+            cudaMemset(g_dslots, 0, (size_t)capacity * 4 * sizeof(uint64_t)) == cudaSuccess) {
+            g_dcap = capacity;
+        } else {
+            if (g_dslots) cudaFree(g_dslots);
+            g_dslots = nullptr;
+            cudaGetLastError();
+        }
+    }
     return GFE_OK;
 }
 
@@ -574,13 +650,40 @@ gfe_status gfe_trace_read(gfe_trace_record *out, int64_t cap, int64_t *count, in
     if (!count || cap < 0 || (cap > 0 && !out)) return (set_error("gfe_trace_read: bad arguments"), GFE_EINVAL);
     std::lock_guard<std::mutex> g(g_prof_mu);
     resolve_locked();
-    *count = (int64_t)g_trace.size();
+    resolve_device_locked();
+    // device-timed records: starts relative to the earliest of them
+    std::vector<gfe_trace_record> all(g_trace);
+    uint64_t t0 = ~0ull;
+    for (auto &tt : g_dtimes)
+        if (tt.first && tt.first < t0) t0 = tt.first;
+    for (size_t q = 0; q < g_dtimes.size(); ++q) {
+        const DevSlot &d = g_dmeta[q];
+        gfe_trace_record r{};
+        r.kind = d.kind;
+        r.clock = 1;  // device clock
+        r.m = d.m;
+        r.n = d.n;
+        r.k = d.k;
+        r.stream = (uint64_t)(uintptr_t)d.st;
+        r.start_ms = g_dtimes[q].first >= t0 ? (double)(g_dtimes[q].first - t0) * 1e-6 : 0.0;
+        r.ms = g_dtimes[q].second > g_dtimes[q].first ? (double)(g_dtimes[q].second - g_dtimes[q].first) * 1e-6 : 0.0;
+        all.push_back(r);
+    }
+    *count = (int64_t)all.size();
     const int64_t c = std::min<int64_t>(cap, *count);
-    if (c) std::memcpy(out, g_trace.data(), (size_t)c * sizeof(gfe_trace_record));
+    if (c) std::memcpy(out, all.data(), (size_t)c * sizeof(gfe_trace_record));
     if (reset) {
         g_trace.clear();
         if (g_trace_t0) g_evpool.push_back(g_trace_t0);
         g_trace_t0 = nullptr;
+        // keep the device buffer, start its slots over
+        if (g_dslots) {
+            cudaMemset(g_dslots, 0, (size_t)g_dnext * 4 * sizeof(uint64_t));
+            cudaDeviceSynchronize();
+        }
+        g_dnext = g_dresolved = 0;
+        g_dmeta.clear();
+        g_dtimes.clear();
     }
     return GFE_OK;
 }

@@ -48,6 +48,10 @@ void prof_begin(const Launch &L, Kind k, cudaEvent_t *ev0);
 void prof_end(const Launch &L, Kind k, cudaEvent_t ev0, double madds, double bytes = 0, int64_t m = 0,
               int64_t n = 0, int64_t kk = 0);
 void prof_sync_point();
+// A device trace slot for this launch (4 words: start, end, CTA counters),
+// or null: the kernel stamps %globaltimer itself, no events are recorded
+uint64_t *prof_device_slot(const Launch &L, Kind k, int64_t m, int64_t n, int64_t kk);
+void prof_count(Kind k);  // count a launch timed on the device
 void prof_count_sync(double wait_ms);
 void prof_host_ms(double ms);
 extern bool g_prof_on;

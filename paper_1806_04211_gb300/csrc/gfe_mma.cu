@@ -155,7 +155,7 @@ constexpr int EPI_WARPS = 8;
 template <bool F8>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_mad_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int p, int M,
-             int N, int K, const void *Wv, int64_t ldw, void *Cv, int64_t ldc, int *err) {
+             int N, int K, const void *Wv, int64_t ldw, void *Cv, int64_t ldc, int *err, uint64_t *tslot) {
     using G = Cfg<F8>;
     constexpr int TBK = G::TBK, A_STAGE = G::A_STAGE, B_STAGE = G::B_STAGE, B_SLAB = G::B_SLAB;
     extern __shared__ __align__(1024) uint8_t smraw[];
@@ -168,6 +168,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ uint32_t tmem_base;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // launch trace: the first CTA to start stamps the start, the last to end
+    // the end (%globaltimer, ns); slot = {start, end, CTAs in, CTAs out}
+    if (tslot && threadIdx.x == 0 && atomicAdd((unsigned long long *)&tslot[2], 1ull) == 0ull) tslot[0] = gtimer();
     const int mt = (M + TBM - 1) / TBM, nt = (N + TBN - 1) / TBN;
     const int ntiles = mt * nt;
     const int nk = (K + TBK - 1) / TBK;
@@ -404,6 +407,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
+    if (tslot && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd((unsigned long long *)&tslot[3], 1ull) == (unsigned long long)gridDim.x - 1) tslot[1] = gtimer();
+    }
 }
 
 // Failure-detection self-test: waits (with the kernel's bounded-wait helper
@@ -527,14 +534,17 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
         int64_t ctas = g_num_sms;
         if (L.tiles_per_cta > 0) ctas = std::max<int64_t>(ctas, (tiles + L.tiles_per_cta - 1) / L.tiles_per_cta);
         const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
-        cudaEvent_t ev;
-        prof_begin(L, K_MAD_TC, &ev);
+        // timed on the device when the launch trace has a slot, else by events
+        uint64_t *tslot = prof_device_slot(L, K_MAD_TC, m, n, kk);
+        cudaEvent_t ev = nullptr;
+        if (!tslot) prof_begin(L, K_MAD_TC, &ev);
+        else prof_count(K_MAD_TC);
         if (f8)
             k_mad_tc<true><<<grid, TC_THREADS, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C,
-                                                                ldc, err);
+                                                                ldc, err, tslot);
         else
             k_mad_tc<false><<<grid, TC_THREADS, TC_SMEM, L.st>>>(ma, mb, L.p, (int)m, (int)n, (int)kk, Wk, ldwk, C,
-                                                                 ldc, err);
+                                                                 ldc, err, tslot);
         prof_end(L, K_MAD_TC, ev, (double)m * (double)n * (double)kk,
                  (double)es * ((double)m * kk + (double)kk * n + (Wk ? 2.0 : 1.0) * (double)m * n), m, n, kk);
     }

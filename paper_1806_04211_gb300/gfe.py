@@ -42,7 +42,7 @@ class GfeProfile(ctypes.Structure):
 
 
 class GfeTraceRecord(ctypes.Structure):
-    _fields_ = [("kind", _i32), ("pad", _i32), ("m", _i64), ("n", _i64), ("k", _i64), ("stream", ctypes.c_uint64),
+    _fields_ = [("kind", _i32), ("clock", _i32), ("m", _i64), ("n", _i64), ("k", _i64), ("stream", ctypes.c_uint64),
                 ("start_ms", ctypes.c_double), ("ms", ctypes.c_double)]
 
 
@@ -399,8 +399,8 @@ def trace_read(reset: bool = True) -> list:
     _check(lib().gfe_trace_read(None, 0, ctypes.byref(n), 0))
     buf = (GfeTraceRecord * max(n.value, 1))()
     _check(lib().gfe_trace_read(buf, n.value, ctypes.byref(n), 1 if reset else 0))
-    return [dict(kind=KINDS[r.kind], m=r.m, n=r.n, k=r.k, stream=r.stream, start_ms=r.start_ms, ms=r.ms)
-            for r in buf[:n.value]]
+    return [dict(kind=KINDS[r.kind], clock=("event", "device")[r.clock], m=r.m, n=r.n, k=r.k, stream=r.stream,
+                 start_ms=r.start_ms, ms=r.ms) for r in buf[:n.value]]
 
 
 class Server:
