@@ -117,21 +117,47 @@ gfe_status gfe_rank(const gfe_matrix *A, int64_t *rank_dev, int64_t *pivot_cols,
 
 /*
  * gfe_batch_echelon -- count independent matrices (any sizes, any fields)
- * echelonised concurrently: a pool of host workers (gfe_set_batch_workers,
- * default 8), each with its own CUDA stream and its own slice of the
- * workspace, takes the matrices in order; the work is ordered after what was
- * queued on `stream` before the call and `stream` waits for all of it.
+ * echelonised concurrently: small matrices (gfe_set_batch_small_max) by one
+ * launch of a kernel that gives each its own thread block, the others by a
+ * pool of host workers (gfe_set_batch_workers, default 8), each with its own
+ * CUDA stream and its own slice of the workspace, taking them in order; the
+ * work is ordered after what was queued on `stream` before the call and
+ * `stream` waits for all of it.
  * outs[i] receives the result of As[i], identical to a separate gfe_echelon
  * call.  The paper's matrices are independent problems; the concurrency is
  * the GPU-side analogue of its many workers (Section 2.1).
- * gfe_query_batch_workspace: workers x the largest single workspace.
+ * gfe_query_batch_workspace: workers x the largest single workspace of the
+ * matrices the workers take, plus m x ceil16(n) bytes (GF(2): m x
+ * ceil128(n) / 8) for each small matrix and its job table.
  */
 gfe_status gfe_query_batch_workspace(const gfe_matrix *As, int32_t count, uint32_t flags,
                                      size_t *ws_bytes);
 gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32_t count,
                              uint32_t flags, void *ws, size_t ws_bytes, void *stream);
-/* number of concurrent workers of gfe_batch_echelon (<= 0: default 8) */
+/*
+ * Matrices of a batch with at most `side` rows and columns (side <= 2048,
+ * the default) over GF(2) (GFE_BITS64) or GF(p) with 3 <= p <= 13 (GFE_U8),
+ * and no dense E / T asked for, are echelonised together by ONE kernel
+ * launch, one thread block per matrix, with no host round trip; the others
+ * go to the workers below.  side = 0 sends every matrix to the workers.
+ * GFE_EINVAL if side < 0.
+ */
+gfe_status gfe_set_batch_small_max(int32_t side);
+/* number of concurrent workers of gfe_batch_echelon (<= 0: default 8; at
+ * most GFE_MAX_BATCH_WORKERS, larger values are clamped to it) */
+#define GFE_MAX_BATCH_WORKERS 256
 gfe_status gfe_set_batch_workers(int32_t workers);
+/*
+ * How gfe_batch_echelon's workers wait for the GPU (a leaf's result, the end
+ * of a matrix): GFE_WAIT_SPIN polls (lowest latency, one host core per
+ * worker), GFE_WAIT_BLOCK sleeps on a blocking-sync event (many workers on
+ * few cores), GFE_WAIT_AUTO (the default) sleeps when there are more workers
+ * than host threads.  GFE_EINVAL for any other value.
+ */
+#define GFE_WAIT_AUTO 0
+#define GFE_WAIT_SPIN 1
+#define GFE_WAIT_BLOCK 2
+gfe_status gfe_set_wait_policy(int32_t policy);
 
 /*
  * Serving form: requests arrive one matrix at a time and are echelonised

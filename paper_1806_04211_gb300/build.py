@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgfe.so")
-SOURCES = ["gfe_kernels.cu", "gfe_mma.cu", "gfe_chief.cu", "gfe_api.cu", "gfe_server.cu", "gfe_noalloc.cu"]
+SOURCES = ["gfe_kernels.cu", "gfe_mma.cu", "gfe_chief.cu", "gfe_api.cu", "gfe_server.cu", "gfe_noalloc.cu",
+           "gfe_small.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -169,6 +169,7 @@ void prof_sync_point() {
 }
 
 void prof_count_sync(double wait_ms) {
+    if (!g_prof_on) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof.host_syncs += 1;
     g_prof.host_wait_ms += wait_ms;
@@ -362,7 +363,7 @@ static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_
                 if (!cuda_ok(cudaMemcpyAsync(dmap, map.data(), 4 * n, cudaMemcpyHostToDevice, L.st), "map"))
                     return GFE_ECUDA;
                 build_E(L, A->fmt, m, n, r, out->E, out->ldE, Ro.ptr, Ro.ld, dmap);
-                if (!cuda_ok(cudaStreamSynchronize(L.st), "sync")) return GFE_ECUDA;
+                if (!cuda_ok(host_wait(L.st), "sync")) return GFE_ECUDA;
             }
             if (wantT) {
                 map.assign(m, 0);
@@ -380,7 +381,7 @@ static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_
             }
         }
         (void)es;
-        if (!cuda_ok(cudaStreamSynchronize(L.st), "final sync")) return GFE_ECUDA;
+        if (!cuda_ok(host_wait(L.st), "final sync")) return GFE_ECUDA;
         if (!cuda_ok(cudaGetLastError(), "kernel launch")) return GFE_ECUDA;
         if (check_tc && tc_error_flag(true)) {
             set_error("a tensor-core multiply-add timed out waiting on its pipeline");
@@ -431,16 +432,77 @@ static int batch_workers(int32_t count) {
     return count < w ? (count > 0 ? count : 1) : w;
 }
 
-gfe_status gfe_query_batch_workspace(const gfe_matrix *As, int32_t count, uint32_t flags, size_t *ws_bytes) {
-    if (!ws_bytes || count < 0 || (count && !As)) return (set_error("bad batch arguments"), GFE_EINVAL);
+// GFE_WAIT_AUTO: workers sleep in their waits when there are more of them
+// than host threads
+static int g_wait_policy = GFE_WAIT_AUTO;
+
+static bool workers_sleep(int nw) {
+    if (g_wait_policy == GFE_WAIT_BLOCK) return true;
+    if (g_wait_policy == GFE_WAIT_SPIN) return false;
+    const unsigned hw = std::thread::hardware_concurrency();
+    return hw == 0 || (unsigned)nw > hw;
+}
+
+// The batch is split: matrices that fit the one-CTA kernel (gfe_small.cu)
+// and need no dense E / T are echelonised together by ONE launch; the
+// others go to the pool of workers.  Workspace: the workers' slices, then
+// each small matrix's m x ldw area, then the job table.
+static int64_t g_batch_small_max = SMALL_MAX;
+
+static bool batch_small(const gfe_matrix &A, uint32_t flags) {
+    if (flags & (GFE_WANT_DENSE_E | GFE_WANT_DENSE_T)) return false;
+    if (A.m > g_batch_small_max || A.n > g_batch_small_max) return false;
+    return small_eligible(A.p, A.fmt, A.m, A.n);
+}
+
+struct BatchPlan {
+    std::vector<int32_t> small, rest;
+    std::vector<size_t> small_off;  // offset of each small matrix's area
+    int nw = 0;
+    size_t slice = 0, small_base = 0, jobs_off = 0, total = 0;
+};
+
+static gfe_status batch_plan(const gfe_matrix *As, int32_t count, uint32_t flags, BatchPlan &P) {
     size_t best = 0;
     for (int32_t i = 0; i < count; ++i) {
+        gfe_status st = check_matrix(&As[i]);
+        if (st) return st;
+        if (batch_small(As[i], flags)) {
+            P.small.push_back(i);
+            continue;
+        }
+        P.rest.push_back(i);
         size_t w = 0;
-        gfe_status st = gfe_query_workspace(&As[i], flags, &w);
+        st = gfe_query_workspace(&As[i], flags, &w);
         if (st) return st;
         best = std::max(best, w);
     }
-    *ws_bytes = al256(best) * (size_t)batch_workers(count);
+    P.nw = P.rest.empty() ? 0 : batch_workers((int32_t)P.rest.size());
+    P.slice = al256(best);
+    size_t off = P.slice * (size_t)P.nw;
+    P.small_base = off;
+    for (int32_t i : P.small) {
+        P.small_off.push_back(off);
+        off += al256((size_t)As[i].m * (size_t)small_ldw(As[i].fmt, As[i].n));
+    }
+    P.jobs_off = off;
+    if (!P.small.empty()) off += al256(P.small.size() * sizeof(SmallJob));
+    P.total = off;
+    return GFE_OK;
+}
+
+gfe_status gfe_query_batch_workspace(const gfe_matrix *As, int32_t count, uint32_t flags, size_t *ws_bytes) {
+    if (!ws_bytes || count < 0 || (count && !As)) return (set_error("bad batch arguments"), GFE_EINVAL);
+    BatchPlan P;
+    gfe_status st = batch_plan(As, count, flags, P);
+    if (st) return st;
+    *ws_bytes = P.total;
+    return GFE_OK;
+}
+
+gfe_status gfe_set_batch_small_max(int32_t side) {
+    if (side < 0) return (set_error("bad small-matrix side"), GFE_EINVAL);
+    g_batch_small_max = std::min<int64_t>(side, SMALL_MAX);
     return GFE_OK;
 }
 
@@ -448,20 +510,83 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
                              void *ws, size_t ws_bytes, void *stream) {
     if (count < 0 || (count && (!As || !outs))) return (set_error("bad batch arguments"), GFE_EINVAL);
     if (count == 0) return GFE_OK;
-    size_t need = 0;
-    gfe_status st = gfe_query_batch_workspace(As, count, flags, &need);
+    BatchPlan P;
+    gfe_status st = batch_plan(As, count, flags, P);
     if (st) return st;
-    if (!ws || ws_bytes < need) {
-        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+    if (!ws || ws_bytes < P.total) {
+        set_error("workspace too small: need " + std::to_string(P.total) + " bytes");
         return GFE_EINVAL;
     }
-    const int nw = batch_workers(count);
-    const size_t slice = need / (size_t)nw;
+    for (int32_t i : P.small)
+        if (!outs[i].rank) return (set_error("rank output is NULL"), GFE_EINVAL);
+    const int nw = P.nw;
+    const size_t slice = P.slice;
+    const int32_t nrest = (int32_t)P.rest.size();
     int dev = 0;
     if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return GFE_ECUDA;
     cudaEvent_t start;
     if (!cuda_ok(cudaEventCreateWithFlags(&start, cudaEventDisableTiming), "event")) return GFE_ECUDA;
     cudaEventRecord(start, (cudaStream_t)stream);
+    // the small matrices: one job table, one launch on a stream of their own,
+    // the most expensive matrices first (their CTAs start first)
+    cudaStream_t small_st = nullptr;
+    cudaEvent_t small_done = nullptr;
+    if (!P.small.empty()) {
+        std::vector<SmallJob> jobs;
+        jobs.reserve(P.small.size());
+        const bool tr = (flags & GFE_WANT_TRANSFORM) != 0;
+        for (size_t q = 0; q < P.small.size(); ++q) {
+            const gfe_matrix &A = As[P.small[q]];
+            const gfe_result &o = outs[P.small[q]];
+            SmallJob J;
+            J.A = A.data;
+            J.lda = A.ld;
+            J.W = (char *)ws + P.small_off[q];
+            J.ldw = small_ldw(A.fmt, A.n);
+            J.m = (int32_t)A.m;
+            J.n = (int32_t)A.n;
+            J.p = A.p;
+            J.fmt = A.fmt;
+            J.rank = o.rank;
+            J.pcols = o.pivot_cols;
+            J.prows = o.pivot_rows;
+            J.R = o.R;
+            J.ldR = o.ldR;
+            J.M = tr ? o.M : nullptr;
+            J.ldM = o.ldM;
+            J.K = tr ? o.K : nullptr;
+            J.ldK = o.ldK;
+            jobs.push_back(J);
+        }
+        auto cost = [](const SmallJob &J) {
+            const double w = (double)J.m * J.n * std::min(J.m, J.n);
+            return J.fmt == GFE_BITS64 ? w / 32 : w;
+        };
+        std::stable_sort(jobs.begin(), jobs.end(),
+                         [&](const SmallJob &a, const SmallJob &b) { return cost(a) > cost(b); });
+        SmallJob *djobs = (SmallJob *)((char *)ws + P.jobs_off);
+        Launch L;
+        launch_for(&As[P.small[0]], flags, nullptr, L);
+        bool ok = cuda_ok(cudaStreamCreateWithFlags(&small_st, cudaStreamNonBlocking), "stream") &&
+                  cuda_ok(cudaStreamWaitEvent(small_st, start, 0), "stream wait");
+        L.st = small_st;
+        // pageable source: the call returns once the table has been staged
+        ok = ok && cuda_ok(cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(SmallJob),
+                                           cudaMemcpyHostToDevice, small_st),
+                           "job table upload");
+        if (ok) {
+            ech_small_batch(L, djobs, (int)jobs.size());
+            ok = cuda_ok(cudaGetLastError(), "small-matrix launch") &&
+                 cuda_ok(cudaEventCreateWithFlags(&small_done, cudaEventDisableTiming), "event") &&
+                 cuda_ok(cudaEventRecord(small_done, small_st), "event record");
+        }
+        if (!ok) {
+            if (small_st) cudaStreamDestroy(small_st);
+            if (small_done) cudaEventDestroy(small_done);
+            cudaEventDestroy(start);
+            return GFE_ECUDA;
+        }
+    }
     std::atomic<int32_t> next(0);
     std::mutex mu;
     gfe_status first = GFE_OK;
@@ -470,11 +595,24 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
     std::vector<cudaEvent_t> done(nw, nullptr);
     std::vector<std::thread> pool;
     const bool trafo = (flags & (GFE_WANT_TRANSFORM | GFE_WANT_DENSE_T)) != 0;
+    const bool sleep = workers_sleep(nw);
     for (int w = 0; w < nw; ++w) {
         pool.emplace_back([&, w] {
             cudaSetDevice(dev);
             cudaStream_t s = nullptr;
             gfe_status mine = GFE_OK;
+            struct WaitGuard {
+                ~WaitGuard() {
+                    if (g_wait_event) cudaEventDestroy(g_wait_event);
+                    g_wait_event = nullptr;
+                }
+            } wg;
+            if (sleep && cudaEventCreateWithFlags(&g_wait_event, cudaEventDisableTiming | cudaEventBlockingSync) !=
+                             cudaSuccess) {
+                g_wait_event = nullptr;
+                mine = GFE_ECUDA;
+                set_error("worker event set-up failed");
+            }
             if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaStreamWaitEvent(s, start, 0) != cudaSuccess) {
                 mine = GFE_ECUDA;
@@ -482,8 +620,9 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
             }
             streams[w] = s;
             while (mine == GFE_OK) {
-                const int32_t i = next.fetch_add(1);
-                if (i >= count) break;
+                const int32_t q = next.fetch_add(1);
+                if (q >= nrest) break;
+                const int32_t i = P.rest[q];
                 mine = run(&As[i], &outs[i], outs[i].rank, outs[i].pivot_cols, outs[i].pivot_rows, flags, trafo,
                            true, (char *)ws + slice * w, slice, s, false);
             }
@@ -493,7 +632,7 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
                     first = mine;
                     first_msg = gfe_last_error();
                 }
-                next.store(count);
+                next.store(nrest);
             }
             if (s) {
                 cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming);
@@ -509,6 +648,11 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
         }
         if (streams[w]) cudaStreamDestroy(streams[w]);
     }
+    if (small_done) {
+        cudaStreamWaitEvent((cudaStream_t)stream, small_done, 0);
+        cudaEventDestroy(small_done);
+        cudaStreamDestroy(small_st);
+    }
     cudaEventDestroy(start);
     if (first != GFE_OK) {
         set_error(first_msg);
@@ -521,8 +665,14 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
     return GFE_OK;
 }
 
+gfe_status gfe_set_wait_policy(int32_t policy) {
+    if (policy < GFE_WAIT_AUTO || policy > GFE_WAIT_BLOCK) return (set_error("bad wait policy"), GFE_EINVAL);
+    g_wait_policy = policy;
+    return GFE_OK;
+}
+
 gfe_status gfe_set_batch_workers(int32_t workers) {
-    g_batch_workers = workers > 0 ? (workers > 64 ? 64 : workers) : 0;
+    g_batch_workers = workers > 0 ? (workers > GFE_MAX_BATCH_WORKERS ? GFE_MAX_BATCH_WORKERS : workers) : 0;
     return GFE_OK;
 }
 

@@ -253,10 +253,10 @@ struct Ctx {
     void sync() {
         if (dry) return;
         const double t0 = now_ms();
-        check(cudaStreamSynchronize(main_st), "cudaStreamSynchronize");
+        check(host_wait(main_st), "cudaStreamSynchronize");
         for (auto &lv : levels) {
-            if (lv.s1) check(cudaStreamSynchronize(lv.s1), "cudaStreamSynchronize");
-            if (lv.s2) check(cudaStreamSynchronize(lv.s2), "cudaStreamSynchronize");
+            if (lv.s1) check(host_wait(lv.s1), "cudaStreamSynchronize");
+            if (lv.s2) check(host_wait(lv.s2), "cudaStreamSynchronize");
         }
         check(cudaGetLastError(), "kernel launch");
         sg.top = 0;
@@ -425,6 +425,14 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
 int64_t g_block_threshold = 0, g_block_big = 0;
 // rows of a leaf block in the leaf grid; 0: auto_leaf_rows
 int64_t g_leaf_rows = 0;
+
+thread_local cudaEvent_t g_wait_event = nullptr;
+
+cudaError_t host_wait(cudaStream_t s) {
+    if (!g_wait_event) return cudaStreamSynchronize(s);
+    cudaError_t e = cudaEventRecord(g_wait_event, s);
+    return e != cudaSuccess ? e : cudaEventSynchronize(g_wait_event);
+}
 
 int64_t auto_leaf_rows(int p, int64_t m, int64_t n) {
     (void)m;
@@ -1011,7 +1019,8 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
         ~HpGuard() { hp_release(dev, s); }
     } hpg;
     if (!dry) {
-        X.check(cudaEventCreateWithFlags(&evg.e, cudaEventDisableTiming), "cudaEventCreate");
+        X.check(cudaEventCreateWithFlags(&evg.e, cudaEventDisableTiming | (g_wait_event ? cudaEventBlockingSync : 0)),
+                "cudaEventCreate");
         X.ev = evg.e;
         hpg.dev = X.dev;
         hpg.s = hp_acquire(X.dev);

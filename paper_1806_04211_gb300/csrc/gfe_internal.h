@@ -83,6 +83,32 @@ int ech_leaf_cols(int p);
 void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64_t ldh,
               int32_t *info, void *M, int64_t ldm, void *K, int64_t ldk, void *R, int64_t ldr);
 
+// Batched form for small matrices (gfe_small.cu): one launch, one CTA per
+// matrix, the whole echelonisation with transformation inside the CTA.
+// A job reads A in the API storage, works in place in W (m rows of ldw
+// bytes: one byte per entry, or GF(2) words), and writes r, Ups, rho and
+// R, M, K in the API storage (any of pcols, prows, R, M, K may be null).
+constexpr int SMALL_MAX = 2048;  // rows and columns of a small matrix
+constexpr int SMALL_MAX_P = 13;  // byte entries with lazy reduction: (p-1)^2 + (p-1) <= 255
+struct SmallJob {
+    const void *A;
+    int64_t lda;  // bytes
+    void *W;
+    int64_t ldw;  // bytes, a multiple of 16 (small_ldw)
+    int32_t m, n, p, fmt;
+    int64_t *rank, *pcols, *prows;
+    void *R, *M, *K;
+    int64_t ldR, ldM, ldK;  // bytes
+};
+// fmt: 0 = one byte per entry (3 <= p <= SMALL_MAX_P), 1 = GF(2) words
+inline bool small_eligible(int p, int fmt, int64_t m, int64_t n) {
+    if (m <= 0 || n <= 0 || m > SMALL_MAX || n > SMALL_MAX) return false;
+    return fmt == 1 ? p == 2 : (fmt == 0 && p >= 3 && p <= SMALL_MAX_P);
+}
+// workspace row pitch (bytes) of a small matrix: 16-byte vectors
+inline int64_t small_ldw(int fmt, int64_t n) { return fmt == 1 ? (n + 127) / 128 * 16 : (n + 15) / 16 * 16; }
+void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count);
+
 // An index array for a gather: a device copy, or, when it has at most
 // MAP_INLINE entries, the host array itself, which is then passed by value
 // with the launch (no separate upload on the stream).
@@ -142,6 +168,11 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
                int64_t *syncs);
 
 extern int64_t g_block_threshold, g_block_big, g_leaf_rows;
+// A host thread that set g_wait_event (a cudaEventBlockingSync event) sleeps
+// in its waits for the GPU instead of spinning: the batched form runs more
+// workers than the host has cores.  host_wait(s) waits for stream s either way.
+extern thread_local cudaEvent_t g_wait_event;
+cudaError_t host_wait(cudaStream_t s);
 int64_t auto_leaf_rows(int p, int64_t m, int64_t n);
 int64_t auto_block(int p, int64_t m, int64_t n);
 

@@ -1291,11 +1291,18 @@ __global__ void k_import_u8_vec(int p, int64_t rows, int64_t cols, typename Cd<C
     }
 }
 
-// codec -> residues [0, p), 16 entries per thread
+// codec -> residues [0, p), 16 entries per thread; e4m3 bytes go through a
+// 256-entry table (res(dec(b)) for every byte b), which keeps the kernel on
+// HBM rather than on the integer pipe
 template <int C>
 __global__ void k_export_u8_vec(int p, int64_t rows, int64_t cols, uint8_t *dst, int64_t ldd,
                                 const typename Cd<C>::T *src, int64_t lds) {
     using T = typename Cd<C>::T;
+    __shared__ uint8_t tab[256];
+    if constexpr (sizeof(T) == 1) {
+        for (int x = threadIdx.x; x < 256; x += blockDim.x) tab[x] = (uint8_t)res(Cd<C>::dec((T)x), p);
+        __syncthreads();
+    }
     const int64_t nv = (cols + 15) >> 4;
     for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
         const T *sr = src + row * lds;
@@ -1312,7 +1319,12 @@ __global__ void k_export_u8_vec(int p, int64_t rows, int64_t cols, uint8_t *dst,
                 for (int j = 0; j < 4; ++j) {
                     o[j] = 0;
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) o[j] |= (uint32_t)res(Cd<C>::dec(e[4 * j + b]), p) << (8 * b);
+                    for (int b = 0; b < 4; ++b) {
+                        uint32_t r;
+                        if constexpr (sizeof(T) == 1) r = tab[e[4 * j + b]];
+                        else r = (uint32_t)res(Cd<C>::dec(e[4 * j + b]), p);
+                        o[j] |= r << (8 * b);
+                    }
                 }
                 *(uint4 *)(dr + c0) = make_uint4(o[0], o[1], o[2], o[3]);
             } else {

@@ -8,6 +8,7 @@ fallback implementation.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 
@@ -60,6 +61,8 @@ SIGNATURES = {
     "gfe_batch_echelon": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), _i32, ctypes.c_uint32,
                                  _vp, ctypes.c_size_t, _vp]),
     "gfe_set_batch_workers": (_i32, [_i32]),
+    "gfe_set_wait_policy": (_i32, [_i32]),
+    "gfe_set_batch_small_max": (_i32, [_i32]),
     "gfe_server_create": (_i32, [ctypes.POINTER(_vp), ctypes.c_size_t, _i32, _i32]),
     "gfe_submit": (_i32, [_vp, ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), ctypes.c_uint32, _vp,
                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -265,6 +268,65 @@ def _cut_result(mat: GfeMatrix, bufs: dict, r: int) -> dict:
     return d
 
 
+WAIT_POLICIES = {"auto": 0, "spin": 1, "block": 2}
+
+
+def set_wait_policy(policy: str) -> None:
+    """gfe_set_wait_policy: how the batched form's workers wait ("auto", "spin", "block")."""
+    _check(lib().gfe_set_wait_policy(WAIT_POLICIES[policy]))
+
+
+def set_batch_small_max(side: int = 2048) -> None:
+    """gfe_set_batch_small_max: largest side of a batch matrix taken by the one-launch kernel (0: none)."""
+    _check(lib().gfe_set_batch_small_max(side))
+
+
+def _alloc_results(args, dev, transform: bool):
+    """Result buffers of a whole batch carved out of three allocations (index
+    arrays, byte matrices, GF(2) words): same shapes as _alloc_result."""
+    shapes = []
+    n_idx = n_u8 = n_w = 0
+    for mat in args:
+        m, nn = mat.m, mat.n
+        mn = min(m, nn)
+        bits = mat.fmt == GFE_BITS64
+        mats = [("R", max(mn, 1), max(nn, 1))]
+        if transform:
+            mats += [("M", max(mn, 1), max(mn, 1)), ("K", max(m, 1), max(mn, 1))]
+        mats = [(k, r, words_per_row(c) if bits else c) for k, r, c in mats]
+        shapes.append((bits, max(mn, 1), mats))
+        n_idx += 1 + 2 * max(mn, 1)
+        for _, r, c in mats:
+            if bits:
+                n_w += r * c
+            else:
+                n_u8 += r * c
+    idx = torch.empty(n_idx, dtype=torch.int64, device=dev)
+    u8 = torch.empty(n_u8, dtype=torch.uint8, device=dev)
+    wb = torch.zeros(n_w, dtype=torch.int64, device=dev)  # rows are padded to whole 16-byte pairs of words
+    out, oi, ou, ow = [], 0, 0, 0
+    for bits, k, mats in shapes:
+        bufs = dict(rank=idx[oi:oi + 1], ups=idx[oi + 1:oi + 1 + k], rho=idx[oi + 1 + k:oi + 1 + 2 * k])
+        oi += 1 + 2 * k
+        for key, r, c in mats:
+            if bits:
+                bufs[key] = wb[ow:ow + r * c].view(r, c)
+                ow += r * c
+            else:
+                bufs[key] = u8[ou:ou + r * c].view(r, c)
+                ou += r * c
+        es = 8 if bits else 1
+
+        def ld(t):
+            return 0 if t is None else t.stride(0) * es
+
+        res = GfeResult(bufs["rank"].data_ptr(), bufs["ups"].data_ptr(), bufs["rho"].data_ptr(), _ptr(bufs["R"]),
+                        ld(bufs["R"]), _ptr(bufs.get("M")), ld(bufs.get("M")), _ptr(bufs.get("K")),
+                        ld(bufs.get("K")), None, 0, None, 0)
+        out.append((bufs, res))
+    return out, idx
+
+
 def batch_echelon(mats, transform: bool = True, impl: str = "tensor", workers: int | None = None, stream=None):
     """gfe_batch_echelon over a list of (A, p) or (A, p, n) tuples; returns a list of dicts."""
     args = [matrix_arg(*mt) if len(mt) == 3 else matrix_arg(mt[0], mt[1]) for mt in mats]
@@ -275,14 +337,18 @@ def batch_echelon(mats, transform: bool = True, impl: str = "tensor", workers: i
     if workers is not None:
         _check(lib().gfe_set_batch_workers(workers))
     arr = (GfeMatrix * len(args))(*args)
-    allocs = [_alloc_result(a, dev, transform) for a in args]
+    allocs, idx = _alloc_results(args, dev, transform)
     ress = (GfeResult * len(args))(*[r for _, r in allocs])
     need = ctypes.c_size_t(0)
     _check(lib().gfe_query_batch_workspace(arr, len(args), flags, ctypes.byref(need)))
     ws = _workspace(need.value, dev)
     _check(lib().gfe_batch_echelon(arr, ress, len(args), flags, ws.data_ptr(), ws.numel(), _stream(stream)))
-    ranks = torch.stack([b["rank"] for b, _ in allocs]).cpu().tolist()
-    return [_cut_result(a, b, int(r[0])) for a, (b, _), r in zip(args, allocs, ranks)]
+    at = [0]
+    for a in args[:-1]:
+        at.append(at[-1] + 1 + 2 * max(min(a.m, a.n), 1))
+    with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+        ranks = idx[torch.tensor(at, device=dev)].cpu().tolist()
+    return [_cut_result(a, b, int(r)) for a, (b, _), r in zip(args, allocs, ranks)]
 
 
 def rank(A: torch.Tensor, p: int, n: int | None = None, impl: str = "tensor", stream=None) -> dict:

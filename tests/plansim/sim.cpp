@@ -249,5 +249,64 @@ void any_nonzero(const Launch& L, int64_t rows, int64_t cols, const void* A, int
     for (int64_t r = 0; r < rows; ++r) for (int64_t c = 0; c < cols; ++c)
         if (get(A, r * lda + c) != 0) { chk(flag, 4, "flag", true); *flag = 1; return; }
 }
+// the one-launch small-matrix batch: every job's result from its definition
+// (column-by-column Gauss-Jordan on [A | 1] with the topmost available row as
+// pivot, pivots scaled to -1), written in the API storage; the workspace
+// area of a job is marked written, as the kernel works in place there
+void ech_small_batch(const Launch& L, const SmallJob* jobs, int count) {
+    setL(L, "ech_small_batch");
+    chk(jobs, sizeof(SmallJob) * count, "jobs");
+    for (int q = 0; q < count; ++q) {
+        const SmallJob& J = jobs[q];
+        const int m = J.m, n = J.n, p = J.p;
+        const bool bits = J.fmt == 1;
+        chk(J.W, (size_t)m * J.ldw, "small ws", true);
+        std::vector<std::vector<int>> B(m, std::vector<int>(n + m, 0));
+        for (int y = 0; y < m; ++y) {
+            for (int c = 0; c < n; ++c) {
+                if (bits) { const uint64_t* w = (const uint64_t*)((const char*)J.A + y * J.lda) + (c >> 6); chk(w, 8, "small A"); B[y][c] = (int)((*w >> (c & 63)) & 1); }
+                else { const uint8_t* b = (const uint8_t*)J.A + y * J.lda + c; chk(b, 1, "small A"); B[y][c] = *b % p; }
+            }
+            B[y][n + y] = 1;
+        }
+        std::vector<int> isp(m, 0), pr, pc;  // pivot rows / columns in pivot order
+        for (int c = 0; c < n; ++c) {
+            int x = -1;
+            for (int y = 0; y < m; ++y) if (!isp[y] && B[y][c]) { x = y; break; }
+            if (x < 0) continue;
+            const int s = (p - inv(B[x][c], p)) % p;
+            for (auto& v : B[x]) v = v * s % p;
+            for (int y = 0; y < m; ++y) if (y != x && B[y][c]) { const int f = B[y][c]; for (int k = 0; k < n + m; ++k) B[y][k] = (B[y][k] + f * B[x][k]) % p; }
+            isp[x] = 1; pr.push_back(x); pc.push_back(c);
+        }
+        const int r = (int)pc.size();
+        std::vector<int> rho, rhob, ups = pc, upsb;
+        for (int y = 0; y < m; ++y) (isp[y] ? rho : rhob).push_back(y);
+        { size_t l = 0; for (int c = 0; c < n; ++c) { if (l < pc.size() && pc[l] == c) ++l; else upsb.push_back(c); } }
+        chk(J.rank, 8, "rank", true); *J.rank = r;
+        for (int l = 0; l < r; ++l) {
+            if (J.pcols) { chk(J.pcols + l, 8, "pcols", true); J.pcols[l] = ups[l]; }
+            if (J.prows) { chk(J.prows + l, 8, "prows", true); J.prows[l] = rho[l]; }
+        }
+        auto out = [&](void* base, int64_t ld, int row, int col, int v) {
+            if (bits) {
+                uint64_t* w = (uint64_t*)((char*)base + row * ld) + (col >> 6); chk(w, 8, "small out", true);
+                *w = (*w & ~(1ull << (col & 63))) | ((uint64_t)(v & 1) << (col & 63));
+            } else { uint8_t* b = (uint8_t*)base + row * ld + col; chk(b, 1, "small out", true); *b = (uint8_t)v; }
+        };
+        for (int l = 0; l < r; ++l) {  // pivot l (ascending column) sits in row pr[l]
+            if (J.R) for (int t = 0; t < n - r; ++t) out(J.R, J.ldR, l, t, B[pr[l]][upsb[t]]);
+            if (J.M) for (int s2 = 0; s2 < r; ++s2) out(J.M, J.ldM, l, s2, B[pr[l]][n + rho[s2]]);
+        }
+        if (J.K) for (int t = 0; t < m - r; ++t) for (int s2 = 0; s2 < r; ++s2) out(J.K, J.ldK, t, s2, B[rhob[t]][n + rho[s2]]);
+        if (bits) {  // pad bits of every written output word are 0
+            auto pad = [&](void* base, int64_t ld, int rows, int cols) {
+                if (!base || cols <= 0 || !(cols & 63)) return;
+                for (int y = 0; y < rows; ++y) { uint64_t* w = (uint64_t*)((char*)base + y * ld) + (cols >> 6); *w &= (1ull << (cols & 63)) - 1; }
+            };
+            pad(J.R, J.ldR, r, n - r); pad(J.M, J.ldM, r, r); pad(J.K, J.ldK, m - r, r);
+        }
+    }
+}
 void write_i64(const Launch&, int64_t* dst, const int32_t* src, int64_t count, int64_t offset) { for (int64_t t = 0; t < count; ++t) dst[t] = src[t] + offset; }
 }

@@ -90,6 +90,14 @@ def test_block_policy_validation():
     gfe.set_block_policy()
 
 
+def test_wait_policy_validation():
+    for bad in (-1, 3):
+        with pytest.raises(gfe.GfeError):
+            gfe._check(gfe.lib().gfe_set_wait_policy(bad))
+    for name in ("spin", "block", "auto"):
+        gfe.set_wait_policy(name)
+
+
 def test_auto_block_table():
     """The default policy's measured table: GF(2) grows with the size, larger
     fields keep 2048; every side is a multiple of the 1024-row leaf."""

@@ -173,10 +173,13 @@ def test_planner_sim_detects_a_planted_race(sim):
     assert races(sim) == 0
 
 
-def test_batch_matches_oracle_without_races(sim):
+@pytest.mark.parametrize("policy", [1, 2])
+def test_batch_matches_oracle_without_races(sim, policy):
     """gfe_batch_echelon: two workers, each on its own stream with its own
-    side streams and workspace slice, fenced to the caller's stream."""
+    side streams and workspace slice, fenced to the caller's stream; the
+    workers either poll (1) or wait on their own blocking event (2)."""
     assert sim.gfe_set_batch_workers(2) == 0
+    assert sim.gfe_set_wait_policy(policy) == 0
     rng = np.random.RandomState(5)
     mats = [(rng.randint(0, p, (rng.randint(1, 150), rng.randint(1, 150))).astype(np.uint8), p)
             for p in [3, 5, 7, 251, 2, 3, 11, 13]]
@@ -214,6 +217,7 @@ def test_batch_matches_oracle_without_races(sim):
         assert np.array_equal(R[:r, :n - r], ref["R"])
     assert races(sim) == 0
     sim.gfe_set_batch_workers(0)
+    sim.gfe_set_wait_policy(0)
 
 
 @pytest.mark.parametrize("p", [7, 251, 2])
