@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain CUDA-core comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched (C4) and served (C5) legs")
-    ap.add_argument("--c4", type=int, default=512, help="matrices of the batched leg")
+    ap.add_argument("--c4", type=int, default=4096, help="matrices of the batched leg")
     ap.add_argument("--c5", type=int, default=120, help="measured requests of the serving leg")
     ap.add_argument("--no-c3", action="store_true", help="skip the C3 tensor-vs-plain leg")
     return ap.parse_args()
@@ -262,28 +262,40 @@ def c5_requests(count, seed=1):
     return out
 
 
-def bench_batched(dev, count):
-    """C4 sample: one gfe_batch_echelon call vs the plain per-matrix path."""
+def bench_batched(dev, count, plain_count=512):
+    """C4: gfe_batch_echelon over `count` matrices of the seeded draw (median
+    of three calls after one untimed call) vs the plain per-matrix path on the
+    first `plain_count`.  The library sends a matrix of side <= 2048 and work
+    m n min(m,n) <= 4e9 over GF(2) or GF(p <= 13) to its one-launch kernel
+    (one thread block per matrix) and the rest to its blocked planner."""
     import torch
     from paper_1806_04211_gb300 import gfe, synth
     specs = c4_matrices(count)
     mats = [(synth.matrix(p, m, n, seed=5000 + i, rank=rk, device=dev), p, n) for i, (p, m, n, rk) in enumerate(specs)]
     units = float(sum(m * n * min(m, n) for p, m, n, rk in specs))
-    gfe.batch_echelon(mats[:16])
+    one_launch = sum(1 for p, m, n, rk in specs if m * n * min(m, n) <= 4e9 and (p == 2 or p <= 13))
+    gfe.batch_echelon(mats)
     torch.cuda.synchronize()
-    t = time.perf_counter()
-    res = gfe.batch_echelon(mats, workers=32)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t
+    times = []
+    for _ in range(3):
+        t = time.perf_counter()
+        res = gfe.batch_echelon(mats)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    tb = sorted(times)[1]
     madds = float(sum(m * n * d["rank"] for (p, m, n, rk), d in zip(specs, res)))
+    pc = min(plain_count, count)
     t = time.perf_counter()
-    for A, p, n in mats:
+    for A, p, n in mats[:pc]:
         gfe.echelon(A, p, n=n, impl="plain")
     torch.cuda.synchronize()
     tp = time.perf_counter() - t
-    return {"matrices": count, "of": 4096, "batched_matrices_per_s": count / tb, "plain_matrices_per_s": count / tp,
-            "speedup": tp / tb, "batched_madds_per_s": madds / tb, "workers": 32,
-            "sample": "first %d of the seeded C4 draw (sum m*n*min(m,n) = %.3g)" % (count, units)}
+    return {"matrices": count, "of": 4096, "batched_matrices_per_s": count / tb, "plain_matrices_per_s": pc / tp,
+            "speedup": (tp / pc) / (tb / count), "batched_madds_per_s": madds / tb, "wall_ms": tb * 1e3,
+            "wall_ms_runs": [x * 1e3 for x in times], "one_launch_matrices": one_launch,
+            "planner_matrices": count - one_launch, "plain_sample": pc,
+            "sample": "seeded C4 draw, %d matrices (sum m*n*min(m,n) = %.3g), median of 3 calls; plain path "
+                      "timed on the first %d" % (count, units, pc)}
 
 
 C5_WORKERS = 12

@@ -447,11 +447,17 @@ static bool workers_sleep(int nw) {
 // and need no dense E / T are echelonised together by ONE launch; the
 // others go to the pool of workers.  Workspace: the workers' slices, then
 // each small matrix's m x ldw area, then the job table.
+// A matrix whose work m n min(m,n) is above the cut-off would keep one SM
+// busy long after the others are done (one CTA runs it at about 2e11
+// multiply-adds/s); the blocked Chief spreads it over the whole GPU.
+constexpr double SMALL_WORK_DEFAULT = 4e9;
 static int64_t g_batch_small_max = SMALL_MAX;
+static double g_batch_small_work = SMALL_WORK_DEFAULT;
 
 static bool batch_small(const gfe_matrix &A, uint32_t flags) {
     if (flags & (GFE_WANT_DENSE_E | GFE_WANT_DENSE_T)) return false;
     if (A.m > g_batch_small_max || A.n > g_batch_small_max) return false;
+    if ((double)A.m * (double)A.n * (double)std::min(A.m, A.n) > g_batch_small_work) return false;
     return small_eligible(A.p, A.fmt, A.m, A.n);
 }
 
@@ -500,9 +506,10 @@ gfe_status gfe_query_batch_workspace(const gfe_matrix *As, int32_t count, uint32
     return GFE_OK;
 }
 
-gfe_status gfe_set_batch_small_max(int32_t side) {
+gfe_status gfe_set_batch_small_max(int32_t side, double max_work) {
     if (side < 0) return (set_error("bad small-matrix side"), GFE_EINVAL);
     g_batch_small_max = std::min<int64_t>(side, SMALL_MAX);
+    g_batch_small_work = max_work > 0 ? max_work : SMALL_WORK_DEFAULT;
     return GFE_OK;
 }
 
@@ -527,10 +534,11 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
     cudaEvent_t start;
     if (!cuda_ok(cudaEventCreateWithFlags(&start, cudaEventDisableTiming), "event")) return GFE_ECUDA;
     cudaEventRecord(start, (cudaStream_t)stream);
-    // the small matrices: one job table, one launch on a stream of their own,
-    // the most expensive matrices first (their CTAs start first)
-    cudaStream_t small_st = nullptr;
-    cudaEvent_t small_done = nullptr;
+    // the small matrices: one job table, one launch per storage format, each
+    // on a stream of its own, the most expensive matrices first (their CTAs
+    // start first)
+    cudaStream_t small_st[2] = {nullptr, nullptr};
+    cudaEvent_t small_done[2] = {nullptr, nullptr};
     if (!P.small.empty()) {
         std::vector<SmallJob> jobs;
         jobs.reserve(P.small.size());
@@ -562,27 +570,43 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
             const double w = (double)J.m * J.n * std::min(J.m, J.n);
             return J.fmt == GFE_BITS64 ? w / 32 : w;
         };
-        std::stable_sort(jobs.begin(), jobs.end(),
-                         [&](const SmallJob &a, const SmallJob &b) { return cost(a) > cost(b); });
+        std::stable_sort(jobs.begin(), jobs.end(), [&](const SmallJob &a, const SmallJob &b) {
+            return a.fmt != b.fmt ? a.fmt < b.fmt : cost(a) > cost(b);
+        });
+        const int n_u8 = (int)(std::find_if(jobs.begin(), jobs.end(),
+                                            [](const SmallJob &J) { return J.fmt == GFE_BITS64; }) -
+                               jobs.begin());
+        const int nfmt[2] = {n_u8, (int)jobs.size() - n_u8};
         SmallJob *djobs = (SmallJob *)((char *)ws + P.jobs_off);
         Launch L;
         launch_for(&As[P.small[0]], flags, nullptr, L);
-        bool ok = cuda_ok(cudaStreamCreateWithFlags(&small_st, cudaStreamNonBlocking), "stream") &&
-                  cuda_ok(cudaStreamWaitEvent(small_st, start, 0), "stream wait");
-        L.st = small_st;
+        bool ok = cuda_ok(cudaStreamCreateWithFlags(&small_st[0], cudaStreamNonBlocking), "stream") &&
+                  cuda_ok(cudaStreamWaitEvent(small_st[0], start, 0), "stream wait");
         // pageable source: the call returns once the table has been staged
         ok = ok && cuda_ok(cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(SmallJob),
-                                           cudaMemcpyHostToDevice, small_st),
+                                           cudaMemcpyHostToDevice, small_st[0]),
                            "job table upload");
-        if (ok) {
-            ech_small_batch(L, djobs, (int)jobs.size());
+        if (ok && nfmt[1]) {  // GF(2) on a second stream, once the table is on the device
+            cudaEvent_t up = nullptr;
+            ok = cuda_ok(cudaStreamCreateWithFlags(&small_st[1], cudaStreamNonBlocking), "stream") &&
+                 cuda_ok(cudaEventCreateWithFlags(&up, cudaEventDisableTiming), "event") &&
+                 cuda_ok(cudaEventRecord(up, small_st[0]), "event record") &&
+                 cuda_ok(cudaStreamWaitEvent(small_st[1], up, 0), "stream wait");
+            if (up) cudaEventDestroy(up);
+        }
+        for (int f = 0; ok && f < 2; ++f) {
+            if (!nfmt[f]) continue;
+            L.st = small_st[f];
+            ech_small_batch(L, djobs + (f ? n_u8 : 0), nfmt[f], f ? GFE_BITS64 : GFE_U8);
             ok = cuda_ok(cudaGetLastError(), "small-matrix launch") &&
-                 cuda_ok(cudaEventCreateWithFlags(&small_done, cudaEventDisableTiming), "event") &&
-                 cuda_ok(cudaEventRecord(small_done, small_st), "event record");
+                 cuda_ok(cudaEventCreateWithFlags(&small_done[f], cudaEventDisableTiming), "event") &&
+                 cuda_ok(cudaEventRecord(small_done[f], small_st[f]), "event record");
         }
         if (!ok) {
-            if (small_st) cudaStreamDestroy(small_st);
-            if (small_done) cudaEventDestroy(small_done);
+            for (int f = 0; f < 2; ++f) {
+                if (small_st[f]) cudaStreamDestroy(small_st[f]);
+                if (small_done[f]) cudaEventDestroy(small_done[f]);
+            }
             cudaEventDestroy(start);
             return GFE_ECUDA;
         }
@@ -648,10 +672,12 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
         }
         if (streams[w]) cudaStreamDestroy(streams[w]);
     }
-    if (small_done) {
-        cudaStreamWaitEvent((cudaStream_t)stream, small_done, 0);
-        cudaEventDestroy(small_done);
-        cudaStreamDestroy(small_st);
+    for (int f = 0; f < 2; ++f) {
+        if (small_done[f]) {
+            cudaStreamWaitEvent((cudaStream_t)stream, small_done[f], 0);
+            cudaEventDestroy(small_done[f]);
+        }
+        if (small_st[f]) cudaStreamDestroy(small_st[f]);
     }
     cudaEventDestroy(start);
     if (first != GFE_OK) {

@@ -107,7 +107,8 @@ inline bool small_eligible(int p, int fmt, int64_t m, int64_t n) {
 }
 // workspace row pitch (bytes) of a small matrix: 16-byte vectors
 inline int64_t small_ldw(int fmt, int64_t n) { return fmt == 1 ? (n + 127) / 128 * 16 : (n + 15) / 16 * 16; }
-void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count);
+// launches the kernel for count jobs of one storage format (fmt)
+void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int fmt);
 
 // An index array for a gather: a device copy, or, when it has at most
 // MAP_INLINE entries, the host array itself, which is then passed by value

@@ -18,21 +18,27 @@
 //     instead, and every later row operation updates it with the rest of the
 //     row (the classical in-place Gauss-Jordan inverse).  The workspace is
 //     then just the m x n matrix;
-//   * GF(p), 3 <= p <= 13: one byte per entry, four entries per 32-bit word,
-//     one integer multiply-add updates four; entries are reduced lazily
-//     (every klazy pivot steps, while p-1 + klazy (p-1)^2 <= 255 keeps every
-//     byte below 256), and every test of an entry for zero reduces it first;
-//   * GF(2): 64 columns per word; eliminating with pivot row i is an XOR of
-//     row i, minus its bit c, into every row with bit c set (that bit then
-//     holds the transformation entry, 1);
+//   * GF(p), 3 <= p <= 13, one byte per entry, blocked by panels of BK
+//     columns (the delayed update of the paper's blocked scheme, inside one
+//     CTA): the panel is eliminated in shared memory, one thread per row,
+//     with bytes reduced lazily (every klazy pivot steps, while
+//     p-1 + klazy (p-1)^2 <= 255 keeps every byte below 256); its pivot
+//     columns then hold the coefficients with which each row combines the
+//     panel's pivot rows, and the rest of every row is updated in ONE pass
+//     as a rank-kp multiply-add (two entries per 32-bit word in 16-bit
+//     lanes, exact reduction at the end), so each row is read and written
+//     once per panel instead of once per pivot;
+//   * GF(2), unblocked: 64 columns per word; eliminating with pivot row i is
+//     an XOR of row i, minus its bit c, into every row with bit c set (that
+//     bit then holds the transformation entry, 1);
 //   * the search for the next column's pivot row is fused into the update of
-//     the rows (each warp tests the entry it has just written), so a pivot
-//     step is one pass over the matrix and three CTA barriers.
-// The matrix lives in the workspace (HBM / L2); one warp updates one row
-// with 16-byte accesses (bytes) or one word per lane (GF(2)).
+//     the rows (each thread tests the entry it has just written), so a pivot
+//     step is one pass and three CTA barriers.
+// The matrix lives in the workspace (HBM / L2).
 #include "gfe.h"
 #include "gfe_internal.h"
 
+#include <atomic>
 #include <climits>
 
 namespace gfe {
@@ -53,14 +59,16 @@ struct SmallShared {
     int r;
 };
 
-// minimum of v over the CTA (every thread calls it, every thread gets it)
-__device__ __forceinline__ int cta_min(int v, SmallShared &S) {
+// minimum of v over the CTA of WARPS warps (every thread calls it, every
+// thread gets it); wmin holds WARPS ints of shared memory
+template <int WARPS>
+__device__ __forceinline__ int cta_min(int v, int *wmin) {
     v = __reduce_min_sync(0xffffffffu, v);
-    if ((threadIdx.x & 31) == 0) S.wmin[threadIdx.x >> 5] = v;
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
     __syncthreads();
-    int r = S.wmin[0];
+    int r = wmin[0];
 #pragma unroll
-    for (int w = 1; w < SM_WARPS; ++w) r = min(r, S.wmin[w]);
+    for (int w = 1; w < WARPS; ++w) r = min(r, wmin[w]);
     __syncthreads();
     return r;
 }
@@ -100,26 +108,58 @@ __device__ __forceinline__ uint32_t clear_byte(uint32_t x, int q, int base) {
     return (q >= base && q < base + 4) ? x & ~(0xFFu << (8 * (q - base))) : x;
 }
 
-// ---- GF(p), 3 <= p <= 13, one byte per entry -------------------------------
-__device__ void small_u8(const SmallJob &J, SmallShared &S) {
+// ---- GF(p), 3 <= p <= 13: one byte per entry, panels of BK columns --------
+constexpr int BK = 32;             // panel width: two 16-byte vectors per row
+constexpr int U8_THREADS = 1024;   // one thread per row (two rows above 1024) in the panel
+constexpr int U8_WARPS = U8_THREADS / 32;
+
+struct U8Shared {
+    uint8_t P[SMALL_MAX * BK];        // the panel, row j at BK j
+    uint8_t OLD[BK * SMALL_MAX];      // this panel's pivot rows before the update (ldw apart)
+    int16_t piv_of_col[SMALL_MAX];    // pivot row of column c, -1: none
+    int16_t col_of_row[SMALL_MAX];    // the column row j is the pivot of, -1: none
+    int16_t ups[SMALL_MAX], upsbar[SMALL_MAX], rho[SMALL_MAX], rhobar[SMALL_MAX];
+    alignas(16) uint8_t prow[BK];     // the scaled pivot row, panel part
+    alignas(16) uint8_t coef[U8_WARPS][BK];  // per warp: the row's coefficients of the pivot rows
+    int16_t piv_row[BK], piv_pc[BK];  // this panel's pivots: row, panel column
+    uint8_t red[256];                 // x mod p
+    uint8_t inv[16];                  // a^-1 mod p
+    int wmin[U8_WARPS];
+    int r, kp;
+};
+
+// x mod p in both 16-bit lanes of w (lanes < 2^16); rcp = ceil(2^32 / p)
+__device__ __forceinline__ uint32_t mod_lanes(uint32_t w, uint32_t p, uint32_t rcp) {
+    uint32_t lo = w & 0xFFFFu, hi = w >> 16;
+    lo -= p * __umulhi(lo, rcp);
+    hi -= p * __umulhi(hi, rcp);
+    return lo | (hi << 16);
+}
+
+__global__ void __launch_bounds__(U8_THREADS) k_ech_small_u8(const SmallJob *jobs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    U8Shared &S = *reinterpret_cast<U8Shared *>(smem_raw);
+    const SmallJob J = jobs[blockIdx.x];
     const int m = J.m, n = J.n, p = J.p;
+    if (m <= 0 || n <= 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint8_t *W = (uint8_t *)J.W;
-    const int64_t ldw = J.ldw;  // multiple of 16, >= n, <= SMALL_MAX
+    const int ldw = (int)J.ldw;  // multiple of 16, >= n, <= SMALL_MAX
     const uint8_t *A = (const uint8_t *)J.A;
-    for (int x = tid; x < 256; x += SM_THREADS) S.red[x] = (uint8_t)(x % p);
+    const uint32_t rcp = (uint32_t)((0x100000000ull + (uint64_t)p - 1) / (uint64_t)p);
+    for (int x = tid; x < 256; x += U8_THREADS) S.red[x] = (uint8_t)(x % p);
     if (tid < 16) {
         int v = 0;
         for (int y = 1; y < p; ++y)
             if ((tid % p) * y % p == 1) v = y;
         S.inv[tid] = (uint8_t)v;
     }
-    for (int c = tid; c < n; c += SM_THREADS) S.piv_of_col[c] = -1;
-    for (int j = tid; j < m; j += SM_THREADS) S.col_of_row[j] = -1;
+    for (int c = tid; c < n; c += U8_THREADS) S.piv_of_col[c] = -1;
+    for (int j = tid; j < m; j += U8_THREADS) S.col_of_row[j] = -1;
     __syncthreads();
     // A -> W, residues in [0, p), zero padding up to ldw
-    const int vpr = (int)(ldw >> 4);
-    for (int v = tid; v < m * vpr; v += SM_THREADS) {
+    const int vpr = ldw >> 4;
+    for (int v = tid; v < m * vpr; v += U8_THREADS) {
         const int j = v / vpr, k0 = (v - j * vpr) << 4;
         uint32_t o[4] = {0u, 0u, 0u, 0u};
         const uint8_t *a = A + (int64_t)j * J.lda;
@@ -131,82 +171,103 @@ __device__ void small_u8(const SmallJob &J, SmallShared &S) {
     __syncthreads();
 
     const int klazy = (255 - (p - 1)) / ((p - 1) * (p - 1));
-    int steps = 0;
-    int known = INT_MAX;  // pivot row of column c found while updating for c - 1
-    bool have_known = false;
-    for (int c = 0; c < n; ++c) {
-        int i;
-        if (have_known) {
-            i = known;
-        } else {
-            int best = INT_MAX;
-            for (int j = tid; j < m; j += SM_THREADS)
-                if (S.col_of_row[j] < 0 && S.red[W[j * ldw + c]]) {
-                    best = j;
-                    break;
-                }
-            i = cta_min(best, S);
+    for (int c0 = 0; c0 < n; c0 += BK) {
+        const int kw = min(BK, n - c0);
+        // panel load (its second vector may lie past the row pitch: zeros)
+        for (int v = tid; v < 2 * m; v += U8_THREADS) {
+            const int j = v >> 1, k = c0 + 16 * (v & 1);
+            *(uint4 *)(S.P + j * BK + 16 * (v & 1)) =
+                k < ldw ? *(const uint4 *)(W + j * ldw + k) : make_uint4(0u, 0u, 0u, 0u);
         }
-        have_known = false;
-        if (i == INT_MAX) continue;  // no pivot in column c
-        // pivot row scaled so that its pivot is -1; position c keeps the
-        // transformation entry s = -a^-1
-        const uint8_t *wi = W + i * ldw;
-        const int s = p - S.inv[S.red[wi[c]]];
-        for (int k = tid; k < ldw; k += SM_THREADS)
-            S.prow[k] = k == c ? (uint8_t)s : (k < n ? S.red[s * S.red[wi[k]]] : (uint8_t)0);
-        if (tid == 0) {
-            S.piv_of_col[c] = (int16_t)i;
-            S.col_of_row[i] = (int16_t)c;
-        }
+        if (tid == 0) S.kp = 0;
         __syncthreads();
-        const bool reduce = ++steps >= klazy;
-        if (reduce) steps = 0;
-        const int c1 = c + 1;
-        int best = INT_MAX;  // topmost non-pivot row with a non-zero in column c1
-        for (int j = warp; j < m; j += SM_WARPS) {
-            uint8_t *row = W + j * ldw;
-            if (j == i) {
-                for (int k0 = lane << 4; k0 < ldw; k0 += 512) *(uint4 *)(row + k0) = *(const uint4 *)(S.prow + k0);
-                continue;
+        // panel elimination, column by column
+        int steps = 0, known = INT_MAX;
+        bool have_known = false;
+        for (int cc = 0; cc < kw; ++cc) {
+            int i;
+            if (have_known) {
+                i = known;
+            } else {
+                int best = INT_MAX;
+                for (int j = tid; j < m; j += U8_THREADS)
+                    if (S.col_of_row[j] < 0 && S.red[S.P[j * BK + cc]]) {
+                        best = j;
+                        break;
+                    }
+                i = cta_min<U8_WARPS>(best, S.wmin);
             }
-            const uint32_t f = __shfl_sync(0xffffffffu, lane == 0 ? (uint32_t)S.red[row[c]] : 0u, 0);
-            const bool cand = S.col_of_row[j] < 0 && c1 < n;
-            if (f == 0 && !reduce) {
-                if (lane == 0 && cand && S.red[row[c1]]) best = min(best, j);
-                continue;
+            have_known = false;
+            if (i == INT_MAX) continue;
+            const int s = p - S.inv[S.red[S.P[i * BK + cc]]];
+            if (tid < BK)
+                S.prow[tid] = tid == cc ? (uint8_t)s : (tid < kw ? S.red[s * S.red[S.P[i * BK + tid]]] : (uint8_t)0);
+            if (tid == 0) {
+                S.piv_of_col[c0 + cc] = (int16_t)i;
+                S.col_of_row[i] = (int16_t)(c0 + cc);
+                S.piv_row[S.kp] = (int16_t)i;
+                S.piv_pc[S.kp] = (int16_t)cc;
+                S.kp = S.kp + 1;
             }
-            for (int k0 = lane << 4; k0 < ldw; k0 += 512) {
-                uint4 w = *(const uint4 *)(row + k0);
-                const uint4 pv = *(const uint4 *)(S.prow + k0);
-                const int q = c - k0;
-                w.x = clear_byte(w.x, q, 0);
-                w.y = clear_byte(w.y, q, 4);
-                w.z = clear_byte(w.z, q, 8);
-                w.w = clear_byte(w.w, q, 12);
-                w.x += f * pv.x;
-                w.y += f * pv.y;
-                w.z += f * pv.z;
-                w.w += f * pv.w;
-                if (reduce) {
-                    w.x = red4(w.x, S.red);
-                    w.y = red4(w.y, S.red);
-                    w.z = red4(w.z, S.red);
-                    w.w = red4(w.w, S.red);
+            __syncthreads();
+            const bool reduce = ++steps >= klazy;
+            if (reduce) steps = 0;
+            const int c1 = cc + 1;
+            int best = INT_MAX;
+            const uint4 pv0 = *(const uint4 *)(S.prow), pv1 = *(const uint4 *)(S.prow + 16);
+            for (int j = tid; j < m; j += U8_THREADS) {
+                uint4 *row = (uint4 *)(S.P + j * BK);
+                if (j == i) {
+                    row[0] = pv0;
+                    row[1] = pv1;
+                    continue;
                 }
-                *(uint4 *)(row + k0) = w;
-                if (cand && c1 >= k0 && c1 < k0 + 16 && S.red[byte_of(w, c1 - k0)]) best = min(best, j);
+                const uint32_t f = S.red[S.P[j * BK + cc]];
+                const bool cand = S.col_of_row[j] < 0 && c1 < kw;
+                if (f == 0 && !reduce) {
+                    if (cand && S.red[S.P[j * BK + c1]]) best = min(best, j);
+                    continue;
+                }
+                uint4 w0 = row[0], w1 = row[1];
+                w0.x = clear_byte(w0.x, cc, 0);
+                w0.y = clear_byte(w0.y, cc, 4);
+                w0.z = clear_byte(w0.z, cc, 8);
+                w0.w = clear_byte(w0.w, cc, 12);
+                w1.x = clear_byte(w1.x, cc, 16);
+                w1.y = clear_byte(w1.y, cc, 20);
+                w1.z = clear_byte(w1.z, cc, 24);
+                w1.w = clear_byte(w1.w, cc, 28);
+                w0.x += f * pv0.x;
+                w0.y += f * pv0.y;
+                w0.z += f * pv0.z;
+                w0.w += f * pv0.w;
+                w1.x += f * pv1.x;
+                w1.y += f * pv1.y;
+                w1.z += f * pv1.z;
+                w1.w += f * pv1.w;
+                if (reduce) {
+                    w0.x = red4(w0.x, S.red);
+                    w0.y = red4(w0.y, S.red);
+                    w0.z = red4(w0.z, S.red);
+                    w0.w = red4(w0.w, S.red);
+                    w1.x = red4(w1.x, S.red);
+                    w1.y = red4(w1.y, S.red);
+                    w1.z = red4(w1.z, S.red);
+                    w1.w = red4(w1.w, S.red);
+                }
+                row[0] = w0;
+                row[1] = w1;
+                if (cand && (c1 < 16 ? S.red[byte_of(w0, c1)] : S.red[byte_of(w1, c1 - 16)])) best = min(best, j);
+            }
+            const int nx = cta_min<U8_WARPS>(best, S.wmin);
+            if (nx != INT_MAX) {
+                known = nx;
+                have_known = true;
             }
         }
-        const int nx = cta_min(best, S);
-        if (nx != INT_MAX) {
-            known = nx;
-            have_known = true;
-        }
-    }
-    if (steps > 0) {  // last lazy round: every entry to [0, p)
-        for (int v = tid; v < m * vpr; v += SM_THREADS) {
-            uint4 *q = (uint4 *)(W + (int64_t)v * 16);
+        // the panel exactly reduced
+        for (int v = tid; v < 2 * m; v += U8_THREADS) {
+            uint4 *q = (uint4 *)(S.P + 16 * v);
             uint4 w = *q;
             w.x = red4(w.x, S.red);
             w.y = red4(w.y, S.red);
@@ -214,8 +275,67 @@ __device__ void small_u8(const SmallJob &J, SmallShared &S) {
             w.w = red4(w.w, S.red);
             *q = w;
         }
+        const int kp = S.kp;  // written before the last barrier of the loop
+        if (kp > 0) {
+            // the pivot rows as they were before this panel's operations
+            for (int v = tid; v < kp * vpr; v += U8_THREADS) {
+                const int q = v / vpr, k0 = (v - q * vpr) << 4;
+                *(uint4 *)(S.OLD + q * ldw + k0) = *(const uint4 *)(W + S.piv_row[q] * ldw + k0);
+            }
+            __syncthreads();
+            // every row: rest += sum_q coef_q * OLD_q, coef_q = P[j][pivot column q] - [j = pivot row q]
+            for (int j = warp; j < m; j += U8_WARPS) {
+                uint32_t cq = 0;
+                if (lane < kp) {
+                    cq = S.P[j * BK + S.piv_pc[lane]];
+                    if (S.piv_row[lane] == j) cq = cq ? cq - 1 : (uint32_t)(p - 1);
+                    S.coef[warp][lane] = (uint8_t)cq;
+                }
+                if (!__any_sync(0xffffffffu, cq != 0)) continue;
+                __syncwarp();
+                uint8_t *row = W + j * ldw;
+                for (int k0 = lane << 4; k0 < ldw; k0 += 512) {
+                    if (k0 >= c0 && k0 < c0 + BK) continue;  // the panel's own columns come from P
+                    const uint4 w = *(const uint4 *)(row + k0);
+                    uint32_t e[4] = {w.x & 0x00FF00FFu, w.y & 0x00FF00FFu, w.z & 0x00FF00FFu, w.w & 0x00FF00FFu};
+                    uint32_t o[4] = {(w.x >> 8) & 0x00FF00FFu, (w.y >> 8) & 0x00FF00FFu, (w.z >> 8) & 0x00FF00FFu,
+                                     (w.w >> 8) & 0x00FF00FFu};
+                    for (int q4 = 0; q4 < kp; q4 += 4) {
+                        const uint32_t c4 = *(const uint32_t *)(&S.coef[warp][q4]);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const uint32_t c = (c4 >> (8 * t)) & 0xFFu;
+                            if (q4 + t < kp && c) {
+                                const uint4 v = *(const uint4 *)(S.OLD + (q4 + t) * ldw + k0);
+                                e[0] += c * (v.x & 0x00FF00FFu);
+                                e[1] += c * (v.y & 0x00FF00FFu);
+                                e[2] += c * (v.z & 0x00FF00FFu);
+                                e[3] += c * (v.w & 0x00FF00FFu);
+                                o[0] += c * ((v.x >> 8) & 0x00FF00FFu);
+                                o[1] += c * ((v.y >> 8) & 0x00FF00FFu);
+                                o[2] += c * ((v.z >> 8) & 0x00FF00FFu);
+                                o[3] += c * ((v.w >> 8) & 0x00FF00FFu);
+                            }
+                        }
+                    }
+                    uint4 out;
+                    out.x = mod_lanes(e[0], p, rcp) | (mod_lanes(o[0], p, rcp) << 8);
+                    out.y = mod_lanes(e[1], p, rcp) | (mod_lanes(o[1], p, rcp) << 8);
+                    out.z = mod_lanes(e[2], p, rcp) | (mod_lanes(o[2], p, rcp) << 8);
+                    out.w = mod_lanes(e[3], p, rcp) | (mod_lanes(o[3], p, rcp) << 8);
+                    *(uint4 *)(row + k0) = out;
+                }
+                __syncwarp();
+            }
+        }
+        // the panel back into W
+        for (int v = tid; v < 2 * m; v += U8_THREADS) {
+            const int j = v >> 1, k = c0 + 16 * (v & 1);
+            if (k < ldw) *(uint4 *)(W + j * ldw + k) = *(const uint4 *)(S.P + j * BK + 16 * (v & 1));
+        }
+        __syncthreads();
     }
-    __syncthreads();
+    // outputs
     if (warp == 0) {
         const int r = split_list(S.piv_of_col, n, S.ups, S.upsbar);
         if (lane == 0) S.r = r;
@@ -225,12 +345,12 @@ __device__ void small_u8(const SmallJob &J, SmallShared &S) {
     __syncthreads();
     const int r = S.r;
     if (tid == 0) *J.rank = r;
-    for (int l = tid; l < r; l += SM_THREADS) {
+    for (int l = tid; l < r; l += U8_THREADS) {
         if (J.pcols) J.pcols[l] = S.ups[l];
         if (J.prows) J.prows[l] = S.rho[l];
     }
     uint8_t *R = (uint8_t *)J.R, *M = (uint8_t *)J.M, *K = (uint8_t *)J.K;
-    for (int l = warp; l < r; l += SM_WARPS) {
+    for (int l = warp; l < r; l += U8_WARPS) {
         const uint8_t *src = W + S.piv_of_col[S.ups[l]] * ldw;
         if (R)
             for (int t = lane; t < n - r; t += 32) R[l * J.ldR + t] = src[S.upsbar[t]];
@@ -238,7 +358,7 @@ __device__ void small_u8(const SmallJob &J, SmallShared &S) {
             for (int s2 = lane; s2 < r; s2 += 32) M[l * J.ldM + s2] = src[S.col_of_row[S.rho[s2]]];
     }
     if (K)
-        for (int t = warp; t < m - r; t += SM_WARPS) {
+        for (int t = warp; t < m - r; t += U8_WARPS) {
             const uint8_t *src = W + S.rhobar[t] * ldw;
             for (int s2 = lane; s2 < r; s2 += 32) K[t * J.ldK + s2] = src[S.col_of_row[S.rho[s2]]];
         }
@@ -281,7 +401,7 @@ __device__ void small_gf2(const SmallJob &J, SmallShared &S) {
                     best = j;
                     break;
                 }
-            i = cta_min(best, S);
+            i = cta_min<SM_WARPS>(best, S.wmin);
         }
         have_known = false;
         if (i == INT_MAX) continue;
@@ -308,7 +428,7 @@ __device__ void small_gf2(const SmallJob &J, SmallShared &S) {
             }
             if (cand && lane == c1w && (y & c1b)) best = min(best, j);
         }
-        const int nx = cta_min(best, S);
+        const int nx = cta_min<SM_WARPS>(best, S.wmin);
         if (nx != INT_MAX) {
             known = nx;
             have_known = true;
@@ -352,21 +472,27 @@ __device__ void small_gf2(const SmallJob &J, SmallShared &S) {
             gather(W + (int64_t)S.rhobar[t] * ldq, S.rho, r, K + t * (J.ldK >> 3), true);
 }
 
-__global__ void __launch_bounds__(SM_THREADS) k_ech_small(const SmallJob *jobs) {
+__global__ void __launch_bounds__(SM_THREADS) k_ech_small_gf2(const SmallJob *jobs) {
     __shared__ SmallShared S;
     const SmallJob J = jobs[blockIdx.x];
     if (J.m <= 0 || J.n <= 0) return;
-    if (J.fmt == GFE_BITS64) small_gf2(J, S);
-    else small_u8(J, S);
+    small_gf2(J, S);
 }
 
 }  // namespace
 
-void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count) {
+void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int fmt) {
     if (count <= 0) return;
+    static std::atomic<bool> attr_set[64];  // the byte kernel's dynamic shared memory, once per device
+    int dev = 0;
+    if (fmt == GFE_U8 && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev].load()) {
+        cudaFuncSetAttribute(k_ech_small_u8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(U8Shared));
+        attr_set[dev].store(true);
+    }
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
-    k_ech_small<<<count, SM_THREADS, 0, L.st>>>(jobs_dev);
+    if (fmt == GFE_BITS64) k_ech_small_gf2<<<count, SM_THREADS, 0, L.st>>>(jobs_dev);
+    else k_ech_small_u8<<<count, U8_THREADS, sizeof(U8Shared), L.st>>>(jobs_dev);
     prof_end(L, K_ECH, ev, 0, 0, count, 0);
 }
 

@@ -8,6 +8,7 @@ fallback implementation.
 """
 from __future__ import annotations
 
+import collections.abc
 import contextlib
 import ctypes
 import os
@@ -62,7 +63,7 @@ SIGNATURES = {
                                  _vp, ctypes.c_size_t, _vp]),
     "gfe_set_batch_workers": (_i32, [_i32]),
     "gfe_set_wait_policy": (_i32, [_i32]),
-    "gfe_set_batch_small_max": (_i32, [_i32]),
+    "gfe_set_batch_small_max": (_i32, [_i32, ctypes.c_double]),
     "gfe_server_create": (_i32, [ctypes.POINTER(_vp), ctypes.c_size_t, _i32, _i32]),
     "gfe_submit": (_i32, [_vp, ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), ctypes.c_uint32, _vp,
                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -276,55 +277,88 @@ def set_wait_policy(policy: str) -> None:
     _check(lib().gfe_set_wait_policy(WAIT_POLICIES[policy]))
 
 
-def set_batch_small_max(side: int = 2048) -> None:
-    """gfe_set_batch_small_max: largest side of a batch matrix taken by the one-launch kernel (0: none)."""
-    _check(lib().gfe_set_batch_small_max(side))
+def set_batch_small_max(side: int = 2048, max_work: float = 0.0) -> None:
+    """gfe_set_batch_small_max: largest side (0: none) and work m*n*min(m,n)
+    (<= 0: the default) of a batch matrix taken by the one-launch kernel."""
+    _check(lib().gfe_set_batch_small_max(side, max_work))
+
+
+class BatchResult(collections.abc.Mapping):
+    """One matrix's result of batch_echelon: the same keys and tensors as
+    echelon()'s dict, sliced from the batch's shared buffers when read."""
+
+    __slots__ = ("_bufs", "_mat", "_slots", "_r")
+
+    def __init__(self, bufs, mat, slots, r):
+        self._bufs, self._mat, self._slots, self._r = bufs, mat, slots, r
+
+    def __getitem__(self, key):
+        if key == "rank":
+            return self._r
+        r, m, nn = self._r, self._mat.m, self._mat.n
+        bits = self._mat.fmt == GFE_BITS64
+        if key in ("ups", "rho"):
+            off = self._slots["idx"] + 1 + (0 if key == "ups" else self._slots["k"])
+            return self._bufs[0][off:off + r]
+        if key not in self._slots:
+            raise KeyError(key)
+        off, rows, cols = self._slots[key]
+        t = self._bufs[2 if bits else 1][off:off + rows * cols].view(rows, cols)
+        want = {"R": (r, nn - r), "M": (r, r), "K": (m - r, r)}[key]
+        if bits:
+            return t[:want[0], :words_per_row(want[1])] if want[0] else t[:0]
+        return t[:want[0], :want[1]]
+
+    def __iter__(self):
+        return iter(["rank", "ups", "rho", "R"] + (["M", "K"] if "M" in self._slots else []))
+
+    def __len__(self):
+        return 6 if "M" in self._slots else 4
 
 
 def _alloc_results(args, dev, transform: bool):
-    """Result buffers of a whole batch carved out of three allocations (index
-    arrays, byte matrices, GF(2) words): same shapes as _alloc_result."""
-    shapes = []
-    n_idx = n_u8 = n_w = 0
+    """Result buffers of a whole batch: three allocations (index arrays, byte
+    matrices, GF(2) words; shapes as _alloc_result's), the C structs made
+    from their addresses, and each matrix's slots in them."""
+    slots, n_idx, n_u8, n_w = [], 0, 0, 0
     for mat in args:
         m, nn = mat.m, mat.n
-        mn = min(m, nn)
+        k = max(min(m, nn), 1)
         bits = mat.fmt == GFE_BITS64
-        mats = [("R", max(mn, 1), max(nn, 1))]
-        if transform:
-            mats += [("M", max(mn, 1), max(mn, 1)), ("K", max(m, 1), max(mn, 1))]
-        mats = [(k, r, words_per_row(c) if bits else c) for k, r, c in mats]
-        shapes.append((bits, max(mn, 1), mats))
-        n_idx += 1 + 2 * max(mn, 1)
-        for _, r, c in mats:
+        sl = {"idx": n_idx, "k": k}
+        n_idx += 1 + 2 * k
+        shapes = [("R", k, max(nn, 1))] + ([("M", k, k), ("K", max(m, 1), k)] if transform else [])
+        for key, rows, cols in shapes:
             if bits:
-                n_w += r * c
+                cols = words_per_row(cols)
+                sl[key] = (n_w, rows, cols)
+                n_w += rows * cols
             else:
-                n_u8 += r * c
+                sl[key] = (n_u8, rows, cols)
+                n_u8 += rows * cols
+        slots.append(sl)
     idx = torch.empty(n_idx, dtype=torch.int64, device=dev)
     u8 = torch.empty(n_u8, dtype=torch.uint8, device=dev)
     wb = torch.zeros(n_w, dtype=torch.int64, device=dev)  # rows are padded to whole 16-byte pairs of words
-    out, oi, ou, ow = [], 0, 0, 0
-    for bits, k, mats in shapes:
-        bufs = dict(rank=idx[oi:oi + 1], ups=idx[oi + 1:oi + 1 + k], rho=idx[oi + 1 + k:oi + 1 + 2 * k])
-        oi += 1 + 2 * k
-        for key, r, c in mats:
-            if bits:
-                bufs[key] = wb[ow:ow + r * c].view(r, c)
-                ow += r * c
-            else:
-                bufs[key] = u8[ou:ou + r * c].view(r, c)
-                ou += r * c
-        es = 8 if bits else 1
+    pi, pu, pw = idx.data_ptr(), u8.data_ptr(), wb.data_ptr()
+    res = []
+    for mat, sl in zip(args, slots):
+        bits = mat.fmt == GFE_BITS64
+        base, es = (pw, 8) if bits else (pu, 1)
 
-        def ld(t):
-            return 0 if t is None else t.stride(0) * es
+        def at(key):
+            if key not in sl:
+                return None, 0
+            off, rows, cols = sl[key]
+            return base + off * es, cols * es
 
-        res = GfeResult(bufs["rank"].data_ptr(), bufs["ups"].data_ptr(), bufs["rho"].data_ptr(), _ptr(bufs["R"]),
-                        ld(bufs["R"]), _ptr(bufs.get("M")), ld(bufs.get("M")), _ptr(bufs.get("K")),
-                        ld(bufs.get("K")), None, 0, None, 0)
-        out.append((bufs, res))
-    return out, idx
+        R, ldR = at("R")
+        M, ldM = at("M")
+        K, ldK = at("K")
+        o = sl["idx"]
+        res.append(GfeResult(pi + 8 * o, pi + 8 * (o + 1), pi + 8 * (o + 1 + sl["k"]), R, ldR, M, ldM, K, ldK,
+                             None, 0, None, 0))
+    return (idx, u8, wb), slots, res
 
 
 def batch_echelon(mats, transform: bool = True, impl: str = "tensor", workers: int | None = None, stream=None):
@@ -337,18 +371,15 @@ def batch_echelon(mats, transform: bool = True, impl: str = "tensor", workers: i
     if workers is not None:
         _check(lib().gfe_set_batch_workers(workers))
     arr = (GfeMatrix * len(args))(*args)
-    allocs, idx = _alloc_results(args, dev, transform)
-    ress = (GfeResult * len(args))(*[r for _, r in allocs])
+    bufs, slots, res = _alloc_results(args, dev, transform)
+    ress = (GfeResult * len(args))(*res)
     need = ctypes.c_size_t(0)
     _check(lib().gfe_query_batch_workspace(arr, len(args), flags, ctypes.byref(need)))
     ws = _workspace(need.value, dev)
     _check(lib().gfe_batch_echelon(arr, ress, len(args), flags, ws.data_ptr(), ws.numel(), _stream(stream)))
-    at = [0]
-    for a in args[:-1]:
-        at.append(at[-1] + 1 + 2 * max(min(a.m, a.n), 1))
     with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
-        ranks = idx[torch.tensor(at, device=dev)].cpu().tolist()
-    return [_cut_result(a, b, int(r)) for a, (b, _), r in zip(args, allocs, ranks)]
+        ranks = bufs[0][torch.tensor([sl["idx"] for sl in slots], device=dev)].cpu().tolist()
+    return [BatchResult(bufs, a, sl, int(r)) for a, sl, r in zip(args, slots, ranks)]
 
 
 def rank(A: torch.Tensor, p: int, n: int | None = None, impl: str = "tensor", stream=None) -> dict:

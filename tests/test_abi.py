@@ -110,3 +110,10 @@ def test_auto_block_table():
     for p in (2, 3, 251):
         for n in (100, 5000, 20000, 70000, 200000):
             assert gfe.auto_block(p, n, n) % 1024 == 0
+
+
+def test_batch_small_policy_validation():
+    with pytest.raises(gfe.GfeError):
+        gfe._check(gfe.lib().gfe_set_batch_small_max(-1, 0.0))
+    gfe.set_batch_small_max(512, 1e8)
+    gfe.set_batch_small_max()

@@ -113,7 +113,7 @@ def test_small_kernel_equals_worker_path_at_full_side():
              (13, 2048, 1500, None)]
     mats = [(p, m, n, synth.matrix(p, m, n, seed=950 + i, rank=rk)) for i, (p, m, n, rk) in enumerate(specs)]
     args = [(A.to(DEV), p, n) for p, m, n, A in mats]
-    gfe.set_batch_small_max(2048)
+    gfe.set_batch_small_max(2048, 1e12)  # above the default work cut-off: force the one-launch kernel
     small = gfe.batch_echelon(args)
     gfe.set_batch_small_max(0)
     try:

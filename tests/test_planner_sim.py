@@ -234,3 +234,76 @@ def test_rank_deficient_wide_zero_blocks(sim, p):
     else:
         check(sim, A, p)
     sim.gfe_set_block_policy(0, 0)
+
+
+def test_small_batch_two_formats_without_races(sim):
+    """A batch of bit-packed GF(2) and byte matrices all taken by the
+    one-launch small-matrix path (a stream per storage format) plus one
+    GF(251) matrix on a worker: oracle results, no unordered access."""
+    rng = np.random.RandomState(11)
+    specs = [(2, 70, 130), (3, 40, 33), (2, 1, 65), (13, 90, 64), (7, 17, 1), (2, 128, 128), (251, 30, 40)]
+    keep, args, outs, refs = [], [], [], []
+    for p, m, n in specs:
+        mn = min(m, n)
+        if p == 2:
+            B = rng.randint(0, 2, (m, n)).astype(np.uint8)
+            if m > 60:
+                B[m // 2:] = 0  # rank-deficient
+            A = O.pack_bits(B)
+            ref = O.echelon_gf2(A, m, n)
+            wr = lambda c: max(((c + 63) // 64 + 1) // 2 * 2, 2)  # the oracle's even word count
+            R = np.zeros((max(mn, 1), wr(n)), np.uint64)
+            M = np.zeros((max(mn, 1), wr(mn)), np.uint64)
+            K = np.zeros((max(m, 1), wr(mn)), np.uint64)
+            fmt = 1
+        else:
+            A = rng.randint(0, p, (m, n)).astype(np.uint8)
+            ref = O.echelon(A, p)
+            R = np.zeros((max(mn, 1), max(n, 1)), np.uint8)
+            M = np.zeros((max(mn, 1), max(mn, 1)), np.uint8)
+            K = np.zeros((max(m, 1), max(mn, 1)), np.uint8)
+            fmt = 0
+        rank = np.zeros(1, np.int64)
+        pc = np.zeros(max(mn, 1), np.int64)
+        pr = np.zeros(max(mn, 1), np.int64)
+        for a in (A, rank, pc, pr, R, M, K):
+            sim.sim_register(a.ctypes.data, a.nbytes)
+        keep.append((A, rank, pc, pr, R, M, K))
+        refs.append(ref)
+        args.append(gfe.GfeMatrix(p, m, n, fmt, A.ctypes.data, A.strides[0]))
+        outs.append(gfe.GfeResult(rank.ctypes.data, pc.ctypes.data, pr.ctypes.data, R.ctypes.data, R.strides[0],
+                                  M.ctypes.data, M.strides[0], K.ctypes.data, K.strides[0], None, 0, None, 0))
+    arr = (gfe.GfeMatrix * len(args))(*args)
+    res = (gfe.GfeResult * len(args))(*outs)
+    need = ctypes.c_size_t(0)
+    assert sim.gfe_query_batch_workspace(arr, len(args), 1, ctypes.byref(need)) == 0
+    ws = np.zeros(need.value, np.uint8)
+    sim.sim_register(ws.ctypes.data, ws.nbytes)
+    assert sim.gfe_batch_echelon(arr, res, len(args), 1, ws.ctypes.data, ws.nbytes, None) == 0, sim.gfe_last_error()
+    for (p, m, n), ref, (A, rank, pc, pr, R, M, K) in zip(specs, refs, keep):
+        r = ref["rank"]
+        assert int(rank[0]) == r, (p, m, n)
+        assert np.array_equal(pr[:r], ref["rho"]) and np.array_equal(pc[:r], ref["ups"])
+        for got, want in ((R, ref["R"]), (M, ref["M"]), (K, ref["K"])):
+            want = np.asarray(want)
+            if want.size:
+                assert np.array_equal(got[:want.shape[0], :want.shape[1]].view(want.dtype), want), (p, m, n)
+    assert races(sim) == 0
+
+
+def test_batch_split_by_side_and_work(sim):
+    """The work cut-off and the side limit move matrices between the
+    one-launch kernel and the workers: the workspace query follows the
+    split (a small matrix needs m x ceil16(n) bytes, a worker its slice)."""
+    def need(side, work):
+        assert sim.gfe_set_batch_small_max(side, ctypes.c_double(work)) == 0
+        A = np.zeros((300, 300), np.uint8)
+        arr = (gfe.GfeMatrix * 1)(gfe.GfeMatrix(7, 300, 300, 0, A.ctypes.data, 300))
+        n = ctypes.c_size_t(0)
+        assert sim.gfe_query_batch_workspace(arr, 1, 1, ctypes.byref(n)) == 0
+        return n.value
+    small = need(2048, 0.0)
+    assert small < 300 * 304 + 4096          # the matrix itself and the job table
+    assert need(2048, 1e6) > small           # 300^3 > 1e6: a worker slice
+    assert need(256, 0.0) > small            # side 300 > 256: a worker slice
+    sim.gfe_set_batch_small_max(2048, ctypes.c_double(0.0))
