@@ -188,6 +188,12 @@ gfe_status gfe_poll(gfe_server *server, uint64_t ticket, gfe_status *done_status
 gfe_status gfe_wait(gfe_server *server, uint64_t ticket, int64_t timeout_us, gfe_status *done_status);
 gfe_status gfe_server_latency(gfe_server *server, uint64_t ticket, double *us, int32_t release);
 gfe_status gfe_server_destroy(gfe_server *server);
+/* Server requests of work m n min(m,n) at most max_work that the batched
+ * form's one-launch kernels take are grouped: a worker runs every such
+ * queued request with the same flags (up to 256) as one batched call.
+ * Default 2e7 (about 270^3); <= 0 turns grouping off.  Applies to requests
+ * admitted after the call. */
+gfe_status gfe_set_server_group_work(double max_work);
 
 /*
  * gfe_mad -- the job MAD (Section 4.1): C := W + A B over GF(p), A m x k,

@@ -461,6 +461,15 @@ static bool batch_small(const gfe_matrix &A, uint32_t flags) {
     return small_eligible(A.p, A.fmt, A.m, A.n);
 }
 
+}  // extern "C"
+
+namespace gfe {
+// for the server's grouping of small requests
+bool batch_takes_small(const gfe_matrix &A, uint32_t flags) { return batch_small(A, flags); }
+}  // namespace gfe
+
+extern "C" {
+
 struct BatchPlan {
     std::vector<int32_t> small, rest;
     std::vector<size_t> small_off;  // offset of each small matrix's area
@@ -534,11 +543,11 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
     cudaEvent_t start;
     if (!cuda_ok(cudaEventCreateWithFlags(&start, cudaEventDisableTiming), "event")) return GFE_ECUDA;
     cudaEventRecord(start, (cudaStream_t)stream);
-    // the small matrices: one job table, one launch per storage format, each
-    // on a stream of its own, the most expensive matrices first (their CTAs
-    // start first)
-    cudaStream_t small_st[2] = {nullptr, nullptr};
-    cudaEvent_t small_done[2] = {nullptr, nullptr};
+    // the small matrices: one job table, one launch per kind of kernel (bytes
+    // with p <= 13, bytes with larger p, GF(2) words), each on a stream of its
+    // own, the most expensive matrices first (their CTAs start first)
+    cudaStream_t small_st[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t small_done[3] = {nullptr, nullptr, nullptr};
     if (!P.small.empty()) {
         std::vector<SmallJob> jobs;
         jobs.reserve(P.small.size());
@@ -566,17 +575,13 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
             J.ldK = o.ldK;
             jobs.push_back(J);
         }
-        auto cost = [](const SmallJob &J) {
-            const double w = (double)J.m * J.n * std::min(J.m, J.n);
-            return J.fmt == GFE_BITS64 ? w / 32 : w;
-        };
-        std::stable_sort(jobs.begin(), jobs.end(), [&](const SmallJob &a, const SmallJob &b) {
-            return a.fmt != b.fmt ? a.fmt < b.fmt : cost(a) > cost(b);
+        std::stable_sort(jobs.begin(), jobs.end(), [](const SmallJob &a, const SmallJob &b) {
+            const int ka = small_kind(a.p, a.fmt), kb = small_kind(b.p, b.fmt);
+            if (ka != kb) return ka < kb;
+            return (double)a.m * a.n * std::min(a.m, a.n) > (double)b.m * b.n * std::min(b.m, b.n);
         });
-        const int n_u8 = (int)(std::find_if(jobs.begin(), jobs.end(),
-                                            [](const SmallJob &J) { return J.fmt == GFE_BITS64; }) -
-                               jobs.begin());
-        const int nfmt[2] = {n_u8, (int)jobs.size() - n_u8};
+        int nkind[3] = {0, 0, 0};
+        for (const SmallJob &J : jobs) ++nkind[small_kind(J.p, J.fmt)];
         SmallJob *djobs = (SmallJob *)((char *)ws + P.jobs_off);
         Launch L;
         launch_for(&As[P.small[0]], flags, nullptr, L);
@@ -586,26 +591,33 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
         ok = ok && cuda_ok(cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(SmallJob),
                                            cudaMemcpyHostToDevice, small_st[0]),
                            "job table upload");
-        if (ok && nfmt[1]) {  // GF(2) on a second stream, once the table is on the device
-            cudaEvent_t up = nullptr;
-            ok = cuda_ok(cudaStreamCreateWithFlags(&small_st[1], cudaStreamNonBlocking), "stream") &&
-                 cuda_ok(cudaEventCreateWithFlags(&up, cudaEventDisableTiming), "event") &&
-                 cuda_ok(cudaEventRecord(up, small_st[0]), "event record") &&
-                 cuda_ok(cudaStreamWaitEvent(small_st[1], up, 0), "stream wait");
-            if (up) cudaEventDestroy(up);
+        cudaEvent_t up = nullptr;
+        ok = ok && cuda_ok(cudaEventCreateWithFlags(&up, cudaEventDisableTiming), "event") &&
+             cuda_ok(cudaEventRecord(up, small_st[0]), "event record");
+        for (int k = 1; ok && k < 3; ++k)  // the other kinds beside it, once the table is on the device
+            if (nkind[k])
+                ok = cuda_ok(cudaStreamCreateWithFlags(&small_st[k], cudaStreamNonBlocking), "stream") &&
+                     cuda_ok(cudaStreamWaitEvent(small_st[k], up, 0), "stream wait");
+        if (up) cudaEventDestroy(up);
+        int first = 0;
+        for (int k = 0; ok && k < 3; ++k) {
+            if (nkind[k]) {
+                L.st = small_st[k];
+                ech_small_batch(L, djobs + first, nkind[k], k);
+                ok = cuda_ok(cudaGetLastError(), "small-matrix launch") &&
+                     cuda_ok(cudaEventCreateWithFlags(&small_done[k], cudaEventDisableTiming), "event") &&
+                     cuda_ok(cudaEventRecord(small_done[k], small_st[k]), "event record");
+            }
+            first += nkind[k];
         }
-        for (int f = 0; ok && f < 2; ++f) {
-            if (!nfmt[f]) continue;
-            L.st = small_st[f];
-            ech_small_batch(L, djobs + (f ? n_u8 : 0), nfmt[f], f ? GFE_BITS64 : GFE_U8);
-            ok = cuda_ok(cudaGetLastError(), "small-matrix launch") &&
-                 cuda_ok(cudaEventCreateWithFlags(&small_done[f], cudaEventDisableTiming), "event") &&
-                 cuda_ok(cudaEventRecord(small_done[f], small_st[f]), "event record");
+        if (ok && !nkind[0]) {  // stream 0 only carried the upload: its end orders nothing else
+            ok = cuda_ok(cudaEventCreateWithFlags(&small_done[0], cudaEventDisableTiming), "event") &&
+                 cuda_ok(cudaEventRecord(small_done[0], small_st[0]), "event record");
         }
         if (!ok) {
-            for (int f = 0; f < 2; ++f) {
-                if (small_st[f]) cudaStreamDestroy(small_st[f]);
-                if (small_done[f]) cudaEventDestroy(small_done[f]);
+            for (int k = 0; k < 3; ++k) {
+                if (small_st[k]) cudaStreamDestroy(small_st[k]);
+                if (small_done[k]) cudaEventDestroy(small_done[k]);
             }
             cudaEventDestroy(start);
             return GFE_ECUDA;
@@ -672,12 +684,12 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
         }
         if (streams[w]) cudaStreamDestroy(streams[w]);
     }
-    for (int f = 0; f < 2; ++f) {
-        if (small_done[f]) {
-            cudaStreamWaitEvent((cudaStream_t)stream, small_done[f], 0);
-            cudaEventDestroy(small_done[f]);
+    for (int k = 0; k < 3; ++k) {
+        if (small_done[k]) {
+            cudaStreamWaitEvent((cudaStream_t)stream, small_done[k], 0);
+            cudaEventDestroy(small_done[k]);
         }
-        if (small_st[f]) cudaStreamDestroy(small_st[f]);
+        if (small_st[k]) cudaStreamDestroy(small_st[k]);
     }
     cudaEventDestroy(start);
     if (first != GFE_OK) {

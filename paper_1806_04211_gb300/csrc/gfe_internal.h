@@ -90,6 +90,8 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
 // R, M, K in the API storage (any of pcols, prows, R, M, K may be null).
 constexpr int SMALL_MAX = 2048;  // rows and columns of a small matrix
 constexpr int SMALL_MAX_P = 13;  // byte entries with lazy reduction: (p-1)^2 + (p-1) <= 255
+// the three kernels: bytes with 3 <= p <= 13, bytes with 17 <= p <= 251, GF(2) words
+enum SmallKind { SMALL_BYTES = 0, SMALL_WIDE = 1, SMALL_GF2 = 2 };
 struct SmallJob {
     const void *A;
     int64_t lda;  // bytes
@@ -100,15 +102,16 @@ struct SmallJob {
     void *R, *M, *K;
     int64_t ldR, ldM, ldK;  // bytes
 };
-// fmt: 0 = one byte per entry (3 <= p <= SMALL_MAX_P), 1 = GF(2) words
+// fmt: 0 = one byte per entry (odd p <= 251), 1 = GF(2) words
 inline bool small_eligible(int p, int fmt, int64_t m, int64_t n) {
     if (m <= 0 || n <= 0 || m > SMALL_MAX || n > SMALL_MAX) return false;
-    return fmt == 1 ? p == 2 : (fmt == 0 && p >= 3 && p <= SMALL_MAX_P);
+    return fmt == 1 ? p == 2 : (fmt == 0 && p >= 3 && p <= 251);
 }
+inline int small_kind(int p, int fmt) { return fmt == 1 ? SMALL_GF2 : (p <= SMALL_MAX_P ? SMALL_BYTES : SMALL_WIDE); }
 // workspace row pitch (bytes) of a small matrix: 16-byte vectors
 inline int64_t small_ldw(int fmt, int64_t n) { return fmt == 1 ? (n + 127) / 128 * 16 : (n + 15) / 16 * 16; }
-// launches the kernel for count jobs of one storage format (fmt)
-void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int fmt);
+// launches the kernel for count jobs of one kind (SmallKind)
+void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int kind);
 
 // An index array for a gather: a device copy, or, when it has at most
 // MAP_INLINE entries, the host array itself, which is then passed by value

@@ -5,12 +5,19 @@
 // queued request that fits may be admitted, so small requests flow past a
 // large one that waits for memory (continuous batching: requests that arrive
 // while others run join as slots and memory free up, and their work overlaps
-// on the GPU).  Results are those of gfe_echelon on the same matrix.
+// on the GPU).  A worker that admits a small request (one the batched form's
+// one-launch kernels take, of work at most gfe_set_server_group_work) also
+// admits every other such queued request with the same flags, up to
+// MAX_GROUP, and runs the group as one gfe_batch_echelon call: one launch per
+// kind of kernel, one thread block per request.  Results are those of
+// gfe_echelon on the same matrix.
 #include "gfe.h"
 #include "gfe_internal.h"
 
 #include <chrono>
 #include <condition_variable>
+#include <algorithm>
+#include <atomic>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -92,45 +99,114 @@ struct gfe_server {
 using gfe::cuda_ok;
 using gfe::set_error;
 
+namespace gfe {
+bool batch_takes_small(const gfe_matrix &A, uint32_t flags);  // gfe_api.cu
+}
+
+// most requests one worker takes together into the one-launch kernels
+constexpr size_t MAX_GROUP = 256;
+// A request joins a group only if its work m n min(m,n) is at most this: one
+// CTA runs about 1e11 mul-adds/s, so larger requests would wait longer in
+// the group than the blocked planner takes for them on the whole GPU.
+static std::atomic<double> g_group_work{2e7};
+
+static bool takes_group(const Req *r) {
+    const double work = (double)r->A.m * (double)r->A.n * (double)std::min(r->A.m, r->A.n);
+    return work <= g_group_work.load() && gfe::batch_takes_small(r->A, r->flags);
+}
+
+// workspace of a group of small requests (gfe_query_batch_workspace), 0 on error
+static size_t group_ws(const std::vector<Req *> &g) {
+    std::vector<gfe_matrix> As;
+    As.reserve(g.size());
+    for (Req *r : g) As.push_back(r->A);
+    size_t need = 0;
+    if (gfe_query_batch_workspace(As.data(), (int32_t)As.size(), g.front()->flags, &need) != GFE_OK) return 0;
+    return need;
+}
+
 static void worker_loop(gfe_server *S) {
     cudaSetDevice(S->device);
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
-        Req *job = nullptr;
+        std::vector<Req *> group;  // one request, or small ones run by one gfe_batch_echelon
+        size_t gws = 0, goff = 0;
         // admit the first queued request whose workspace fits
         for (;;) {
             if (S->stop && S->queue.empty()) break;
             for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+                Req *r = *it;
+                if (takes_group(r)) {
+                    std::vector<Req *> g{r};
+                    for (auto jt = std::next(it); jt != S->queue.end() && g.size() < MAX_GROUP; ++jt)
+                        if ((*jt)->flags == r->flags && takes_group(*jt))
+                            g.push_back(*jt);
+                    // the largest prefix of the group whose workspace fits
+                    for (;;) {
+                        const size_t need = group_ws(g);
+                        if (need && S->arena.take(need, &goff)) {
+                            gws = need;
+                            break;
+                        }
+                        if (g.size() == 1) break;
+                        g.resize(g.size() / 2);
+                    }
+                    if (!gws) continue;
+                    for (Req *q : g) S->queue.erase(std::find(S->queue.begin(), S->queue.end(), q));
+                    group = std::move(g);
+                    break;
+                }
                 size_t off = 0;
-                if (S->arena.take((*it)->ws, &off)) {
-                    job = *it;
-                    job->off = off;
+                if (S->arena.take(r->ws, &off)) {
+                    r->off = off;
+                    group.push_back(r);
                     S->queue.erase(it);
                     break;
                 }
             }
-            if (job || S->stop) break;
+            if (!group.empty() || S->stop) break;
             S->cv_work.wait(lk);
         }
-        if (!job) break;
+        if (group.empty()) break;
         ++S->busy;
         lk.unlock();
-        gfe_status rc = GFE_ECUDA;
-        if (st && (!job->ready || cudaStreamWaitEvent(st, job->ready, 0) == cudaSuccess))
-            rc = gfe_echelon(&job->A, &job->out, job->flags, S->base + job->off, job->ws, st);
-        if (job->ready) {
-            cudaEventDestroy(job->ready);
-            job->ready = nullptr;
+        gfe_status rc = st ? GFE_OK : GFE_ECUDA;
+        for (Req *r : group)
+            if (rc == GFE_OK && r->ready && cudaStreamWaitEvent(st, r->ready, 0) != cudaSuccess) rc = GFE_ECUDA;
+        if (rc == GFE_OK) {
+            if (gws) {  // one call for the group; it returns once queued: wait for its end
+                std::vector<gfe_matrix> As;
+                std::vector<gfe_result> outs;
+                for (Req *r : group) {
+                    As.push_back(r->A);
+                    outs.push_back(r->out);
+                }
+                rc = gfe_batch_echelon(As.data(), outs.data(), (int32_t)group.size(), group.front()->flags,
+                                       S->base + goff, gws, st);
+                if (rc == GFE_OK && !cuda_ok(cudaStreamSynchronize(st), "group sync")) rc = GFE_ECUDA;
+            } else {
+                Req *job = group.front();
+                rc = gfe_echelon(&job->A, &job->out, job->flags, S->base + job->off, job->ws, st);
+            }
         }
+        for (Req *r : group)
+            if (r->ready) {
+                cudaEventDestroy(r->ready);
+                r->ready = nullptr;
+            }
         std::string msg = rc ? gfe_last_error() : "";
         lk.lock();
         --S->busy;
-        S->arena.give(job->off, job->ws);
-        job->status = rc;
-        job->err = msg;
-        job->t_done = Clock::now();
+        if (gws) S->arena.give(goff, gws);
+        else S->arena.give(group.front()->off, group.front()->ws);
+        const Clock::time_point now = Clock::now();
+        for (Req *r : group) {
+            r->status = rc;
+            r->err = msg;
+            r->t_done = now;
+        }
         S->cv_done.notify_all();
         S->cv_work.notify_all();  // memory freed: others may fit now
     }
@@ -139,6 +215,11 @@ static void worker_loop(gfe_server *S) {
 }
 
 extern "C" {
+
+gfe_status gfe_set_server_group_work(double max_work) {
+    g_group_work.store(max_work);
+    return GFE_OK;
+}
 
 gfe_status gfe_server_create(gfe_server **out, size_t hbm_cap_bytes, int32_t workers, int32_t device) {
     if (!out || hbm_cap_bytes < 4096 || workers < 1 || workers > 64)

@@ -108,6 +108,42 @@ __device__ __forceinline__ uint32_t clear_byte(uint32_t x, int q, int base) {
     return (q >= base && q < base + 4) ? x & ~(0xFFu << (8 * (q - base))) : x;
 }
 
+// The outputs of one byte matrix from its final in-place state W (exact
+// residues): r, Ups, rho, and R, M, K gathered through the index lists.
+// Every thread of the CTA calls it.
+template <int THREADS, class Sh>
+__device__ void write_outputs_u8(const SmallJob &J, Sh &S, const uint8_t *W, int ldw) {
+    constexpr int WARPS = THREADS / 32;
+    const int m = J.m, n = J.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp == 0) {
+        const int r = split_list(S.piv_of_col, n, S.ups, S.upsbar);
+        if (lane == 0) S.r = r;
+    } else if (warp == 1) {
+        split_list(S.col_of_row, m, S.rho, S.rhobar);
+    }
+    __syncthreads();
+    const int r = S.r;
+    if (tid == 0) *J.rank = r;
+    for (int l = tid; l < r; l += THREADS) {
+        if (J.pcols) J.pcols[l] = S.ups[l];
+        if (J.prows) J.prows[l] = S.rho[l];
+    }
+    uint8_t *R = (uint8_t *)J.R, *M = (uint8_t *)J.M, *K = (uint8_t *)J.K;
+    for (int l = warp; l < r; l += WARPS) {
+        const uint8_t *src = W + S.piv_of_col[S.ups[l]] * ldw;
+        if (R)
+            for (int t = lane; t < n - r; t += 32) R[l * J.ldR + t] = src[S.upsbar[t]];
+        if (M)
+            for (int s2 = lane; s2 < r; s2 += 32) M[l * J.ldM + s2] = src[S.col_of_row[S.rho[s2]]];
+    }
+    if (K)
+        for (int t = warp; t < m - r; t += WARPS) {
+            const uint8_t *src = W + S.rhobar[t] * ldw;
+            for (int s2 = lane; s2 < r; s2 += 32) K[t * J.ldK + s2] = src[S.col_of_row[S.rho[s2]]];
+        }
+}
+
 // ---- GF(p), 3 <= p <= 13: one byte per entry, panels of BK columns --------
 constexpr int BK = 32;             // panel width: two 16-byte vectors per row
 constexpr int U8_THREADS = 1024;   // one thread per row (two rows above 1024) in the panel
@@ -335,33 +371,219 @@ __global__ void __launch_bounds__(U8_THREADS) k_ech_small_u8(const SmallJob *job
         }
         __syncthreads();
     }
-    // outputs
-    if (warp == 0) {
-        const int r = split_list(S.piv_of_col, n, S.ups, S.upsbar);
-        if (lane == 0) S.r = r;
-    } else if (warp == 1) {
-        split_list(S.col_of_row, m, S.rho, S.rhobar);
+    write_outputs_u8<U8_THREADS>(J, S, W, ldw);
+}
+
+// ---- GF(p), 17 <= p <= 251: one byte per entry, panels of BK columns held
+// as 16-bit lanes (a product (p-1)^2 no longer fits a byte) -----------------
+// Same route as k_ech_small_u8.  In the panel every pivot step is reduced at
+// once ((p-1) + (p-1)^2 < 2^16); the rest update accumulates the kp products
+// of an entry in a 32-bit lane ((p-1) + 32 (p-1)^2 < 2^21) and reduces once.
+constexpr int WP_THREADS = 1024;
+constexpr int WP_WARPS = WP_THREADS / 32;
+
+struct WShared {
+    uint16_t P[SMALL_MAX * BK];       // the panel, row j at BK j, exact residues
+    uint8_t OLD[BK * SMALL_MAX];      // this panel's pivot rows before the update (ldw apart)
+    int16_t piv_of_col[SMALL_MAX];
+    int16_t col_of_row[SMALL_MAX];
+    int16_t ups[SMALL_MAX], upsbar[SMALL_MAX], rho[SMALL_MAX], rhobar[SMALL_MAX];
+    alignas(16) uint16_t prow[BK];
+    alignas(16) uint8_t coef[WP_WARPS][BK];
+    int16_t piv_row[BK], piv_pc[BK];
+    uint8_t inv[256];
+    int wmin[WP_WARPS];
+    int r, kp;
+};
+
+// x mod p for x < 2^21 (rcp = ceil(2^32 / p))
+__device__ __forceinline__ uint32_t mod_small(uint32_t x, uint32_t p, uint32_t rcp) {
+    return x - p * __umulhi(x, rcp);
+}
+
+__global__ void __launch_bounds__(WP_THREADS, 1) k_ech_small_w(const SmallJob *jobs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WShared &S = *reinterpret_cast<WShared *>(smem_raw);
+    const SmallJob J = jobs[blockIdx.x];
+    const int m = J.m, n = J.n, p = J.p;
+    if (m <= 0 || n <= 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint8_t *W = (uint8_t *)J.W;
+    const int ldw = (int)J.ldw;
+    const uint8_t *A = (const uint8_t *)J.A;
+    const uint32_t up = (uint32_t)p;
+    const uint32_t rcp = (uint32_t)((0x100000000ull + (uint64_t)p - 1) / (uint64_t)p);
+    for (int a = tid; a < 256; a += WP_THREADS) {
+        int v = 0;
+        if (a > 0 && a < p)
+            for (int y = 1; y < p; ++y)
+                if (a * y % p == 1) {
+                    v = y;
+                    break;
+                }
+        S.inv[a] = (uint8_t)v;
+    }
+    for (int c = tid; c < n; c += WP_THREADS) S.piv_of_col[c] = -1;
+    for (int j = tid; j < m; j += WP_THREADS) S.col_of_row[j] = -1;
+    __syncthreads();
+    const int vpr = ldw >> 4;
+    for (int v = tid; v < m * vpr; v += WP_THREADS) {
+        const int j = v / vpr, k0 = (v - j * vpr) << 4;
+        uint32_t o[4] = {0u, 0u, 0u, 0u};
+        const uint8_t *a = A + (int64_t)j * J.lda;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (k0 + q < n) o[q >> 2] |= mod_small(a[k0 + q], up, rcp) << (8 * (q & 3));
+        *(uint4 *)(W + j * ldw + k0) = make_uint4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();
-    const int r = S.r;
-    if (tid == 0) *J.rank = r;
-    for (int l = tid; l < r; l += U8_THREADS) {
-        if (J.pcols) J.pcols[l] = S.ups[l];
-        if (J.prows) J.prows[l] = S.rho[l];
-    }
-    uint8_t *R = (uint8_t *)J.R, *M = (uint8_t *)J.M, *K = (uint8_t *)J.K;
-    for (int l = warp; l < r; l += U8_WARPS) {
-        const uint8_t *src = W + S.piv_of_col[S.ups[l]] * ldw;
-        if (R)
-            for (int t = lane; t < n - r; t += 32) R[l * J.ldR + t] = src[S.upsbar[t]];
-        if (M)
-            for (int s2 = lane; s2 < r; s2 += 32) M[l * J.ldM + s2] = src[S.col_of_row[S.rho[s2]]];
-    }
-    if (K)
-        for (int t = warp; t < m - r; t += U8_WARPS) {
-            const uint8_t *src = W + S.rhobar[t] * ldw;
-            for (int s2 = lane; s2 < r; s2 += 32) K[t * J.ldK + s2] = src[S.col_of_row[S.rho[s2]]];
+
+    for (int c0 = 0; c0 < n; c0 += BK) {
+        const int kw = min(BK, n - c0);
+        // panel load: 16 bytes -> 16 lanes of 16 bits (past the row pitch: zeros)
+        for (int v = tid; v < 2 * m; v += WP_THREADS) {
+            const int j = v >> 1, k = c0 + 16 * (v & 1);
+            uint4 b = k < ldw ? *(const uint4 *)(W + j * ldw + k) : make_uint4(0u, 0u, 0u, 0u);
+            uint4 *dst = (uint4 *)(S.P + j * BK + 16 * (v & 1));
+            dst[0] = make_uint4(__byte_perm(b.x, 0, 0x4140), __byte_perm(b.x, 0, 0x4342), __byte_perm(b.y, 0, 0x4140),
+                                __byte_perm(b.y, 0, 0x4342));
+            dst[1] = make_uint4(__byte_perm(b.z, 0, 0x4140), __byte_perm(b.z, 0, 0x4342), __byte_perm(b.w, 0, 0x4140),
+                                __byte_perm(b.w, 0, 0x4342));
         }
+        if (tid == 0) S.kp = 0;
+        __syncthreads();
+        int known = INT_MAX;
+        bool have_known = false;
+        for (int cc = 0; cc < kw; ++cc) {
+            int i;
+            if (have_known) {
+                i = known;
+            } else {
+                int best = INT_MAX;
+                for (int j = tid; j < m; j += WP_THREADS)
+                    if (S.col_of_row[j] < 0 && S.P[j * BK + cc]) {
+                        best = j;
+                        break;
+                    }
+                i = cta_min<WP_WARPS>(best, S.wmin);
+            }
+            have_known = false;
+            if (i == INT_MAX) continue;
+            const uint32_t s = up - S.inv[S.P[i * BK + cc]];
+            if (tid < BK)
+                S.prow[tid] = tid == cc ? (uint16_t)s : (tid < kw ? (uint16_t)mod_small(s * S.P[i * BK + tid], up, rcp) : 0);
+            if (tid == 0) {
+                S.piv_of_col[c0 + cc] = (int16_t)i;
+                S.col_of_row[i] = (int16_t)(c0 + cc);
+                S.piv_row[S.kp] = (int16_t)i;
+                S.piv_pc[S.kp] = (int16_t)cc;
+                S.kp = S.kp + 1;
+            }
+            __syncthreads();
+            const int c1 = cc + 1;
+            int best = INT_MAX;
+            const uint4 *pv = (const uint4 *)S.prow;
+            for (int j = tid; j < m; j += WP_THREADS) {
+                uint4 *row = (uint4 *)(S.P + j * BK);
+                if (j == i) {
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) row[h] = pv[h];
+                    continue;
+                }
+                const uint32_t f = S.P[j * BK + cc];
+                const bool cand = S.col_of_row[j] < 0 && c1 < kw;
+                if (f == 0) {
+                    if (cand && S.P[j * BK + c1]) best = min(best, j);
+                    continue;
+                }
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {  // lanes 8h .. 8h+7
+                    uint4 w = row[h];
+                    const uint4 q = pv[h];
+                    const int l = cc - 8 * h;  // lane of column cc in this vector, if 0 <= l < 8
+                    w.x = (l == 0) ? w.x & 0xFFFF0000u : ((l == 1) ? w.x & 0x0000FFFFu : w.x);
+                    w.y = (l == 2) ? w.y & 0xFFFF0000u : ((l == 3) ? w.y & 0x0000FFFFu : w.y);
+                    w.z = (l == 4) ? w.z & 0xFFFF0000u : ((l == 5) ? w.z & 0x0000FFFFu : w.z);
+                    w.w = (l == 6) ? w.w & 0xFFFF0000u : ((l == 7) ? w.w & 0x0000FFFFu : w.w);
+                    w.x = mod_lanes(w.x + f * q.x, up, rcp);
+                    w.y = mod_lanes(w.y + f * q.y, up, rcp);
+                    w.z = mod_lanes(w.z + f * q.z, up, rcp);
+                    w.w = mod_lanes(w.w + f * q.w, up, rcp);
+                    row[h] = w;
+                }
+                if (cand && S.P[j * BK + c1]) best = min(best, j);
+            }
+            const int nx = cta_min<WP_WARPS>(best, S.wmin);
+            if (nx != INT_MAX) {
+                known = nx;
+                have_known = true;
+            }
+        }
+        const int kp = S.kp;
+        if (kp > 0) {
+            for (int v = tid; v < kp * vpr; v += WP_THREADS) {
+                const int q = v / vpr, k0 = (v - q * vpr) << 4;
+                *(uint4 *)(S.OLD + q * ldw + k0) = *(const uint4 *)(W + S.piv_row[q] * ldw + k0);
+            }
+            __syncthreads();
+            for (int j = warp; j < m; j += WP_WARPS) {
+                uint32_t cq = 0;
+                if (lane < kp) {
+                    cq = S.P[j * BK + S.piv_pc[lane]];
+                    if (S.piv_row[lane] == j) cq = cq ? cq - 1 : up - 1;
+                    S.coef[warp][lane] = (uint8_t)cq;
+                }
+                if (!__any_sync(0xffffffffu, cq != 0)) continue;
+                __syncwarp();
+                uint8_t *row = W + j * ldw;
+                for (int k0 = lane << 3; k0 < ldw; k0 += 256) {
+                    if (k0 >= c0 && k0 < c0 + BK) continue;
+                    const uint2 w = *(const uint2 *)(row + k0);
+                    uint32_t acc[8];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        acc[e] = (w.x >> (8 * e)) & 0xFFu;
+                        acc[4 + e] = (w.y >> (8 * e)) & 0xFFu;
+                    }
+                    for (int q4 = 0; q4 < kp; q4 += 4) {
+                        const uint32_t c4 = *(const uint32_t *)(&S.coef[warp][q4]);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const uint32_t c = (c4 >> (8 * t)) & 0xFFu;
+                            if (q4 + t < kp && c) {
+                                const uint2 v = *(const uint2 *)(S.OLD + (q4 + t) * ldw + k0);
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    acc[e] += c * ((v.x >> (8 * e)) & 0xFFu);
+                                    acc[4 + e] += c * ((v.y >> (8 * e)) & 0xFFu);
+                                }
+                            }
+                        }
+                    }
+                    uint2 out = make_uint2(0u, 0u);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        out.x |= mod_small(acc[e], up, rcp) << (8 * e);
+                        out.y |= mod_small(acc[4 + e], up, rcp) << (8 * e);
+                    }
+                    *(uint2 *)(row + k0) = out;
+                }
+                __syncwarp();
+            }
+        }
+        // the panel back into W as bytes
+        for (int v = tid; v < 2 * m; v += WP_THREADS) {
+            const int j = v >> 1, k = c0 + 16 * (v & 1);
+            if (k < ldw) {
+                const uint4 *src = (const uint4 *)(S.P + j * BK + 16 * (v & 1));
+                const uint4 a = src[0], b = src[1];
+                *(uint4 *)(W + j * ldw + k) = make_uint4(__byte_perm(a.x, a.y, 0x6420), __byte_perm(a.z, a.w, 0x6420),
+                                                         __byte_perm(b.x, b.y, 0x6420), __byte_perm(b.z, b.w, 0x6420));
+            }
+        }
+        __syncthreads();
+    }
+    write_outputs_u8<WP_THREADS>(J, S, W, ldw);
 }
 
 // ---- GF(2), 64 columns per word ---------------------------------------------
@@ -481,18 +703,21 @@ __global__ void __launch_bounds__(SM_THREADS) k_ech_small_gf2(const SmallJob *jo
 
 }  // namespace
 
-void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int fmt) {
+void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int kind) {
     if (count <= 0) return;
-    static std::atomic<bool> attr_set[64];  // the byte kernel's dynamic shared memory, once per device
+    // the byte kernels' dynamic shared memory, set once per device
+    static std::atomic<bool> attr_set[64];
     int dev = 0;
-    if (fmt == GFE_U8 && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev].load()) {
+    if (kind != SMALL_GF2 && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev].load()) {
         cudaFuncSetAttribute(k_ech_small_u8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(U8Shared));
+        cudaFuncSetAttribute(k_ech_small_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WShared));
         attr_set[dev].store(true);
     }
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
-    if (fmt == GFE_BITS64) k_ech_small_gf2<<<count, SM_THREADS, 0, L.st>>>(jobs_dev);
-    else k_ech_small_u8<<<count, U8_THREADS, sizeof(U8Shared), L.st>>>(jobs_dev);
+    if (kind == SMALL_GF2) k_ech_small_gf2<<<count, SM_THREADS, 0, L.st>>>(jobs_dev);
+    else if (kind == SMALL_BYTES) k_ech_small_u8<<<count, U8_THREADS, sizeof(U8Shared), L.st>>>(jobs_dev);
+    else k_ech_small_w<<<count, WP_THREADS, sizeof(WShared), L.st>>>(jobs_dev);
     prof_end(L, K_ECH, ev, 0, 0, count, 0);
 }
 

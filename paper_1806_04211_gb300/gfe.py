@@ -64,6 +64,7 @@ SIGNATURES = {
     "gfe_set_batch_workers": (_i32, [_i32]),
     "gfe_set_wait_policy": (_i32, [_i32]),
     "gfe_set_batch_small_max": (_i32, [_i32, ctypes.c_double]),
+    "gfe_set_server_group_work": (_i32, [ctypes.c_double]),
     "gfe_server_create": (_i32, [ctypes.POINTER(_vp), ctypes.c_size_t, _i32, _i32]),
     "gfe_submit": (_i32, [_vp, ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), ctypes.c_uint32, _vp,
                           ctypes.POINTER(ctypes.c_uint64)]),

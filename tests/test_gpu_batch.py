@@ -82,15 +82,19 @@ def _check_vs_oracle(p, m, n, A, g):
         assert got.shape == want.shape and np.array_equal(got, want), (p, m, n, k)
 
 
-# edge shapes of the one-launch small-matrix kernel: single rows / columns,
+# edge shapes of the one-launch small-matrix kernels: single rows / columns,
 # ragged widths around the 16-byte vectors and 64-bit words, zero and
-# rank-deficient inputs, every field it takes (p = 11, 13: reduction every 2
-# and every pivot step), both sides of its 2048 limit
+# rank-deficient inputs, fields of all three kernels (p = 11, 13: lazy
+# reduction every 2 and every pivot step; p >= 17: the wide kernel), both
+# sides of the 2048 limit
 SMALL_CASES = [
     (3, 1, 1, None), (5, 1, 37, None), (7, 53, 1, None), (3, 17, 15, 0), (13, 64, 64, None),
     (11, 200, 129, 77), (13, 129, 200, None), (7, 300, 300, 180), (5, 511, 17, None), (3, 16, 2048, None),
     (2, 1, 1, None), (2, 1, 200, None), (2, 130, 1, None), (2, 65, 63, 0), (2, 257, 191, 100),
     (2, 700, 1500, None), (2, 2048, 64, None), (7, 2048, 40, 30),
+    # 17 <= p <= 251: the panel in 16-bit lanes, the rest update in 32-bit lanes
+    (17, 33, 47, None), (251, 300, 129, 77), (31, 129, 300, None), (101, 1, 40, None), (251, 64, 1, None),
+    (193, 700, 700, 300), (251, 2048, 50, None), (37, 17, 15, 0), (251, 511, 511, None),
 ]
 
 
@@ -110,7 +114,7 @@ def test_small_kernel_equals_worker_path_at_full_side():
     """2048 x 2048 (full rank and rank-deficient) by the one-launch kernel and
     by the blocked Chief on the workers: identical results; certified."""
     specs = [(2, 2048, 2048, None), (2, 2048, 2048, 1500), (7, 2048, 2048, None), (3, 1999, 2048, 1200),
-             (13, 2048, 1500, None)]
+             (13, 2048, 1500, None), (251, 2048, 2048, None), (17, 1800, 2048, 1100)]
     mats = [(p, m, n, synth.matrix(p, m, n, seed=950 + i, rank=rk)) for i, (p, m, n, rk) in enumerate(specs)]
     args = [(A.to(DEV), p, n) for p, m, n, A in mats]
     gfe.set_batch_small_max(2048, 1e12)  # above the default work cut-off: force the one-launch kernel

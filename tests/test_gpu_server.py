@@ -63,3 +63,31 @@ def test_server_rejects_oversize_request():
         A = synth.matrix(3, 2000, 2000, seed=1).to(DEV)
         with pytest.raises(gfe.GfeError):
             srv.submit(A, 3)
+
+
+def test_server_groups_small_requests_into_one_launch():
+    """A burst of small requests: a worker takes the queued ones together into
+    the one-launch kernels, so the server makes far fewer echelonisation
+    launches than requests (the per-request planner makes several leaves each);
+    every result still equals the matrix echelonised alone."""
+    fields = [2, 3, 7, 31, 251]
+    reqs = [(p, 300, synth.matrix(p, 300, 300, seed=300 + i, rank=150 if i % 4 == 0 else None).to(DEV))
+            for i, p in enumerate(fields * 8)]
+    torch.cuda.synchronize()
+    gfe.profile_enable(True, kinds=["other"])
+    gfe.profile_read()
+    gfe.lib().gfe_set_server_group_work(1e8)  # 300^3 is above the default
+    try:
+        with gfe.Server(8 << 30, workers=1) as srv:
+            tickets = [srv.submit(A, p, n if p == 2 else None) for p, n, A in reqs]
+            got = [srv.wait(t) for t in tickets]
+        launches = gfe.profile_read()["launches"]["ech_leaf"]
+    finally:
+        gfe.profile_enable(False)
+        gfe.lib().gfe_set_server_group_work(2e7)
+    assert launches < len(reqs), launches
+    for (p, n, A), g in zip(reqs, got):
+        alone = gfe.echelon(A, p, n=n if p == 2 else None)
+        assert g["rank"] == alone["rank"]
+        for k in ("rho", "ups", "R", "M", "K"):
+            assert torch.equal(g[k], alone[k]), (p, n, k)

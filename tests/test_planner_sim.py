@@ -237,9 +237,9 @@ def test_rank_deficient_wide_zero_blocks(sim, p):
 
 
 def test_small_batch_two_formats_without_races(sim):
-    """A batch of bit-packed GF(2) and byte matrices all taken by the
-    one-launch small-matrix path (a stream per storage format) plus one
-    GF(251) matrix on a worker: oracle results, no unordered access."""
+    """A batch of bit-packed GF(2) and byte matrices (small and large p) all
+    taken by the one-launch small-matrix path, one stream per kind of
+    kernel: oracle results, no unordered access."""
     rng = np.random.RandomState(11)
     specs = [(2, 70, 130), (3, 40, 33), (2, 1, 65), (13, 90, 64), (7, 17, 1), (2, 128, 128), (251, 30, 40)]
     keep, args, outs, refs = [], [], [], []
