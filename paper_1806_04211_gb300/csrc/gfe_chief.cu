@@ -103,7 +103,11 @@ struct StageGuard {
 };
 
 // side streams (non-blocking), borrowed per planner run and returned at its
-// end; a stream belongs to the device that was current when it was made
+// end; a stream belongs to the device that was current when it was made.
+// Their priority is one below the critical path's and above the default, so
+// that beside other work on the device (the batched form's one-launch
+// kernels, whose CTAs hold an SM for long) the planner's CTAs are scheduled
+// first as SMs come free.
 static std::mutex g_stream_mu;
 static std::vector<std::pair<int, cudaStream_t>> g_stream_free;
 
@@ -118,7 +122,10 @@ static cudaStream_t stream_acquire(int dev) {
             }
     }
     cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return nullptr;
+    const int prio = greatest < least ? greatest + 1 : least;
+    if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio) != cudaSuccess) return nullptr;
     return s;
 }
 
