@@ -137,11 +137,11 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
 /*
  * Matrices of a batch with at most `side` rows and columns (side <= 2048,
  * the default) and work m n min(m,n) at most max_work (<= 0: the default
- * 4e9), over GF(2) (GFE_BITS64) or GF(p) with 3 <= p <= 13 (GFE_U8), with no
+ * 4e9), over GF(2) (GFE_BITS64) or any odd prime p <= 251 (GFE_U8), with no
  * dense E / T asked for, are echelonised together by ONE kernel launch per
- * storage format, one thread block per matrix, with no host round trip; the
- * others go to the workers below.  side = 0 sends every matrix to the
- * workers.  GFE_EINVAL if side < 0.
+ * kind (p <= 13, larger p, GF(2)), one thread block per matrix, with no host
+ * round trip; the others go to the workers below.  side = 0 sends every
+ * matrix to the workers.  GFE_EINVAL if side < 0.
  */
 gfe_status gfe_set_batch_small_max(int32_t side, double max_work);
 /* number of concurrent workers of gfe_batch_echelon (<= 0: default 8; at

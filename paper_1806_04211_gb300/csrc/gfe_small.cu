@@ -1,6 +1,6 @@
-// Batched form for small matrices: ONE launch echelonises a whole list of
-// independent matrices (rows and columns up to SMALL_MAX), one CTA per
-// matrix, the entire method inside the CTA.  For matrices this small the
+// Batched form for small matrices: ONE launch per kind of kernel echelonises
+// a whole list of independent matrices (rows and columns up to SMALL_MAX),
+// one CTA per matrix, the entire method inside the CTA.  For matrices this small the
 // blocked scheme's work is dominated by its per-block launches and host
 // round trips; here each matrix costs no launch of its own and no host
 // synchronisation at all.
@@ -28,6 +28,8 @@
 //     as a rank-kp multiply-add (two entries per 32-bit word in 16-bit
 //     lanes, exact reduction at the end), so each row is read and written
 //     once per panel instead of once per pivot;
+//   * GF(p), 17 <= p <= 251: the same route with the panel in 16-bit lanes,
+//     reduced after every pivot step, and the rest update in 32-bit lanes;
 //   * GF(2), unblocked: 64 columns per word; eliminating with pivot row i is
 //     an XOR of row i, minus its bit c, into every row with bit c set (that
 //     bit then holds the transformation entry, 1);
