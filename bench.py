@@ -262,7 +262,10 @@ def c5_requests(count, seed=1):
     return out
 
 
-def bench_batched(dev, count, plain_count=512):
+C4_WORKERS = 16  # planner workers for the matrices above the one-launch kernels' work cut-off
+
+
+def bench_batched(dev, count, plain_count=512, clock_index=None):
     """C4: gfe_batch_echelon over `count` matrices of the seeded draw (median
     of three calls after one untimed call) vs the plain per-matrix path on the
     first `plain_count`.  The library sends a matrix of side <= 2048 and work
@@ -274,14 +277,18 @@ def bench_batched(dev, count, plain_count=512):
     mats = [(synth.matrix(p, m, n, seed=5000 + i, rank=rk, device=dev), p, n) for i, (p, m, n, rk) in enumerate(specs)]
     units = float(sum(m * n * min(m, n) for p, m, n, rk in specs))
     one_launch = sum(1 for p, m, n, rk in specs if m * n * min(m, n) <= 4e9 and (p == 2 or p <= 13))
-    gfe.batch_echelon(mats)
+    gfe.batch_echelon(mats, workers=C4_WORKERS)
     torch.cuda.synchronize()
     times = []
+    clocks = Clocks(clock_index) if clock_index is not None else None
+    if clocks:
+        clocks.start()
     for _ in range(3):
         t = time.perf_counter()
-        res = gfe.batch_echelon(mats)
+        res = gfe.batch_echelon(mats, workers=C4_WORKERS)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t)
+    clk = clocks.stop() if clocks else None
     tb = sorted(times)[1]
     madds = float(sum(m * n * d["rank"] for (p, m, n, rk), d in zip(specs, res)))
     pc = min(plain_count, count)
@@ -292,7 +299,8 @@ def bench_batched(dev, count, plain_count=512):
     tp = time.perf_counter() - t
     return {"matrices": count, "of": 4096, "batched_matrices_per_s": count / tb, "plain_matrices_per_s": pc / tp,
             "speedup": (tp / pc) / (tb / count), "batched_madds_per_s": madds / tb, "wall_ms": tb * 1e3,
-            "wall_ms_runs": [x * 1e3 for x in times], "one_launch_matrices": one_launch,
+            "wall_ms_runs": [x * 1e3 for x in times], "clocks": clk, "workers": C4_WORKERS,
+            "one_launch_matrices": one_launch,
             "planner_matrices": count - one_launch, "plain_sample": pc,
             "sample": "seeded C4 draw, %d matrices (sum m*n*min(m,n) = %.3g), median of 3 calls; plain path "
                       "timed on the first %d" % (count, units, pc)}
@@ -531,11 +539,11 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.n)
     batched = served = c3 = None
+    if rank == 0 and not args.no_forms:  # the CUDA-core forms first, before the long tensor-core C3 leg
+        batched = bench_batched(dev, args.c4, clock_index=local)
+        served = bench_serving(dev, 24, args.c5)
     if rank == 0 and not args.no_c3:
         c3 = bench_c3(dev)
-    if rank == 0 and not args.no_forms:
-        batched = bench_batched(dev, args.c4)
-        served = bench_serving(dev, 24, args.c5)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "mul-adds/s", "n_gpus": ws, "steps": args.steps,

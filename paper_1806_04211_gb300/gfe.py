@@ -363,14 +363,20 @@ def _alloc_results(args, dev, transform: bool):
 
 
 def batch_echelon(mats, transform: bool = True, impl: str = "tensor", workers: int | None = None, stream=None):
-    """gfe_batch_echelon over a list of (A, p) or (A, p, n) tuples; returns a list of dicts."""
+    """gfe_batch_echelon over a list of (A, p) or (A, p, n) tuples; returns a
+    list of result mappings.  `workers` applies to this call only (the
+    library's worker count returns to its default afterwards)."""
     args = [matrix_arg(*mt) if len(mt) == 3 else matrix_arg(mt[0], mt[1]) for mt in mats]
     if not args:
         return []
-    dev = mats[0][0].device
-    flags = (WANT_TRANSFORM if transform else 0) | _impl_flag(impl)
     if workers is not None:
         _check(lib().gfe_set_batch_workers(workers))
+        try:
+            return batch_echelon(mats, transform, impl, None, stream)
+        finally:
+            lib().gfe_set_batch_workers(0)
+    dev = mats[0][0].device
+    flags = (WANT_TRANSFORM if transform else 0) | _impl_flag(impl)
     arr = (GfeMatrix * len(args))(*args)
     bufs, slots, res = _alloc_results(args, dev, transform)
     ress = (GfeResult * len(args))(*res)
