@@ -47,17 +47,16 @@ namespace gfe {
 
 namespace {
 
-constexpr int SM_THREADS = 512;
-constexpr int SM_WARPS = SM_THREADS / 32;
+// the GF(2) kernel's CTA and shared memory
+constexpr int G2_THREADS = 512;
+constexpr int G2_WARPS = G2_THREADS / 32;
 
-struct SmallShared {
+struct G2Shared {
     int16_t piv_of_col[SMALL_MAX];  // pivot row of column c, -1: none
     int16_t col_of_row[SMALL_MAX];  // the column row j is the pivot of, -1: none
     int16_t ups[SMALL_MAX], upsbar[SMALL_MAX], rho[SMALL_MAX], rhobar[SMALL_MAX];
-    alignas(16) uint8_t prow[SMALL_MAX];  // the scaled pivot row (GF(2): its words)
-    uint8_t red[256];                     // x mod p
-    uint8_t inv[16];                      // a^-1 mod p
-    int wmin[SM_WARPS];
+    alignas(16) uint64_t prow[SMALL_MAX / 64];  // the pivot row without its pivot bit
+    int wmin[G2_WARPS];
     int r;
 };
 
@@ -589,7 +588,7 @@ __global__ void __launch_bounds__(WP_THREADS, 1) k_ech_small_w(const SmallJob *j
 }
 
 // ---- GF(2), 64 columns per word ---------------------------------------------
-__device__ void small_gf2(const SmallJob &J, SmallShared &S) {
+__device__ void small_gf2(const SmallJob &J, G2Shared &S) {
     const int m = J.m, n = J.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint64_t *W = (uint64_t *)J.W;
@@ -597,10 +596,10 @@ __device__ void small_gf2(const SmallJob &J, SmallShared &S) {
     const int nw = (n + 63) >> 6;
     const uint64_t *A = (const uint64_t *)J.A;
     const int64_t ldaq = J.lda >> 3;
-    uint64_t *prow = (uint64_t *)S.prow;
-    for (int c = tid; c < n; c += SM_THREADS) S.piv_of_col[c] = -1;
-    for (int j = tid; j < m; j += SM_THREADS) S.col_of_row[j] = -1;
-    for (int v = tid; v < m * ldq; v += SM_THREADS) {
+    uint64_t *prow = S.prow;
+    for (int c = tid; c < n; c += G2_THREADS) S.piv_of_col[c] = -1;
+    for (int j = tid; j < m; j += G2_THREADS) S.col_of_row[j] = -1;
+    for (int v = tid; v < m * ldq; v += G2_THREADS) {
         const int j = v / ldq, q = v - j * ldq;
         uint64_t x = 0;
         if (q < nw) {
@@ -620,12 +619,12 @@ __device__ void small_gf2(const SmallJob &J, SmallShared &S) {
             i = known;
         } else {
             int best = INT_MAX;
-            for (int j = tid; j < m; j += SM_THREADS)
+            for (int j = tid; j < m; j += G2_THREADS)
                 if (S.col_of_row[j] < 0 && (W[(int64_t)j * ldq + cw] & cb)) {
                     best = j;
                     break;
                 }
-            i = cta_min<SM_WARPS>(best, S.wmin);
+            i = cta_min<G2_WARPS>(best, S.wmin);
         }
         have_known = false;
         if (i == INT_MAX) continue;
@@ -639,7 +638,7 @@ __device__ void small_gf2(const SmallJob &J, SmallShared &S) {
         const int c1 = c + 1, c1w = c1 >> 6;
         const uint64_t c1b = 1ull << (c1 & 63);
         int best = INT_MAX;
-        for (int j = warp; j < m; j += SM_WARPS) {
+        for (int j = warp; j < m; j += G2_WARPS) {
             if (j == i) continue;
             uint64_t *row = W + (int64_t)j * ldq;
             const uint64_t x = lane < nw ? row[lane] : 0ull;
@@ -652,7 +651,7 @@ __device__ void small_gf2(const SmallJob &J, SmallShared &S) {
             }
             if (cand && lane == c1w && (y & c1b)) best = min(best, j);
         }
-        const int nx = cta_min<SM_WARPS>(best, S.wmin);
+        const int nx = cta_min<G2_WARPS>(best, S.wmin);
         if (nx != INT_MAX) {
             known = nx;
             have_known = true;
@@ -668,7 +667,7 @@ __device__ void small_gf2(const SmallJob &J, SmallShared &S) {
     __syncthreads();
     const int r = S.r;
     if (tid == 0) *J.rank = r;
-    for (int l = tid; l < r; l += SM_THREADS) {
+    for (int l = tid; l < r; l += G2_THREADS) {
         if (J.pcols) J.pcols[l] = S.ups[l];
         if (J.prows) J.prows[l] = S.rho[l];
     }
@@ -686,18 +685,18 @@ __device__ void small_gf2(const SmallJob &J, SmallShared &S) {
         }
     };
     uint64_t *R = (uint64_t *)J.R, *M = (uint64_t *)J.M, *K = (uint64_t *)J.K;
-    for (int l = warp; l < r; l += SM_WARPS) {
+    for (int l = warp; l < r; l += G2_WARPS) {
         const uint64_t *src = W + (int64_t)S.piv_of_col[S.ups[l]] * ldq;
         if (R) gather(src, S.upsbar, n - r, R + l * (J.ldR >> 3), false);
         if (M) gather(src, S.rho, r, M + l * (J.ldM >> 3), true);
     }
     if (K)
-        for (int t = warp; t < m - r; t += SM_WARPS)
+        for (int t = warp; t < m - r; t += G2_WARPS)
             gather(W + (int64_t)S.rhobar[t] * ldq, S.rho, r, K + t * (J.ldK >> 3), true);
 }
 
-__global__ void __launch_bounds__(SM_THREADS) k_ech_small_gf2(const SmallJob *jobs) {
-    __shared__ SmallShared S;
+__global__ void __launch_bounds__(G2_THREADS) k_ech_small_gf2(const SmallJob *jobs) {
+    __shared__ G2Shared S;
     const SmallJob J = jobs[blockIdx.x];
     if (J.m <= 0 || J.n <= 0) return;
     small_gf2(J, S);
@@ -717,7 +716,7 @@ void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int k
     }
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
-    if (kind == SMALL_GF2) k_ech_small_gf2<<<count, SM_THREADS, 0, L.st>>>(jobs_dev);
+    if (kind == SMALL_GF2) k_ech_small_gf2<<<count, G2_THREADS, 0, L.st>>>(jobs_dev);
     else if (kind == SMALL_BYTES) k_ech_small_u8<<<count, U8_THREADS, sizeof(U8Shared), L.st>>>(jobs_dev);
     else k_ech_small_w<<<count, WP_THREADS, sizeof(WShared), L.st>>>(jobs_dev);
     prof_end(L, K_ECH, ev, 0, 0, count, 0);
