@@ -30,9 +30,11 @@
 //     once per panel instead of once per pivot;
 //   * GF(p), 17 <= p <= 251: the same route with the panel in 16-bit lanes,
 //     reduced after every pivot step, and the rest update in 32-bit lanes;
-//   * GF(2), unblocked: 64 columns per word; eliminating with pivot row i is
-//     an XOR of row i, minus its bit c, into every row with bit c set (that
-//     bit then holds the transformation entry, 1);
+//   * GF(2): 64 columns per word, panels of one word per row; eliminating
+//     with pivot row i is an XOR of row i, minus its bit c, into every row
+//     with bit c set (that bit then holds the transformation entry, 1); the
+//     rest of a row is updated once per panel by XORs of the panel's pivot
+//     rows, four at a time through 16-entry tables of their combinations;
 //   * the search for the next column's pivot row is fused into the update of
 //     the rows (each thread tests the entry it has just written), so a pivot
 //     step is one pass and three CTA barriers.
@@ -47,17 +49,21 @@ namespace gfe {
 
 namespace {
 
-// the GF(2) kernel's CTA and shared memory
-constexpr int G2_THREADS = 512;
+// the GF(2) kernel's CTA and shared memory (dynamic)
+constexpr int G2_THREADS = 1024;
 constexpr int G2_WARPS = G2_THREADS / 32;
+constexpr int G2_WORDS = SMALL_MAX / 64;  // words of the longest row
 
 struct G2Shared {
     int16_t piv_of_col[SMALL_MAX];  // pivot row of column c, -1: none
     int16_t col_of_row[SMALL_MAX];  // the column row j is the pivot of, -1: none
     int16_t ups[SMALL_MAX], upsbar[SMALL_MAX], rho[SMALL_MAX], rhobar[SMALL_MAX];
-    alignas(16) uint64_t prow[SMALL_MAX / 64];  // the pivot row without its pivot bit
+    uint64_t P[SMALL_MAX];            // the panel: word pw of every row
+    uint64_t OLD[64][G2_WORDS];       // this panel's pivot rows before its update
+    uint64_t T[16][16][G2_WORDS];     // T[g][t]: XOR of OLD rows 4g + b over the set bits b of t
+    int16_t piv_row[64], piv_pc[64];  // this panel's pivots: row, bit in the panel word
     int wmin[G2_WARPS];
-    int r;
+    int r, kp;
 };
 
 // minimum of v over the CTA of WARPS warps (every thread calls it, every
@@ -592,11 +598,10 @@ __device__ void small_gf2(const SmallJob &J, G2Shared &S) {
     const int m = J.m, n = J.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint64_t *W = (uint64_t *)J.W;
-    const int ldq = (int)(J.ldw >> 3);  // words per workspace row, >= nw, <= 32
+    const int ldq = (int)(J.ldw >> 3);  // words per workspace row, >= nw, <= G2_WORDS
     const int nw = (n + 63) >> 6;
     const uint64_t *A = (const uint64_t *)J.A;
     const int64_t ldaq = J.lda >> 3;
-    uint64_t *prow = S.prow;
     for (int c = tid; c < n; c += G2_THREADS) S.piv_of_col[c] = -1;
     for (int j = tid; j < m; j += G2_THREADS) S.col_of_row[j] = -1;
     for (int v = tid; v < m * ldq; v += G2_THREADS) {
@@ -609,55 +614,98 @@ __device__ void small_gf2(const SmallJob &J, G2Shared &S) {
         W[(int64_t)j * ldq + q] = x;
     }
     __syncthreads();
-    int known = INT_MAX;
-    bool have_known = false;
-    for (int c = 0; c < n; ++c) {
-        const int cw = c >> 6;
-        const uint64_t cb = 1ull << (c & 63);
-        int i;
-        if (have_known) {
-            i = known;
-        } else {
-            int best = INT_MAX;
-            for (int j = tid; j < m; j += G2_THREADS)
-                if (S.col_of_row[j] < 0 && (W[(int64_t)j * ldq + cw] & cb)) {
-                    best = j;
-                    break;
-                }
-            i = cta_min<G2_WARPS>(best, S.wmin);
-        }
-        have_known = false;
-        if (i == INT_MAX) continue;
-        // -a^-1 = 1: the pivot row is row i; bit c keeps the transformation entry 1
-        if (tid < nw) prow[tid] = W[(int64_t)i * ldq + tid] & (tid == cw ? ~cb : ~0ull);
-        if (tid == 0) {
-            S.piv_of_col[c] = (int16_t)i;
-            S.col_of_row[i] = (int16_t)c;
-        }
+    // panels of 64 columns: word pw of every row
+    for (int pw = 0; pw < nw; ++pw) {
+        const int c0 = pw << 6, kw = min(64, n - c0);
+        for (int j = tid; j < m; j += G2_THREADS) S.P[j] = W[(int64_t)j * ldq + pw];
+        if (tid == 0) S.kp = 0;
         __syncthreads();
-        const int c1 = c + 1, c1w = c1 >> 6;
-        const uint64_t c1b = 1ull << (c1 & 63);
-        int best = INT_MAX;
-        for (int j = warp; j < m; j += G2_WARPS) {
-            if (j == i) continue;
-            uint64_t *row = W + (int64_t)j * ldq;
-            const uint64_t x = lane < nw ? row[lane] : 0ull;
-            const bool f = (__shfl_sync(0xffffffffu, x, cw) & cb) != 0;
-            const bool cand = S.col_of_row[j] < 0 && c1 < n;
-            uint64_t y = x;
-            if (f && lane < nw) {
-                y = x ^ prow[lane];
-                row[lane] = y;
+        int known = INT_MAX;
+        bool have_known = false;
+        for (int cc = 0; cc < kw; ++cc) {
+            const uint64_t cb = 1ull << cc;
+            int i;
+            if (have_known) {
+                i = known;
+            } else {
+                int best = INT_MAX;
+                for (int j = tid; j < m; j += G2_THREADS)
+                    if (S.col_of_row[j] < 0 && (S.P[j] & cb)) {
+                        best = j;
+                        break;
+                    }
+                i = cta_min<G2_WARPS>(best, S.wmin);
             }
-            if (cand && lane == c1w && (y & c1b)) best = min(best, j);
+            have_known = false;
+            if (i == INT_MAX) continue;
+            // -a^-1 = 1: row i minus its bit cc (which then holds the transformation entry 1)
+            const uint64_t pr = S.P[i] & ~cb;
+            if (tid == 0) {
+                S.piv_of_col[c0 + cc] = (int16_t)i;
+                S.col_of_row[i] = (int16_t)(c0 + cc);
+                S.piv_row[S.kp] = (int16_t)i;
+                S.piv_pc[S.kp] = (int16_t)cc;
+                S.kp = S.kp + 1;
+            }
+            __syncthreads();
+            const int c1 = cc + 1;
+            const uint64_t c1b = c1 < 64 ? 1ull << c1 : 0ull;
+            int best = INT_MAX;
+            for (int j = tid; j < m; j += G2_THREADS) {
+                if (j == i) continue;
+                uint64_t x = S.P[j];
+                if (x & cb) {
+                    x ^= pr;
+                    S.P[j] = x;
+                }
+                if (c1 < kw && S.col_of_row[j] < 0 && (x & c1b)) best = min(best, j);
+            }
+            const int nx = cta_min<G2_WARPS>(best, S.wmin);
+            if (nx != INT_MAX) {
+                known = nx;
+                have_known = true;
+            }
         }
-        const int nx = cta_min<G2_WARPS>(best, S.wmin);
-        if (nx != INT_MAX) {
-            known = nx;
-            have_known = true;
+        const int kp = S.kp;
+        if (kp > 0) {
+            for (int v = tid; v < kp * nw; v += G2_THREADS) {
+                const int q = v / nw, w = v - q * nw;
+                S.OLD[q][w] = W[(int64_t)S.piv_row[q] * ldq + w];
+            }
+            __syncthreads();
+            const int ng = (kp + 3) >> 2;
+            for (int v = tid; v < ng * 16 * nw; v += G2_THREADS) {
+                const int g = v / (16 * nw), rem = v - g * 16 * nw, t = rem / nw, w = rem - t * nw;
+                uint64_t x = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (((t >> b) & 1) && 4 * g + b < kp) x ^= S.OLD[4 * g + b][w];
+                S.T[g][t][w] = x;
+            }
+            __syncthreads();
+            // every row: rest ^= sum of the pivot rows its coefficient bits select
+            // (coefficient q: bit piv_pc[q] of its panel word, minus 1 on pivot row q itself)
+            for (int j = warp; j < m; j += G2_WARPS) {
+                const uint64_t pj = S.P[j];
+                const bool b0 = lane < kp && ((((pj >> S.piv_pc[lane]) & 1ull) != 0) != (S.piv_row[lane] == j));
+                const bool b1 =
+                    lane + 32 < kp && ((((pj >> S.piv_pc[lane + 32]) & 1ull) != 0) != (S.piv_row[lane + 32] == j));
+                const uint64_t cbits =
+                    (uint64_t)__ballot_sync(0xffffffffu, b0) | ((uint64_t)__ballot_sync(0xffffffffu, b1) << 32);
+                if (!cbits) continue;
+                if (lane < nw && lane != pw) {
+                    uint64_t x = W[(int64_t)j * ldq + lane];
+                    for (int g = 0; g < ng; ++g) {
+                        const int t = (int)((cbits >> (4 * g)) & 15ull);
+                        if (t) x ^= S.T[g][t][lane];
+                    }
+                    W[(int64_t)j * ldq + lane] = x;
+                }
+            }
         }
+        for (int j = tid; j < m; j += G2_THREADS) W[(int64_t)j * ldq + pw] = S.P[j];
+        __syncthreads();
     }
-    __syncthreads();
     if (warp == 0) {
         const int r = split_list(S.piv_of_col, n, S.ups, S.upsbar);
         if (lane == 0) S.r = r;
@@ -695,8 +743,9 @@ __device__ void small_gf2(const SmallJob &J, G2Shared &S) {
             gather(W + (int64_t)S.rhobar[t] * ldq, S.rho, r, K + t * (J.ldK >> 3), true);
 }
 
-__global__ void __launch_bounds__(G2_THREADS) k_ech_small_gf2(const SmallJob *jobs) {
-    __shared__ G2Shared S;
+__global__ void __launch_bounds__(G2_THREADS, 1) k_ech_small_gf2(const SmallJob *jobs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    G2Shared &S = *reinterpret_cast<G2Shared *>(smem_raw);
     const SmallJob J = jobs[blockIdx.x];
     if (J.m <= 0 || J.n <= 0) return;
     small_gf2(J, S);
@@ -709,14 +758,15 @@ void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int k
     // the byte kernels' dynamic shared memory, set once per device
     static std::atomic<bool> attr_set[64];
     int dev = 0;
-    if (kind != SMALL_GF2 && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev].load()) {
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev].load()) {
         cudaFuncSetAttribute(k_ech_small_u8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(U8Shared));
         cudaFuncSetAttribute(k_ech_small_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WShared));
+        cudaFuncSetAttribute(k_ech_small_gf2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(G2Shared));
         attr_set[dev].store(true);
     }
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
-    if (kind == SMALL_GF2) k_ech_small_gf2<<<count, G2_THREADS, 0, L.st>>>(jobs_dev);
+    if (kind == SMALL_GF2) k_ech_small_gf2<<<count, G2_THREADS, sizeof(G2Shared), L.st>>>(jobs_dev);
     else if (kind == SMALL_BYTES) k_ech_small_u8<<<count, U8_THREADS, sizeof(U8Shared), L.st>>>(jobs_dev);
     else k_ech_small_w<<<count, WP_THREADS, sizeof(WShared), L.st>>>(jobs_dev);
     prof_end(L, K_ECH, ev, 0, 0, count, 0);
