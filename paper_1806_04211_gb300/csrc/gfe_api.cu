@@ -501,7 +501,7 @@ static gfe_status batch_plan(const gfe_matrix *As, int32_t count, uint32_t flags
         off += al256((size_t)As[i].m * (size_t)small_ldw(As[i].fmt, As[i].n));
     }
     P.jobs_off = off;
-    if (!P.small.empty()) off += al256(P.small.size() * sizeof(SmallJob));
+    if (!P.small.empty()) off += al256(P.small.size() * sizeof(SmallJob)) + 256;  // + the three job counters
     P.total = off;
     return GFE_OK;
 }
@@ -603,7 +603,8 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
         for (int k = 0; ok && k < 3; ++k) {
             if (nkind[k]) {
                 L.st = small_st[k];
-                ech_small_batch(L, djobs + first, nkind[k], k);
+                int *counters = (int *)((char *)ws + P.jobs_off + al256(P.small.size() * sizeof(SmallJob)));
+                ech_small_batch(L, djobs + first, nkind[k], k, counters + k);
                 ok = cuda_ok(cudaGetLastError(), "small-matrix launch") &&
                      cuda_ok(cudaEventCreateWithFlags(&small_done[k], cudaEventDisableTiming), "event") &&
                      cuda_ok(cudaEventRecord(small_done[k], small_st[k]), "event record");

@@ -1,6 +1,7 @@
-// Batched form for small matrices: ONE launch per kind of kernel echelonises
-// a whole list of independent matrices (rows and columns up to SMALL_MAX),
-// one CTA per matrix, the entire method inside the CTA.  For matrices this small the
+// Batched form for small matrices: ONE persistent launch per kind of kernel
+// echelonises a whole list of independent matrices (rows and columns up to
+// SMALL_MAX); a CTA per SM takes the matrices one after the other from a
+// device counter and runs the entire method on each.  For matrices this small the
 // blocked scheme's work is dominated by its per-block launches and host
 // round trips; here each matrix costs no launch of its own and no host
 // synchronisation at all.
@@ -179,12 +180,8 @@ __device__ __forceinline__ uint32_t mod_lanes(uint32_t w, uint32_t p, uint32_t r
     return lo | (hi << 16);
 }
 
-__global__ void __launch_bounds__(U8_THREADS) k_ech_small_u8(const SmallJob *jobs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    U8Shared &S = *reinterpret_cast<U8Shared *>(smem_raw);
-    const SmallJob J = jobs[blockIdx.x];
+__device__ void small_u8(const SmallJob &J, U8Shared &S) {
     const int m = J.m, n = J.n, p = J.p;
-    if (m <= 0 || n <= 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint8_t *W = (uint8_t *)J.W;
     const int ldw = (int)J.ldw;  // multiple of 16, >= n, <= SMALL_MAX
@@ -408,12 +405,8 @@ __device__ __forceinline__ uint32_t mod_small(uint32_t x, uint32_t p, uint32_t r
     return x - p * __umulhi(x, rcp);
 }
 
-__global__ void __launch_bounds__(WP_THREADS, 1) k_ech_small_w(const SmallJob *jobs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    WShared &S = *reinterpret_cast<WShared *>(smem_raw);
-    const SmallJob J = jobs[blockIdx.x];
+__device__ void small_w(const SmallJob &J, WShared &S) {
     const int m = J.m, n = J.n, p = J.p;
-    if (m <= 0 || n <= 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint8_t *W = (uint8_t *)J.W;
     const int ldw = (int)J.ldw;
@@ -743,32 +736,57 @@ __device__ void small_gf2(const SmallJob &J, G2Shared &S) {
             gather(W + (int64_t)S.rhobar[t] * ldq, S.rho, r, K + t * (J.ldK >> 3), true);
 }
 
-__global__ void __launch_bounds__(G2_THREADS, 1) k_ech_small_gf2(const SmallJob *jobs) {
+// One persistent launch per kernel kind: a CTA per SM claims the next matrix
+// of the table (largest first) from an atomic counter until none is left.
+template <class Sh, void (*JOB)(const SmallJob &, Sh &)>
+__device__ __forceinline__ void run_jobs(const SmallJob *jobs, int count, int *next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    G2Shared &S = *reinterpret_cast<G2Shared *>(smem_raw);
-    const SmallJob J = jobs[blockIdx.x];
-    if (J.m <= 0 || J.n <= 0) return;
-    small_gf2(J, S);
+    Sh &S = *reinterpret_cast<Sh *>(smem_raw);
+    __shared__ int job;
+    for (;;) {
+        if (threadIdx.x == 0) job = atomicAdd(next, 1);
+        __syncthreads();
+        const int q = job;
+        if (q >= count) break;
+        const SmallJob J = jobs[q];
+        if (J.m > 0 && J.n > 0) JOB(J, S);
+        __syncthreads();  // the shared state and `job` are reused by the next matrix
+    }
+}
+
+__global__ void __launch_bounds__(U8_THREADS, 1) k_ech_small_u8(const SmallJob *jobs, int count, int *next) {
+    run_jobs<U8Shared, small_u8>(jobs, count, next);
+}
+__global__ void __launch_bounds__(WP_THREADS, 1) k_ech_small_w(const SmallJob *jobs, int count, int *next) {
+    run_jobs<WShared, small_w>(jobs, count, next);
+}
+__global__ void __launch_bounds__(G2_THREADS, 1) k_ech_small_gf2(const SmallJob *jobs, int count, int *next) {
+    run_jobs<G2Shared, small_gf2>(jobs, count, next);
 }
 
 }  // namespace
 
-void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int kind) {
+void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int kind, int *next) {
     if (count <= 0) return;
-    // the byte kernels' dynamic shared memory, set once per device
-    static std::atomic<bool> attr_set[64];
+    // dynamic shared memory and the SM count, once per device
+    static std::atomic<int> sms[64];
     int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev].load()) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    if (!sms[dev].load()) {
         cudaFuncSetAttribute(k_ech_small_u8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(U8Shared));
         cudaFuncSetAttribute(k_ech_small_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WShared));
         cudaFuncSetAttribute(k_ech_small_gf2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(G2Shared));
-        attr_set[dev].store(true);
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        sms[dev].store(n);
     }
+    const int grid = count < sms[dev].load() ? count : sms[dev].load();  // one CTA per SM (their shared memory)
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
-    if (kind == SMALL_GF2) k_ech_small_gf2<<<count, G2_THREADS, sizeof(G2Shared), L.st>>>(jobs_dev);
-    else if (kind == SMALL_BYTES) k_ech_small_u8<<<count, U8_THREADS, sizeof(U8Shared), L.st>>>(jobs_dev);
-    else k_ech_small_w<<<count, WP_THREADS, sizeof(WShared), L.st>>>(jobs_dev);
+    cudaMemsetAsync(next, 0, sizeof(int), L.st);
+    if (kind == SMALL_GF2) k_ech_small_gf2<<<grid, G2_THREADS, sizeof(G2Shared), L.st>>>(jobs_dev, count, next);
+    else if (kind == SMALL_BYTES) k_ech_small_u8<<<grid, U8_THREADS, sizeof(U8Shared), L.st>>>(jobs_dev, count, next);
+    else k_ech_small_w<<<grid, WP_THREADS, sizeof(WShared), L.st>>>(jobs_dev, count, next);
     prof_end(L, K_ECH, ev, 0, 0, count, 0);
 }
 

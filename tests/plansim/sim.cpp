@@ -253,8 +253,9 @@ void any_nonzero(const Launch& L, int64_t rows, int64_t cols, const void* A, int
 // (column-by-column Gauss-Jordan on [A | 1] with the topmost available row as
 // pivot, pivots scaled to -1), written in the API storage; the workspace
 // area of a job is marked written, as the kernel works in place there
-void ech_small_batch(const Launch& L, const SmallJob* jobs, int count, int) {
+void ech_small_batch(const Launch& L, const SmallJob* jobs, int count, int, int* next) {
     setL(L, "ech_small_batch");
+    chk(next, 4, "job counter", true);
     chk(jobs, sizeof(SmallJob) * count, "jobs");
     for (int q = 0; q < count; ++q) {
         const SmallJob& J = jobs[q];
