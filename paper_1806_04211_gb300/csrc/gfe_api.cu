@@ -604,8 +604,7 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
             if (nkind[k]) {
                 L.st = small_st[k];
                 int *counters = (int *)((char *)ws + P.jobs_off + al256(P.small.size() * sizeof(SmallJob)));
-                ech_small_batch(L, djobs + first, nkind[k], k, counters + k);
-                ok = cuda_ok(cudaGetLastError(), "small-matrix launch") &&
+                ok = cuda_ok(ech_small_batch(L, djobs + first, nkind[k], k, counters + k), "small-matrix launch") &&
                      cuda_ok(cudaEventCreateWithFlags(&small_done[k], cudaEventDisableTiming), "event") &&
                      cuda_ok(cudaEventRecord(small_done[k], small_st[k]), "event record");
             }

@@ -112,7 +112,7 @@ inline int small_kind(int p, int fmt) { return fmt == 1 ? SMALL_GF2 : (p <= SMAL
 inline int64_t small_ldw(int fmt, int64_t n) { return fmt == 1 ? (n + 127) / 128 * 16 : (n + 15) / 16 * 16; }
 // one persistent launch for count jobs of one kind (SmallKind): a CTA per SM
 // takes jobs in table order through the device counter *next (zeroed here)
-void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int kind, int *next);
+cudaError_t ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int kind, int *next);
 
 // An index array for a gather: a device copy, or, when it has at most
 // MAP_INLINE entries, the host array itself, which is then passed by value

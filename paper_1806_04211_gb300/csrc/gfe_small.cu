@@ -766,12 +766,14 @@ __global__ void __launch_bounds__(G2_THREADS, 1) k_ech_small_gf2(const SmallJob 
 
 }  // namespace
 
-void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int kind, int *next) {
-    if (count <= 0) return;
+cudaError_t ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int kind, int *next) {
+    if (count <= 0) return cudaSuccess;
     // dynamic shared memory and the SM count, once per device
     static std::atomic<int> sms[64];
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!sms[dev].load()) {
         cudaFuncSetAttribute(k_ech_small_u8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(U8Shared));
         cudaFuncSetAttribute(k_ech_small_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WShared));
@@ -783,11 +785,14 @@ void ech_small_batch(const Launch &L, const SmallJob *jobs_dev, int count, int k
     const int grid = count < sms[dev].load() ? count : sms[dev].load();  // one CTA per SM (their shared memory)
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
-    cudaMemsetAsync(next, 0, sizeof(int), L.st);
+    e = cudaMemsetAsync(next, 0, sizeof(int), L.st);
+    if (e != cudaSuccess) return e;
     if (kind == SMALL_GF2) k_ech_small_gf2<<<grid, G2_THREADS, sizeof(G2Shared), L.st>>>(jobs_dev, count, next);
     else if (kind == SMALL_BYTES) k_ech_small_u8<<<grid, U8_THREADS, sizeof(U8Shared), L.st>>>(jobs_dev, count, next);
     else k_ech_small_w<<<grid, WP_THREADS, sizeof(WShared), L.st>>>(jobs_dev, count, next);
+    e = cudaGetLastError();
     prof_end(L, K_ECH, ev, 0, 0, count, 0);
+    return e;
 }
 
 }  // namespace gfe

@@ -253,7 +253,7 @@ void any_nonzero(const Launch& L, int64_t rows, int64_t cols, const void* A, int
 // (column-by-column Gauss-Jordan on [A | 1] with the topmost available row as
 // pivot, pivots scaled to -1), written in the API storage; the workspace
 // area of a job is marked written, as the kernel works in place there
-void ech_small_batch(const Launch& L, const SmallJob* jobs, int count, int, int* next) {
+cudaError_t ech_small_batch(const Launch& L, const SmallJob* jobs, int count, int, int* next) {
     setL(L, "ech_small_batch");
     chk(next, 4, "job counter", true);
     chk(jobs, sizeof(SmallJob) * count, "jobs");
@@ -308,6 +308,7 @@ void ech_small_batch(const Launch& L, const SmallJob* jobs, int count, int, int*
             pad(J.R, J.ldR, r, n - r); pad(J.M, J.ldM, r, r); pad(J.K, J.ldK, m - r, r);
         }
     }
+    return cudaSuccess;
 }
 void write_i64(const Launch&, int64_t* dst, const int32_t* src, int64_t count, int64_t offset) { for (int64_t t = 0; t < count; ++t) dst[t] = src[t] + offset; }
 }
