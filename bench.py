@@ -269,14 +269,14 @@ def bench_batched(dev, count, plain_count=512, clock_index=None):
     """C4: gfe_batch_echelon over `count` matrices of the seeded draw (median
     of three calls after one untimed call) vs the plain per-matrix path on the
     first `plain_count`.  The library sends a matrix of side <= 2048 and work
-    m n min(m,n) <= 4e9 over GF(2) or GF(p <= 13) to its one-launch kernel
-    (one thread block per matrix) and the rest to its blocked planner."""
+    m n min(m,n) <= 4e9 (GF(2): a 16th of it) to its one-launch kernels (one
+    thread block per matrix) and the rest to its blocked planner."""
     import torch
     from paper_1806_04211_gb300 import gfe, synth
     specs = c4_matrices(count)
     mats = [(synth.matrix(p, m, n, seed=5000 + i, rank=rk, device=dev), p, n) for i, (p, m, n, rk) in enumerate(specs)]
     units = float(sum(m * n * min(m, n) for p, m, n, rk in specs))
-    one_launch = sum(1 for p, m, n, rk in specs if m * n * min(m, n) <= 4e9 and (p == 2 or p <= 13))
+    one_launch = sum(1 for p, m, n, rk in specs if m * n * min(m, n) / (16 if p == 2 else 1) <= 4e9)
     gfe.batch_echelon(mats, workers=C4_WORKERS)
     torch.cuda.synchronize()
     times = []
