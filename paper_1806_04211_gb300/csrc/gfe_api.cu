@@ -617,9 +617,12 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
             ok = cuda_ok(cudaEventCreateWithFlags(&small_done[0], cudaEventDisableTiming), "event") &&
                  cuda_ok(cudaEventRecord(small_done[0], small_st[0]), "event record");
         }
-        if (!ok) {
+        if (!ok) {  // what was launched still uses the workspace: let it finish first
             for (int k = 0; k < 3; ++k) {
-                if (small_st[k]) cudaStreamDestroy(small_st[k]);
+                if (small_st[k]) {
+                    cudaStreamSynchronize(small_st[k]);
+                    cudaStreamDestroy(small_st[k]);
+                }
                 if (small_done[k]) cudaEventDestroy(small_done[k]);
             }
             cudaEventDestroy(start);

@@ -144,19 +144,26 @@ static void worker_loop(gfe_server *S) {
                         if ((*jt)->flags == r->flags && takes_group(*jt))
                             g.push_back(*jt);
                     // the largest prefix of the group whose workspace fits
+                    bool sized = true;
                     for (;;) {
                         const size_t need = group_ws(g);
-                        if (need && S->arena.take(need, &goff)) {
+                        if (!need) {  // cannot size it as a group: the request goes alone (below)
+                            sized = false;
+                            break;
+                        }
+                        if (S->arena.take(need, &goff)) {
                             gws = need;
                             break;
                         }
                         if (g.size() == 1) break;
                         g.resize(g.size() / 2);
                     }
-                    if (!gws) continue;
-                    for (Req *q : g) S->queue.erase(std::find(S->queue.begin(), S->queue.end(), q));
-                    group = std::move(g);
-                    break;
+                    if (gws) {
+                        for (Req *q : g) S->queue.erase(std::find(S->queue.begin(), S->queue.end(), q));
+                        group = std::move(g);
+                        break;
+                    }
+                    if (sized) continue;  // no room now: retried when memory comes free
                 }
                 size_t off = 0;
                 if (S->arena.take(r->ws, &off)) {
