@@ -201,8 +201,8 @@ def roofline(prof, codec_bytes, trace):
                 "achieved_per_launch_avg": 2.0 * madds / (ms * 1e-3) / 1e12,
                 "algorithmic_flops_per_launch": 2.0 * madds / launches,
                 "algorithmic_bytes_per_launch": prof["bytes"][k] / max(prof["launches"][k], 1)}
-    # CUDA-core multiply-add: 2 integer ops (IMAD) per multiply-add; peak =
-    # 152 SMs x 128 INT32 lanes x max SM clock
+    # CUDA-core multiply-add: 2 integer ops (one IMAD) per multiply-add; peak =
+    # 152 SMs x 128 INT32 lanes x the maximum SM clock x 2 ops per IMAD
     peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 * 2 / 1e12
     achieved = 2.0 * madds / (ms * 1e-3) / 1e12
     return {"kernel": "k_mad_plain (CUDA-core int32)", "bound": "alu", "achieved": achieved, "peak": peak,
