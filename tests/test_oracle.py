@@ -8,6 +8,7 @@ import pytest
 
 from conftest import load_golden
 from oracle import oracle as O
+from paper_1806_04211_gb300 import synth
 
 # ---------------------------------------------------------------------------
 # independent helpers (no oracle code)
@@ -414,3 +415,102 @@ def test_certificate_gf2_accepts_and_rejects():
         arr.view(np.uint64)[0, 0] ^= np.uint64(1 << 3)
         bad[key] = arr
         assert O.certify_gf2(W, m, n, bad) != 0, key
+
+
+@pytest.mark.parametrize("m,n,rank", [(1, 1, None), (70, 130, None), (130, 70, None), (300, 300, 150),
+                                      (257, 513, None), (600, 400, 250)])
+def test_openmp_baseline_equals_oracle(m, n, rank):
+    """The OpenMP timing baseline runs the oracle's GF(2) algorithm on all
+    host cores; its outputs equal the oracle's."""
+    A = synth.matrix(2, m, n, seed=77, rank=rank).numpy()
+    ref = O.echelon_gf2(A, m, n)
+    got = O.echelon_gf2_omp(A, m, n)
+    assert got["rank"] == ref["rank"]
+    for k in ("rho", "ups", "M", "K", "R"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+# ---------------------------------------------------------------------------
+# solving and kernels (the paper's variant list, Section 1; Eq. (echelon))
+# ---------------------------------------------------------------------------
+
+def _all_vectors(p, length):
+    return np.array(list(itertools.product(range(p), repeat=length)), dtype=np.int64).reshape(-1, length)
+
+
+@pytest.mark.parametrize("p,m,n", [(3, 3, 3), (3, 2, 4), (2, 4, 3), (2, 3, 5)])
+def test_nullspaces_brute_force(p, m, n):
+    """Every matrix of the shape: the basis rows span exactly the vectors
+    brute force finds in the left / right kernel, have the stated size, and
+    are the identity on rho_bar / Ups_bar."""
+    ys, xs = _all_vectors(p, m), _all_vectors(p, n)
+    for flat in itertools.product(range(p), repeat=m * n):
+        A = np.array(flat, dtype=np.uint8).reshape(m, n)
+        A64 = A.astype(np.int64)
+        left = {y.astype(np.uint8).tobytes() for y in ys if not ((y @ A64) % p).any()}
+        right = {x.astype(np.uint8).tobytes() for x in xs if not ((A64 @ x) % p).any()}
+        NL, NR = O.nullspace_left(A, p), O.nullspace_right(A, p)
+        r = brute_rank(A, p)
+        assert NL.shape == (m - r, m) and NR.shape == (n - r, n)
+        assert rowspace(NL, p) == left
+        assert rowspace(NR, p) == right
+
+
+def test_nullspace_structure_random():
+    for p, m, n, k in [(7, 40, 30, 12), (251, 25, 60, 20), (2, 50, 70, 33), (5, 60, 60, None)]:
+        A = synth.matrix(p, m, n, seed=3, rank=k).numpy() if p != 2 else \
+            O.unpack_bits(synth.matrix(2, m, n, seed=3, rank=k).numpy(), n)
+        res = O.echelon(A, p)
+        r = res["rank"]
+        NL, NR = O.nullspace_left(A, p), O.nullspace_right(A, p)
+        assert not ((NL.astype(np.int64) @ A) % p).any()
+        assert not ((A.astype(np.int64) @ NR.T.astype(np.int64)) % p).any()
+        nbar = np.setdiff1d(np.arange(m), res["rho"])
+        ubar = np.setdiff1d(np.arange(n), res["ups"])
+        assert np.array_equal(NL[:, nbar], np.eye(m - r, dtype=np.uint8))
+        assert np.array_equal(NR[:, ubar], np.eye(n - r, dtype=np.uint8))
+
+
+@pytest.mark.parametrize("p,m,n", [(3, 2, 3), (3, 3, 2), (2, 3, 3), (2, 2, 4)])
+def test_solve_brute_force(p, m, n):
+    """Every matrix and every right-hand side: consistent iff some x solves
+    it (brute force); then the returned x solves it and is zero on the
+    non-pivot columns, which brute force shows is unique."""
+    xs, bs = _all_vectors(p, n), _all_vectors(p, m)
+    for flat in itertools.product(range(p), repeat=m * n):
+        A = np.array(flat, dtype=np.uint8).reshape(m, n)
+        A64 = A.astype(np.int64)
+        images = {}
+        for x in xs:
+            images.setdefault(((A64 @ x) % p).astype(np.uint8).tobytes(), []).append(x)
+        X, ok = O.solve(A, p, bs.T.astype(np.uint8))
+        ups = O.echelon(A, p)["ups"]
+        ubar = np.setdiff1d(np.arange(n), ups)
+        for j, b in enumerate(bs):
+            sols = images.get(b.astype(np.uint8).tobytes(), [])
+            assert ok[j] == bool(sols)
+            if sols:
+                assert np.array_equal((A64 @ X[:, j]) % p, b)
+                zero_free = [x for x in sols if not x[ubar].any()]
+                assert len(zero_free) == 1 and np.array_equal(zero_free[0], X[:, j])
+
+
+def test_solve_random_consistent_and_planted():
+    for p, m, n, k in [(7, 60, 45, 30), (251, 40, 70, 25), (2, 64, 64, 40), (3, 30, 80, None)]:
+        A = (synth.matrix(p, m, n, seed=8, rank=k).numpy() if p != 2 else
+             O.unpack_bits(synth.matrix(2, m, n, seed=8, rank=k).numpy(), n)).astype(np.uint8)
+        X0 = synth.uniform_u8(n, 9, p, 8, 3).numpy().astype(np.int64)
+        B = ((A.astype(np.int64) @ X0) % p).astype(np.uint8)
+        r = O.echelon(A, p)["rank"]
+        if r < m:  # a column outside the column space: a left-kernel vector y has y b != 0
+            y = O.nullspace_left(A, p)[0].astype(np.int64)
+            e = np.zeros(m, np.int64)
+            e[np.nonzero(y)[0][0]] = 1
+            B[:, 4] = (B[:, 4].astype(np.int64) + e) % p
+        X, ok = O.solve(A, p, B)
+        for j in range(B.shape[1]):
+            if ok[j]:
+                assert np.array_equal((A.astype(np.int64) @ X[:, j]) % p, B[:, j])
+        assert ok.sum() == B.shape[1] - (1 if r < m else 0)
+        if r < m:
+            assert not ok[4]
