@@ -6,9 +6,12 @@ matrix of the workload, inputs resident in HBM.  Metric: m*n*r / time in
 GF(p) multiply-adds per second (bit multiply-adds for GF(2)), the paper's
 cost model (Section 5: an alpha x beta block of rank r costs alpha*beta*r).
 
-Default workload: the bit-packed GF(2) configuration at n = 32768, i.e. one
-uniform Bernoulli(1/2) matrix and its rank-deficient twin (product of
-n x 0.75n and 0.75n x n factors), seeded (synth.py).
+Default workload: the largest single-GPU configuration, bit-packed GF(2) at
+n = 100000, i.e. one uniform Bernoulli(1/2) matrix and its rank-deficient
+twin (product of n x 0.75n and 0.75n x n factors), seeded (synth.py).  The
+plain CUDA-core comparator runs on the n = 32768 member of the same family
+(at n = 100000 it would take minutes per matrix), beside the tensor-core
+path on the same inputs.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n N]
 
@@ -39,12 +42,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--n", type=int, default=100000)
+    ap.add_argument("--plain-n", type=int, default=32768, help="side of the tensor-vs-plain comparison")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain CUDA-core comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched (C4) and served (C5) legs")
     ap.add_argument("--c4", type=int, default=4096, help="matrices of the batched leg")
-    ap.add_argument("--c5", type=int, default=120, help="measured requests of the serving leg")
+    ap.add_argument("--c5", type=int, default=2000, help="measured requests of the serving leg")
+    ap.add_argument("--c5-warmup", type=int, default=200, help="warm-up requests of the serving leg")
+    ap.add_argument("--cpu-omp-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-c3", action="store_true", help="skip the C3 tensor-vs-plain leg")
     return ap.parse_args()
 
@@ -199,6 +205,7 @@ def roofline(prof, codec_bytes, trace):
                 "union_ms": um, "sum_of_launch_ms": ms,
                 "launches": launches, "avg_launch_ms": ms / launches,
                 "achieved_per_launch_avg": 2.0 * madds / (ms * 1e-3) / 1e12,
+                "frac_per_launch_avg": 2.0 * madds / (ms * 1e-3) / 1e12 / peak,
                 "algorithmic_flops_per_launch": 2.0 * madds / launches,
                 "algorithmic_bytes_per_launch": prof["bytes"][k] / max(prof["launches"][k], 1)}
     # CUDA-core multiply-add: 2 integer ops (one IMAD) per multiply-add; peak =
@@ -211,55 +218,86 @@ def roofline(prof, codec_bytes, trace):
             "launches": launches, "avg_launch_ms": ms / launches}
 
 
-def cpu_baseline(n):
-    """The oracle, as it stands, on a bounded sample: a uniform GF(2) matrix
-    of side n_s = min(n, 8192) drawn like the workload's (about 5-15 s on one core)."""
+def host_info():
+    """The timing host: logical CPUs and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or "unknown",
+            "machine": platform.machine()}
+
+
+CPU_SAMPLE = 8192
+
+
+def cpu_omp_worker(ns):
+    """Runs in a child process (OMP_WAIT_POLICY=active, all cores): the
+    OpenMP variant of the oracle's GF(2) elimination on the sample; prints
+    one JSON line."""
     from oracle import oracle as O
     from paper_1806_04211_gb300 import synth
-    ns = min(n, 8192)
+    A = synth.matrix(2, ns, ns, seed=1).numpy()
+    O.echelon_gf2_omp(A[:256], 256, ns)  # thread pool up
+    t = time.perf_counter()
+    r = O.echelon_gf2_omp(A, ns, ns)
+    dt = time.perf_counter() - t
+    print(json.dumps({"seconds": dt, "rank": r["rank"], "threads": O.omp_threads()}), flush=True)
+
+
+def cpu_baseline(n):
+    """The oracle, as it stands, on a bounded sample: a uniform GF(2) matrix
+    of side n_s = min(n, 8192) drawn like the workload's, single-threaded
+    (about 5 s), and the OpenMP variant of the same elimination on all host
+    cores (a child process) on the same sample."""
+    from oracle import oracle as O
+    from paper_1806_04211_gb300 import synth
+    ns = min(n, CPU_SAMPLE)
     A = synth.matrix(2, ns, ns, seed=1).numpy()
     t = time.perf_counter()
     r = O.echelon_gf2(A, ns, ns, want_E=False, want_T=False)
     dt = time.perf_counter() - t
-    return {"value": ns * ns * r["rank"] / dt, "unit": "mul-adds/s", "cores": 1, "kind": "oracle",
-            "sample": "one uniform GF(2) %dx%d matrix (bit-packed oracle, echelon + transformation), %.1f s"
-                      % (ns, ns, dt)}
-
-
-PRIMES = [q for q in range(2, 252) if all(q % d for d in range(2, int(q ** 0.5) + 1))]
+    out = {"value": ns * ns * r["rank"] / dt, "unit": "mul-adds/s", "cores": 1, "kind": "oracle",
+           "sample": "one uniform GF(2) %dx%d matrix of the workload's distribution (bit-packed oracle, "
+                     "echelon + transformation), %.1f s" % (ns, ns, dt),
+           "host": host_info()}
+    try:
+        env = dict(os.environ, OMP_WAIT_POLICY="active")
+        proc = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-omp-worker", str(ns)],
+                              capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+        d = json.loads(proc.stdout.strip().splitlines()[-1])
+        assert d["rank"] == r["rank"]
+        out["openmp"] = {"value": ns * ns * d["rank"] / d["seconds"], "unit": "mul-adds/s",
+                         "cores": d["threads"], "kind": "oracle algorithm, OpenMP (rows in parallel per pivot)",
+                         "seconds": d["seconds"], "sample": "the same matrix"}
+    except Exception as e:  # the single-threaded figure stands on its own
+        out["openmp"] = {"unavailable": repr(e)[:200]}
+    return out
 
 
 def c4_matrices(count, seed=1):
-    """Batched workload (C4): m, n log-uniform in [64, 2048] with aspect ratio
-    <= 4, p uniform in {2, 3, 5, 7}, half of them of rank 0.6 * min(m, n)."""
-    import numpy as np
-    rng = np.random.RandomState(seed)
-    out = []
-    while len(out) < count:
-        m, n = (int(round(64 * 32 ** rng.rand())) for _ in range(2))
-        if max(m, n) > 4 * min(m, n):
-            continue
-        p = [2, 3, 5, 7][rng.randint(4)]
-        rk = int(0.6 * min(m, n)) if len(out) % 2 else None
-        out.append((p, m, n, rk))
-    return out
+    from paper_1806_04211_gb300 import synth
+    return synth.c4_specs(count, seed)
 
 
 def c5_requests(count, seed=1):
-    """Served workload (C5): square n ~ Pareto(1.5) on [256, 16384] (rejection),
-    p uniform over the primes <= 251, 30% of rank 0.6 n."""
-    import numpy as np
-    rng = np.random.RandomState(seed)
-    out = []
-    while len(out) < count:
-        n = 256 * (1 - rng.rand()) ** (-1 / 1.5)
-        if n > 16384:
-            continue
-        n = int(n)
-        p = PRIMES[rng.randint(len(PRIMES))]
-        rk = int(0.6 * n) if rng.rand() < 0.3 else None
-        out.append((p, n, rk))
-    return out
+    from paper_1806_04211_gb300 import synth
+    return synth.c5_specs(count, seed)
 
 
 C4_WORKERS = 16  # planner workers for the matrices above the one-launch kernels' work cut-off
@@ -420,13 +458,17 @@ def run_reference(args, ws, rank):
             "data": "synthetic (seeded SplitMix64)",
             "config": {"workload": workload_name(args.n), "sample": "uniform %dx%d per step" % (ns, ns)},
             "cpu_baseline": {"value": v, "unit": "mul-adds/s", "cores": 1, "kind": "oracle",
-                             "sample": "uniform GF(2) %dx%d, bit-packed oracle, 1 thread" % (ns, ns)},
+                             "sample": "uniform GF(2) %dx%d, bit-packed oracle, 1 thread" % (ns, ns),
+                             "host": host_info()},
             "e2e": {"value": v, "unit": "mul-adds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.cpu_omp_worker:
+        cpu_omp_worker(args.cpu_omp_worker)
+        return
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
@@ -438,14 +480,19 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    insts = []
-    for idx, (p, m, n, rk) in enumerate(workload(args.n)):
-        A = synth.matrix(p, m, n, seed=1 + 1000 * rank + idx, rank=rk, device=dev)
-        insts.append((p, m, n, A))
+
+    def make_insts(n):
+        out = []
+        for idx, (p, m, nn, rk) in enumerate(workload(n)):
+            A = synth.matrix(p, m, nn, seed=1 + 1000 * rank + idx, rank=rk, device=dev)
+            out.append((p, m, nn, A))
+        return out
+
+    insts = make_insts(args.n)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     codec_bytes = 1  # GF(2) entries are stored as e4m3 centred residues inside the library
 
-    def step(impl):
+    def step(impl, insts):
         # the tensor-core path runs the workload's matrices through the
         # batched entry point (concurrent workers); the plain comparator is
         # the per-matrix path, one call after the other
@@ -460,7 +507,7 @@ def main():
             units += m * n * d["rank"]
         return units
 
-    def timed(impl, steps, prof_kinds=None):
+    def timed(impl, insts, steps):
         per, units = [], 0.0
         barrier(ws)
         torch.cuda.synchronize()
@@ -469,7 +516,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            units += step(impl)
+            units += step(impl, insts)
             e1.record(stream)
             e1.synchronize()
             per.append(e0.elapsed_time(e1))
@@ -478,14 +525,14 @@ def main():
         return per, units
 
     for _ in range(args.warmup):
-        step("tensor")
+        step("tensor", insts)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
     gfe.profile_enable(True, kinds=["mad_tensor", "mad_plain"])
     gfe.profile_read(True)
     gfe.trace_enable(1 << 21)
-    per, units = timed("tensor", args.steps)
+    per, units = timed("tensor", insts, args.steps)
     prof = gfe.profile_read(True)
     trace = gfe.trace_read(True)
     gfe.trace_enable(0)
@@ -495,16 +542,6 @@ def main():
     all_units = allsum(ws, units, dev)
     value = all_units / (tot_ms * 1e-3)
     launches = sum(prof["launches"].values())
-
-    # plain CUDA-core path on the same inputs (the comparator the metric names)
-    plain = None
-    if not args.no_plain:
-        for _ in range(1):
-            step("plain")
-        pper, punits = timed("plain", max(1, min(args.steps, 2)))
-        pt = allmax(ws, sum(pper), dev)
-        plain = {"value": allsum(ws, punits, dev) / (pt * 1e-3), "unit": "mul-adds/s",
-                 "ms_per_step": pt / len(pper)}
 
     # end to end through the public API with host buffers: H2D of the inputs,
     # echelonisation, D2H of every output (rank, pivots, R, M, K)
@@ -532,8 +569,32 @@ def main():
             d2h += 8 + sum(o.numel() * o.element_size() for o in outs)
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
+        del devs, res
     e2e_ms = allmax(ws, e2e_ms, dev)
     e2e_units = allsum(ws, e2e_units, dev)
+    del insts, host_in, host_out
+    gfe.release_workspace()
+    torch.cuda.empty_cache()
+    print("main leg: %.4g mul-adds/s, %.1f ms per step; e2e %.4g" % (value, tot_ms / args.steps,
+                                                                     e2e_units / (e2e_ms * 1e-3)),
+          file=sys.stderr, flush=True)
+
+    # the plain CUDA-core path (the comparator the metric names) beside the
+    # tensor-core path, on the same inputs of a smaller member of the family
+    plain = None
+    if not args.no_plain:
+        pinsts = make_insts(args.plain_n)
+        step("tensor", pinsts)
+        tper, tunits = timed("tensor", pinsts, 1)
+        pper, punits = timed("plain", pinsts, 1)
+        tt, pt = allmax(ws, sum(tper), dev), allmax(ws, sum(pper), dev)
+        plain = {"workload": workload_name(args.plain_n), "value": allsum(ws, punits, dev) / (pt * 1e-3),
+                 "unit": "mul-adds/s", "ms_per_step": pt,
+                 "tensor_same_inputs": {"value": allsum(ws, tunits, dev) / (tt * 1e-3), "ms_per_step": tt},
+                 "speedup": pt / tt}
+        del pinsts
+        gfe.release_workspace()
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -541,7 +602,11 @@ def main():
     batched = served = c3 = None
     if rank == 0 and not args.no_forms:  # the CUDA-core forms first, before the long tensor-core C3 leg
         batched = bench_batched(dev, args.c4, clock_index=local)
-        served = bench_serving(dev, 24, args.c5)
+        gfe.release_workspace()
+        torch.cuda.empty_cache()
+        served = bench_serving(dev, args.c5_warmup, args.c5)
+        gfe.release_workspace()
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_c3:
         c3 = bench_c3(dev)
 
@@ -550,7 +615,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "e4m3 operands, fp32 exact-integer accumulation",
                 "data": "synthetic (seeded SplitMix64; uniform + low-rank twin)",
-                "config": {"workload": workload_name(args.n), "p": 2, "n": args.n, "matrices_per_gpu": len(insts),
+                "config": {"workload": workload_name(args.n), "p": 2, "n": args.n, "matrices_per_gpu": len(workload(args.n)),
                            "l2": "flushed between steps (256 MiB write)", "parallelism": "independent matrices per GPU"},
                 "roofline": roofline(prof, codec_bytes, trace),
                 "plain_gpu_path": plain,
@@ -562,7 +627,9 @@ def main():
                 "served_C5": served,
                 "clocks": clk,
                 "gpu_launches": launches,
-                "profile": {"ms": prof["ms"], "launches": prof["launches"], "host_syncs": prof["host_syncs"]}}
+                "gpu_launches_per_step": launches / max(args.steps, 1),
+                "profile": {"ms": prof["ms"], "launches": prof["launches"], "host_syncs": prof["host_syncs"],
+                            "host_syncs_per_step": prof["host_syncs"] / max(args.steps, 1)}}
         print(json.dumps(line), flush=True)
     barrier(ws)
 

@@ -197,11 +197,53 @@ gfe_status gfe_server_destroy(gfe_server *server);
 gfe_status gfe_set_server_group_work(double max_work);
 
 /*
+ * Solving and null spaces from the echelon result.  The transformation
+ * matrix is what gives these (the paper's list of variants, Section 1):
+ * with T = (M 0; K 1) P_rho and T A = E (Eq. (echelon), Section 3.1),
+ *   left null space  {y : y A = 0} has the basis (K 1) P_rho, the rows r..m-1
+ *     of T: row t holds K[t, s] at column rho_s and 1 at column rho_bar_t;
+ *   right null space {x : A x = 0} has the basis whose vector j is 1 at the
+ *     non-pivot column Ups_bar_j, 0 at the other non-pivot columns and
+ *     R[l, j] at the pivot column Ups_l (from E_top x = 0, E_top = -RREF);
+ *   A X = B: column b is consistent iff (T b)[r..] = K b[rho] + b[rho_bar]
+ *     is zero, and then X[Ups_l] = -(M b[rho])[l] with every non-pivot
+ *     variable 0 solves it.
+ * A describes the matrix that was echelonised (p, m, n, fmt; its data is
+ * not read) and res is gfe_echelon's result for it (device rank, pivots,
+ * and K (left), R (right), or M and K (solve)).  Storage is A's: GFE_U8
+ * residues, or GF(2) rows of 64-bit words (ld in bytes, a multiple of 8).
+ *
+ * gfe_nullspace: writes the basis, one vector per row, into N: (m - r) rows
+ *   of m entries (GFE_LEFT) or (n - r) rows of n entries (GFE_RIGHT); N must
+ *   hold m (n) rows when the rank is not known on the host.  Asynchronous
+ *   on `stream` (the pivots stay on the device).  GFE_EINVAL for a bad side,
+ *   a missing K (left) or R (right), or ldn too small.
+ * gfe_solve: B is m x k, X is n x k (pitches ldb, ldx in bytes); X gets the
+ *   solution above for every column (meaningful where consistent[j] = 1);
+ *   consistent (device, k int32) gets 1 for columns in the column space of
+ *   A, else 0.  ws: gfe_solve_workspace(A, k) bytes (its last 256 bytes hold
+ *   the call's status word).  The call reads the rank on `stream` to size
+ *   its two multiply-adds, and returns once the result is complete there.
+ */
+#define GFE_LEFT 0
+#define GFE_RIGHT 1
+gfe_status gfe_nullspace(const gfe_matrix *A, const gfe_result *res, int32_t side, void *N, int64_t ldn,
+                         void *stream);
+size_t gfe_solve_workspace(const gfe_matrix *A, int64_t k);
+gfe_status gfe_solve(const gfe_matrix *A, const gfe_result *res, const void *B, int64_t ldb, int64_t k,
+                     void *X, int64_t ldx, int32_t *consistent, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * gfe_mad -- the job MAD (Section 4.1): C := W + A B over GF(p), A m x k,
  * B k x n, W and C m x n, all GFE_U8 residues (device).  W may be NULL
- * (C := A B, the job MUL) and may equal C.  ws: gfe_mad_workspace() bytes.
- * The block multiply-add is the dominant cost of the method (Section 5,
- * Lemma "closecosts").
+ * (C := A B, the job MUL) and may equal C.  ws: gfe_mad_workspace() bytes;
+ * its last 256 bytes hold the call's own status word, which the call zeroes
+ * on `stream` before the product.  The call returns once the product is
+ * complete on `stream`: it reads that word with a copy on `stream` (no
+ * device-wide or legacy-stream synchronisation), and returns GFE_ETIMEOUT if
+ * a bounded wait of the tensor-core kernel gave up.  Errors of one call are
+ * never reported by another.  The block multiply-add is the dominant cost of
+ * the method (Section 5, Lemma "closecosts").
  */
 size_t gfe_mad_workspace(int32_t p, int64_t m, int64_t n, int64_t k);
 gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k,
@@ -210,18 +252,48 @@ gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k,
                    uint32_t flags, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * gfe_mad_gf2 -- the job MAD (Section 4.1) over GF(2) on bit-packed rows:
+ * C := W + A B, A m x k, B k x n, W and C m x n, rows of 64-bit words
+ * (GFE_BITS64 layout: bit c % 64 of word c / 64 is column c), pitches in
+ * bytes (multiples of 8).  W may be NULL (C := A B) and may equal C.  Pad
+ * bits of the inputs are ignored; those of C are written 0.  The kernel is
+ * the Method of the Four Russians: tables of all 256 combinations of 8 rows
+ * of B in shared memory, one table entry per row of A and 8 bits of k.
+ * Asynchronous on `stream`; allocates nothing.  Products with few output
+ * tiles split k over thread blocks that XOR into C atomically.
+ *
+ * gfe_gf2_peaks -- measures the two rates that bound that kernel on this
+ * GPU: LOP3 instructions per second (one LOP3 computes (a AND b) XOR c on 32
+ * bits, i.e. 32 GF(2) multiply-adds) and bytes per second of conflict-free
+ * 128-bit shared-memory loads.  Synchronises `stream`.
+ */
+gfe_status gfe_mad_gf2(int64_t m, int64_t n, int64_t k, const uint64_t *W, int64_t ldw,
+                       const uint64_t *A, int64_t lda, const uint64_t *B, int64_t ldb,
+                       uint64_t *C, int64_t ldc, void *stream);
+gfe_status gfe_gf2_peaks(double *lop3_per_s, double *lds_bytes_per_s, void *stream);
+
+/*
  * gfe_mad_noalloc -- the same multiply-add as gfe_mad, C := W + A B over
- * GF(p) on GFE_U8 residues, for callers that must not allocate device memory
- * (a fixed device-memory budget owned by the caller, or a path where
- * cudaMalloc / cudaFree could block or synchronise the device).  The paper
- * has no counterpart; this is an interface convenience of this library.
+ * GF(p) on GFE_U8 residues, for callers that cannot allocate device memory:
+ * a caller that owns a fixed device-memory budget and does not let libraries
+ * grow it, or one on a latency-critical path, where cudaMalloc / cudaFree
+ * may block or synchronise the device.  The paper has no counterpart; this
+ * is an interface convenience of this library.
  * Needs no workspace: its scratch is a library-owned device array of
- * gfe_mad_noalloc_max_bytes() bytes (32 MiB) that every GPU loading the
- * library holds until exit.  A product whose scratch (gfe_mad_workspace())
- * would exceed it is rejected with GFE_EINVAL.  The first call on each device
- * (with that device current) looks up the array's device address -- make it
- * before any stream capture.  All calls on a device share the array: calls
- * whose work overlaps on the GPU race and must be ordered by the caller.
+ * gfe_mad_noalloc_max_bytes() bytes (32 MiB).  A product whose scratch
+ * (gfe_mad_workspace()) would exceed it is rejected with GFE_EINVAL; so is a
+ * p that is not a prime <= 251, checked first, as in gfe_mad.
+ * First call on a device: the CUDA runtime loads the library's device code
+ * lazily, so the first call on each device (with that device current) loads
+ * it, reserves the 32 MiB array, and looks up the array's device address;
+ * that call can therefore fail with GFE_ECUDA when the device is full.  Make
+ * it once as a warm-up, before any stream capture; from then on the device
+ * holds the array until the process exits and no call allocates.
+ * All calls on a device share the array and it keeps the last call's
+ * contents (every element a call reads it first writes; the status word is
+ * zeroed by each call).  Calls whose work overlaps on the GPU race on it and
+ * must be ordered by the caller.  Like gfe_mad, the call returns once the
+ * product is complete on `stream`.
  */
 size_t gfe_mad_noalloc_max_bytes(void);
 gfe_status gfe_mad_noalloc(int32_t p, int64_t m, int64_t n, int64_t k,

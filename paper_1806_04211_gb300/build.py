@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgfe.so")
 SOURCES = ["gfe_kernels.cu", "gfe_mma.cu", "gfe_chief.cu", "gfe_api.cu", "gfe_server.cu", "gfe_noalloc.cu",
-           "gfe_small.cu"]
+           "gfe_small.cu", "gfe_solve.cu", "gfe_gf2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -190,6 +190,8 @@ static bool is_prime(int p) {
     return true;
 }
 
+bool field_ok(int p) { return is_prime(p) && p <= 251; }
+
 static gfe_status check_matrix(const gfe_matrix *A) {
     if (!A) return (set_error("matrix argument is NULL"), GFE_EINVAL);
     if (!is_prime(A->p) || A->p > 251) return (set_error("p must be a prime <= 251"), GFE_EINVAL);
@@ -211,7 +213,7 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 static int64_t ld64(int64_t x) { return x > 0 ? (x + 63) / 64 * 64 : 64; }
 
 struct Layout {
-    size_t H, Mo, Ko, Ro, maps, arena, total;
+    size_t H, Mo, Ko, Ro, maps, err, arena, total;
 };
 
 static Layout layout(const gfe_matrix *A, bool trafo, bool wantR) {
@@ -229,6 +231,8 @@ static Layout layout(const gfe_matrix *A, bool trafo, bool wantR) {
     off += wantR ? al256((size_t)std::max<int64_t>(mn, 1) * ld64(n) * es) : 256;
     Lo.maps = off;
     off += al256((size_t)(m + n + 2) * 4);
+    Lo.err = off;  // the call's error word
+    off += 256;
     Lo.arena = off;
     Lo.total = off;
     return Lo;
@@ -283,7 +287,7 @@ static gfe_status query(const gfe_matrix *A, bool trafo, bool wantR, size_t *ws)
 
 static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_dev, int64_t *pcols,
                       int64_t *prows, uint32_t flags, bool trafo, bool wantR, void *ws, size_t ws_bytes,
-                      void *stream, bool check_tc = true) {
+                      void *stream) {
     gfe_status st = check_matrix(A);
     if (st) return st;
     size_t need = 0;
@@ -300,6 +304,10 @@ static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_
     launch_for(A, flags, stream, L);
     Layout Lo = layout(A, trafo, wantR);
     char *base = (char *)ws;
+    // this call's error word, in its own workspace: concurrent calls (the
+    // batch's workers, the server's) never read one another's
+    L.err = (int *)(base + Lo.err);
+    if (!cuda_ok(cudaMemsetAsync(L.err, 0, sizeof(int), L.st), "error word")) return GFE_ECUDA;
     const int64_t m = A->m, n = A->n, mn = std::min(m, n);
     DMat H;
     H.ptr = base + Lo.H;
@@ -383,7 +391,10 @@ static gfe_status run(const gfe_matrix *A, const gfe_result *out, int64_t *rank_
         (void)es;
         if (!cuda_ok(host_wait(L.st), "final sync")) return GFE_ECUDA;
         if (!cuda_ok(cudaGetLastError(), "kernel launch")) return GFE_ECUDA;
-        if (check_tc && tc_error_flag(true)) {
+        int gave_up = 0;
+        if (!cuda_ok(read_error_word(L.st, L.err, &gave_up) ? cudaSuccess : cudaErrorUnknown, "error word read"))
+            return GFE_ECUDA;
+        if (gave_up) {
             set_error("a tensor-core multiply-add timed out waiting on its pipeline");
             return GFE_ETIMEOUT;
         }
@@ -666,7 +677,7 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
                 if (q >= nrest) break;
                 const int32_t i = P.rest[q];
                 mine = run(&As[i], &outs[i], outs[i].rank, outs[i].pivot_cols, outs[i].pivot_rows, flags, trafo,
-                           true, (char *)ws + slice * w, slice, s, false);
+                           true, (char *)ws + slice * w, slice, s);
             }
             if (mine != GFE_OK) {
                 std::lock_guard<std::mutex> g(mu);
@@ -702,10 +713,6 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
         set_error(first_msg);
         return first;
     }
-    if (tc_error_flag(true)) {
-        set_error("a tensor-core multiply-add timed out waiting on its pipeline");
-        return GFE_ETIMEOUT;
-    }
     return GFE_OK;
 }
 
@@ -720,6 +727,7 @@ gfe_status gfe_set_batch_workers(int32_t workers) {
     return GFE_OK;
 }
 
+// operands A, B and C in the codec, then 256 bytes for the call's error word
 size_t gfe_mad_workspace(int32_t p, int64_t m, int64_t n, int64_t k) {
     int es = codec_bytes(codec_for(p < 2 ? 2 : p));
     return al256((size_t)m * ld64(k) * es) + al256((size_t)k * ld64(n) * es) + al256((size_t)m * ld64(n) * es) + 256;
@@ -742,6 +750,8 @@ gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k, const uint8_t *W,
     const int es = codec_bytes(L.codec);
     const int64_t lk = ld64(k), ln = ld64(n);
     char *a = (char *)ws, *b = a + al256((size_t)m * lk * es), *c = b + al256((size_t)k * ln * es);
+    L.err = (int *)(c + al256((size_t)m * ln * es));
+    if (!cuda_ok(cudaMemsetAsync(L.err, 0, sizeof(int), L.st), "error word")) return GFE_ECUDA;
     if (k > 0) {
         import_u8(L, m, k, a, lk, A, lda);
         import_u8(L, k, n, b, ln, B, ldb);
@@ -749,8 +759,12 @@ gfe_status gfe_mad(int32_t p, int64_t m, int64_t n, int64_t k, const uint8_t *W,
     if (W) import_u8(L, m, n, c, ln, W, ldw);
     mad(L, m, n, k, W ? c : nullptr, ln, a, lk, b, ln, c, ln);
     export_u8(L, m, n, C, ldc, c, ln);
-    if (tc_error_flag(true)) return (set_error("tensor-core multiply-add timed out"), GFE_ETIMEOUT);
     if (!cuda_ok(cudaGetLastError(), "kernel launch")) return GFE_ECUDA;
+    // the call returns once the product is complete on `stream`: the read of
+    // its error word is a copy on that stream
+    int gave_up = 0;
+    if (!read_error_word(L.st, L.err, &gave_up)) return (set_error("error word read failed"), GFE_ECUDA);
+    if (gave_up) return (set_error("tensor-core multiply-add timed out"), GFE_ETIMEOUT);
     return GFE_OK;
 }
 
@@ -779,7 +793,6 @@ gfe_status gfe_set_leaf_rows(int64_t rows) {
 gfe_status gfe_selftest_wait_timeout(int64_t limit_us, void *stream) {
     if (limit_us < 1 || limit_us > 10000000) return (set_error("limit_us out of range"), GFE_EINVAL);
     const int gave_up = wait_selftest((cudaStream_t)stream, limit_us);
-    tc_error_flag(true);  // the self-test's error word is not a real failure
     if (gave_up < 0) return (set_error("self-test could not run"), GFE_ECUDA);
     if (!cuda_ok(cudaGetLastError(), "self-test launch")) return GFE_ECUDA;
     if (gave_up == 1) return (set_error("bounded wait gave up as designed"), GFE_ETIMEOUT);

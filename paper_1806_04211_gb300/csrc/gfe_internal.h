@@ -41,6 +41,10 @@ struct Launch {  // per-call launch context
     // CTAs that none takes more than k tiles, so SMs come free for other
     // (higher-priority) streams every few tiles
     int tiles_per_cta = 0;
+    // the call's error word (device memory, zeroed by the call): a bounded
+    // wait of the tensor-core multiply-add that gives up sets it to 1.  Each
+    // call owns its word, so concurrent calls never see one another's errors.
+    int *err = nullptr;
 };
 
 // ---- profiling (gfe_api.cu) ----
@@ -66,10 +70,13 @@ void mad_plain(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, 
 bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_t ldw,
             const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc);
 
-// error word of the tensor-core kernel (a bounded wait ran out); read + reset
-int tc_error_flag(bool reset);
 int64_t tc_k_chunk(int p);
+// runs the bounded-wait self-test on st (with an error word of its own);
+// returns 1 if the wait gave up, 0 if it completed, -1 on a CUDA error
 int wait_selftest(cudaStream_t st, int64_t limit_us);
+// reads a call's error word on stream st (after all work queued on st) into
+// *value; the copy to pageable host memory returns once it is complete
+bool read_error_word(cudaStream_t st, const int *err, int *value);
 
 // Leaf echelonisation of H (alpha <= ECH_LEAF_ROWS, beta <= ech_leaf_cols(p)).
 // info[0] = r, info[1..] = rho (r), info[1+cap..] = gamma (r), cap = ech_leaf_cols(p).
@@ -181,8 +188,9 @@ cudaError_t host_wait(cudaStream_t s);
 int64_t auto_leaf_rows(int p, int64_t m, int64_t n);
 int64_t auto_block(int p, int64_t m, int64_t n);
 
-// ---- error state (gfe_api.cu) ----
+// ---- error state and argument checks (gfe_api.cu) ----
 void set_error(const std::string &s);
+bool field_ok(int p);  // p is a prime <= 251
 bool cuda_ok(cudaError_t e, const char *what);
 
 }  // namespace gfe

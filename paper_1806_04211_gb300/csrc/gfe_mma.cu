@@ -436,38 +436,31 @@ __global__ void k_wait_selftest(uint64_t limit_ns, int *err, int *gave_up) {
 }
 
 // ---- host side ----
-// error word of the kernel: one per device (a module-scope device variable,
-// zero at load); its device address is looked up once per device
-__device__ int g_tc_err;
-
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_once;
 std::mutex g_dev_mu;
 constexpr int MAX_DEV = 64;
-int *g_err_dev[MAX_DEV] = {};
 bool g_attr_dev[MAX_DEV] = {};
 
 int g_num_sms = 148;
 
-// per-device set-up with the device current; returns the error word
-int *dev_setup() {
+// per-device set-up with the device current (the kernels' shared-memory
+// attribute, the SM count); false on a CUDA error
+bool dev_setup() {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return nullptr;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return false;
     std::lock_guard<std::mutex> g(g_dev_mu);
     if (!g_attr_dev[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_tc_err) != cudaSuccess) return nullptr;
         if (cudaFuncSetAttribute(k_mad_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(k_mad_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess)
-            return nullptr;
-        g_err_dev[dev] = (int *)p;
+            return false;
         g_attr_dev[dev] = true;
         int nsm = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
             g_num_sms = nsm;
     }
-    return g_err_dev[dev];
+    return true;
 }
 
 bool init_tc() {
@@ -514,9 +507,10 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
     const int es = f8 ? 1 : 2;
     if (!al16(A) || !al16(B) || (lda * es) % 16 || (ldb * es) % 16) return false;
     if (m > (1 << 30) || n > (1 << 30) || ((m + TBM - 1) / TBM) * ((n + TBN - 1) / TBN) > INT32_MAX) return false;
-    if (!init_tc()) return false;
-    int *err = dev_setup();
-    if (!err) return false;
+    // every call passes its own error word; without one the bounded waits
+    // could report nowhere, so the shape goes to the CUDA-core path
+    int *err = L.err;
+    if (!err || !init_tc() || !dev_setup()) return false;
     const int64_t kc = tc_k_chunk(L.p);
     for (int64_t k0 = 0; k0 < k; k0 += kc) {
         const int64_t kk = k - k0 < kc ? k - k0 : kc;
@@ -551,33 +545,31 @@ bool mad_tc(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int
     return true;
 }
 
-int tc_error_flag(bool reset) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return 0;
-    int *e = nullptr;
-    {
-        std::lock_guard<std::mutex> g(g_dev_mu);
-        e = g_err_dev[dev];
-    }
-    if (!e) return 0;
-    int h = 0;
-    cudaMemcpy(&h, e, sizeof(int), cudaMemcpyDeviceToHost);
-    if (reset && h) cudaMemset(e, 0, sizeof(int));
-    return h;
+bool read_error_word(cudaStream_t st, const int *err, int *value) {
+    *value = 0;
+    if (!err) return true;
+    // pageable destination: the copy is ordered after the work on st and
+    // returns once it is complete
+    return cudaMemcpyAsync(value, err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+           host_wait(st) == cudaSuccess;
 }
 
 }  // namespace gfe
 
 namespace gfe {
-// launches the self-test on `st`; returns the device flag set by the wait
+// launches the self-test on `st` with an error word of its own; returns the
+// flag the wait sets when it gives up (or -1 on a CUDA error)
 int wait_selftest(cudaStream_t st, int64_t limit_us) {
-    int *d = nullptr, h = 0;
+    int *d = nullptr, h = 0;  // d[0] error word, d[1] gave-up flag
     if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return -1;
-    cudaMemsetAsync(d, 0, 2 * sizeof(int), st);
+    if (cudaMemsetAsync(d, 0, 2 * sizeof(int), st) != cudaSuccess) {
+        cudaFree(d);
+        return -1;
+    }
     k_wait_selftest<<<1, 32, 0, st>>>((uint64_t)limit_us * 1000ull, d, d + 1);
-    cudaMemcpyAsync(&h, d + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
+    const bool ok = cudaMemcpyAsync(&h, d + 1, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                    cudaStreamSynchronize(st) == cudaSuccess;
     cudaFree(d);
-    return h;
+    return ok ? h : -1;
 }
 }  // namespace gfe

@@ -1,5 +1,5 @@
 // gfe_mad_noalloc: the block multiply-add C := W + A B over GF(p) (the same
-// computation as gfe_mad) for callers that must not allocate device memory.
+// computation as gfe_mad) for callers that cannot allocate device memory.
 //
 // Who needs it: code that runs where a device allocation is not allowed or
 // not wanted -- a caller that owns a fixed device-memory budget and forbids
@@ -9,17 +9,23 @@
 // uses a scratch array that lives in the library's own device image.
 //
 // The scratch is a file-scope __device__ array of NOALLOC_SCRATCH_BYTES
-// (32 MiB).  Every GPU that loads the library holds it until the process
-// exits.  Host code may not use the array's name as a device address (it is
-// a host-side stand-in), so the first call on each device, with that device
-// current, looks the address up with cudaGetSymbolAddress and keeps it; make
-// that first call on a device before any stream capture.
+// (32 MiB).  The CUDA runtime loads a module's device code lazily, so the
+// array is created on a device by the first call there (the one that looks
+// up its address), not when the library is loaded: that first call reserves
+// the 32 MiB and may fail if the device is full, which is why callers should
+// make it once as a warm-up.  From then on the device holds the array until
+// the process exits.  Host code may not use the array's name as a device
+// address (it is a host-side stand-in), so the first call on each device,
+// with that device current, looks the address up with cudaGetSymbolAddress
+// and keeps it; make that first call on a device before any stream capture.
 //
 // All calls on a device share the one array and it keeps the last call's
-// contents.  Nothing in it has to start at zero: every scratch element the
-// multiply-add reads is written earlier in the same call.  Calls whose work
-// overlaps on the GPU (for example issued on two streams without ordering)
-// race on the array and give wrong results; order them.
+// contents.  The only element that must start at zero is the call's status
+// word (the last 256 bytes of its scratch), which gfe_mad zeroes on the
+// stream before the product; every other scratch element the multiply-add
+// reads is written earlier in the same call.  Calls whose work overlaps on
+// the GPU (for example issued on two streams without ordering) race on the
+// array and give wrong results; order them.
 #include "gfe.h"
 #include "gfe_internal.h"
 
@@ -60,6 +66,7 @@ extern "C" size_t gfe_mad_noalloc_max_bytes(void) { return NOALLOC_SCRATCH_BYTES
 extern "C" gfe_status gfe_mad_noalloc(int32_t p, int64_t m, int64_t n, int64_t k, const uint8_t *W, int64_t ldw,
                                       const uint8_t *A, int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C,
                                       int64_t ldc, uint32_t flags, void *stream) {
+    if (!field_ok(p)) return (set_error("p must be a prime <= 251"), GFE_EINVAL);
     if (m < 0 || n < 0 || k < 0) return (set_error("negative size"), GFE_EINVAL);
     if (m == 0 || n == 0) return GFE_OK;
     const size_t need = gfe_mad_workspace(p, m, n, k);

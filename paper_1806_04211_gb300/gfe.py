@@ -78,6 +78,12 @@ SIGNATURES = {
     "gfe_mad_noalloc_max_bytes": (ctypes.c_size_t, []),
     "gfe_mad_noalloc": (_i32, [_i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_uint32,
                                _vp]),
+    "gfe_nullspace": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), _i32, _vp, _i64, _vp]),
+    "gfe_solve_workspace": (ctypes.c_size_t, [ctypes.POINTER(GfeMatrix), _i64]),
+    "gfe_solve": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), _vp, _i64, _i64, _vp, _i64, _vp, _vp,
+                         ctypes.c_size_t, _vp]),
+    "gfe_mad_gf2": (_i32, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
+    "gfe_gf2_peaks": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp]),
     "gfe_set_block_policy": (_i32, [_i64, _i64]),
     "gfe_auto_block": (_i64, [_i32, _i64, _i64]),
     "gfe_set_leaf_rows": (_i32, [_i64]),
@@ -156,6 +162,11 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
         t = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
         _ws_cache[key] = t
     return t
+
+
+def release_workspace() -> None:
+    """Drop the cached workspace tensors (the next call allocates afresh)."""
+    _ws_cache.clear()
 
 
 def query_workspace(A: torch.Tensor, p: int, n: int | None = None, flags: int = WANT_TRANSFORM) -> int:
@@ -406,6 +417,78 @@ def rank(A: torch.Tensor, p: int, n: int | None = None, impl: str = "tensor", st
     return dict(rank=r, ups=pc[:r], rho=pr[:r])
 
 
+def _result_struct(res, dev, bits: bool):
+    """A gfe_result of device pointers for an echelon() / batch_echelon()
+    result mapping (the rank goes to the device as an int64 scalar)."""
+    es = 8 if bits else 1
+    rk = torch.tensor([int(res["rank"])], dtype=torch.int64, device=dev)
+
+    def p_ld(key):
+        t = res[key] if key in res else None
+        # the result tensors are views of buffers of at least one row: their
+        # address is valid even when the view is empty
+        return (None, 0) if t is None else (t.data_ptr(), t.stride(0) * es)
+
+    R, ldR = p_ld("R")
+    M, ldM = p_ld("M")
+    K, ldK = p_ld("K")
+    ups = res["ups"]
+    rho = res["rho"]
+    keep = (rk, ups, rho)
+    st = GfeResult(rk.data_ptr(), ups.data_ptr(), rho.data_ptr(), R, ldR, M, ldM, K, ldK, None, 0, None, 0)
+    return st, keep
+
+
+def _shape_arg(p: int, m: int, n: int, bits: bool) -> GfeMatrix:
+    return GfeMatrix(p, m, n, GFE_BITS64 if bits else GFE_U8, None, 8 * words_per_row(max(n, 1)) if bits else max(n, 1))
+
+
+def nullspace(res, p: int, m: int, n: int, side: str = "right", bits: bool | None = None, stream=None) -> torch.Tensor:
+    """gfe_nullspace: basis of the left ({y : y A = 0}, rows of (K 1) P_rho)
+    or right ({x : A x = 0}) null space of the matrix `res` was computed for,
+    one basis vector per row, in A's storage (uint8, or GF(2) words)."""
+    r = int(res["rank"])
+    dev = res["ups"].device
+    bits = (p == 2 and res["R"].dtype == torch.int64) if bits is None else bits
+    length = m if side == "left" else n
+    rows = length - r
+    if bits:
+        N = torch.zeros((max(length, 1), words_per_row(max(length, 1))), dtype=torch.int64, device=dev)
+    else:
+        N = torch.zeros((max(length, 1), max(length, 1)), dtype=torch.uint8, device=dev)
+    st, keep = _result_struct(res, dev, bits)
+    mat = _shape_arg(p, m, n, bits)
+    _check(lib().gfe_nullspace(ctypes.byref(mat), ctypes.byref(st), 0 if side == "left" else 1, N.data_ptr(),
+                               N.stride(0) * (8 if bits else 1), _stream(stream)))
+    if bits:
+        return N[:rows, :words_per_row(length)] if rows else N[:0]
+    return N[:rows, :length]
+
+
+def solve(res, p: int, m: int, n: int, B: torch.Tensor, k: int | None = None, stream=None):
+    """gfe_solve: X (n x k) with A X = B where consistent, and the int32
+    consistency flag per column.  B is m x k uint8, or for GF(2) bit rows
+    (int64 words, k given)."""
+    dev = B.device
+    bits = B.dtype == torch.int64
+    if k is None:
+        k = B.shape[1]
+    if bits:
+        X = torch.zeros((max(n, 1), words_per_row(max(k, 1))), dtype=torch.int64, device=dev)
+    else:
+        X = torch.zeros((max(n, 1), max(k, 1)), dtype=torch.uint8, device=dev)
+    ok = torch.zeros(max(k, 1), dtype=torch.int32, device=dev)
+    st, keep = _result_struct(res, dev, bits)
+    mat = _shape_arg(p, m, n, bits)
+    need = lib().gfe_solve_workspace(ctypes.byref(mat), k)
+    ws = _workspace(need, dev)
+    es = 8 if bits else 1
+    _check(lib().gfe_solve(ctypes.byref(mat), ctypes.byref(st), B.data_ptr() if B.numel() else None,
+                           B.stride(0) * es if B.numel() else 0, k, X.data_ptr(), X.stride(0) * es, ok.data_ptr(),
+                           ws.data_ptr(), ws.numel(), _stream(stream)))
+    return X[:n], ok[:k]
+
+
 def mad(W, A: torch.Tensor, B: torch.Tensor, p: int, impl: str = "tensor", out=None, stream=None) -> torch.Tensor:
     """C := W + A B over GF(p) on uint8 residues (gfe_mad); W may be None."""
     m, k = A.shape
@@ -417,6 +500,23 @@ def mad(W, A: torch.Tensor, B: torch.Tensor, p: int, impl: str = "tensor", out=N
                          B.stride(0), C.data_ptr(), C.stride(0), _impl_flag(impl), ws.data_ptr(), ws.numel(),
                          _stream(stream)))
     return C
+
+
+def mad_gf2(W, A: torch.Tensor, B: torch.Tensor, n: int, k: int, out=None, stream=None) -> torch.Tensor:
+    """gfe_mad_gf2: C := W + A B over GF(2) on bit-packed int64 rows (A m x k
+    bits, B k x n bits, W and C m x n bits); W may be None or `out`."""
+    m = A.shape[0]
+    C = out if out is not None else torch.empty((m, words_per_row(max(n, 1))), dtype=torch.int64, device=A.device)
+    _check(lib().gfe_mad_gf2(m, n, k, _ptr(W), 8 * W.stride(0) if W is not None else 0, _ptr(A), 8 * A.stride(0),
+                             _ptr(B), 8 * B.stride(0), C.data_ptr(), 8 * C.stride(0), _stream(stream)))
+    return C
+
+
+def gf2_peaks(stream=None) -> dict:
+    """gfe_gf2_peaks: measured LOP3 rate and 128-bit shared-memory load rate."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().gfe_gf2_peaks(ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+    return {"lop3_per_s": a.value, "lds_bytes_per_s": b.value, "gf2_madds_per_s_alu": 32.0 * a.value}
 
 
 def mad_noalloc(W, A: torch.Tensor, B: torch.Tensor, p: int, out: torch.Tensor, impl: str = "tensor", stream=None):

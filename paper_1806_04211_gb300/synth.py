@@ -116,22 +116,34 @@ def mask_pad_gf2(wd: torch.Tensor, n: int) -> torch.Tensor:
 
 
 def unpack_gf2(wd: torch.Tensor, n: int) -> torch.Tensor:
-    """bit-packed words (m x ldw int64) -> m x n uint8 of 0/1."""
+    """bit-packed words (m x ldw int64) -> m x n uint8 of 0/1 (rows in
+    chunks, so the int64 temporaries stay near 1 GB)."""
     m, ldw = wd.shape
+    out = torch.empty((m, n), dtype=torch.uint8, device=wd.device)
     sh = torch.arange(64, dtype=torch.int64, device=wd.device)
-    bits = ((wd.unsqueeze(-1) >> sh) & 1).to(torch.uint8).view(m, ldw * 64)
-    return bits[:, :n].contiguous()
+    step = max(1, (1 << 27) // (ldw * 64))
+    for r0 in range(0, m, step):
+        r1 = min(m, r0 + step)
+        bits = ((wd[r0:r1].unsqueeze(-1) >> sh) & 1).to(torch.uint8).view(r1 - r0, ldw * 64)
+        out[r0:r1] = bits[:, :n]
+    return out
 
 
 def pack_gf2(bits: torch.Tensor, ldw: int | None = None) -> torch.Tensor:
-    """m x n uint8 of 0/1 -> m x ldw int64 words (bit c%64 of word c/64)."""
+    """m x n uint8 of 0/1 -> m x ldw int64 words (bit c%64 of word c/64).
+    Rows are packed in chunks so the int64 temporaries stay near 1 GB."""
     m, n = bits.shape
     if ldw is None:
         ldw = gf2_words_per_row(n)
-    pad = torch.zeros((m, ldw * 64), dtype=torch.int64, device=bits.device)
-    pad[:, :n] = bits.to(torch.int64)
+    out = torch.empty((m, ldw), dtype=torch.int64, device=bits.device)
     sh = torch.arange(64, dtype=torch.int64, device=bits.device)
-    return (pad.view(m, ldw, 64) << sh).sum(-1)
+    step = max(1, (1 << 27) // (ldw * 64))
+    for r0 in range(0, m, step):
+        r1 = min(m, r0 + step)
+        pad = torch.zeros((r1 - r0, ldw * 64), dtype=torch.int64, device=bits.device)
+        pad[:, :n] = bits[r0:r1].to(torch.int64)
+        out[r0:r1] = (pad.view(r1 - r0, ldw, 64) << sh).sum(-1)
+    return out
 
 
 def matmul_mod(U: torch.Tensor, V: torch.Tensor, p: int) -> torch.Tensor:
@@ -139,24 +151,31 @@ def matmul_mod(U: torch.Tensor, V: torch.Tensor, p: int) -> torch.Tensor:
 
     float32 products of chunks of the inner dimension short enough that every
     partial sum stays below 2^24 (so every float32 value is an exact integer),
-    reduced mod p after each chunk."""
+    reduced mod p after each chunk.  Rows of U go in blocks, so the float32
+    temporaries stay near 1 GB beside V's float32 copy."""
     m, k = U.shape
     n = V.shape[1]
     chunk = max(1, ((1 << 24) - 1) // max((p - 1) * (p - 1), 1))
-    acc = torch.zeros((m, n), dtype=torch.int32, device=U.device)
+    out = torch.empty((m, n), dtype=torch.uint8, device=U.device)
+    rows = max(1, (1 << 28) // max(n, k, 1))
     old = None
     if U.is_cuda:
         old = torch.backends.cuda.matmul.allow_tf32
         torch.backends.cuda.matmul.allow_tf32 = False
     try:
-        for k0 in range(0, k, chunk):
+        for k0 in range(0, max(k, 1), chunk):
             k1 = min(k, k0 + chunk)
-            prod = U[:, k0:k1].to(torch.float32) @ V[k0:k1].to(torch.float32)
-            acc = (acc + prod.to(torch.int32)) % p
+            Vf = V[k0:k1].to(torch.float32)
+            for r0 in range(0, m, rows):
+                r1 = min(m, r0 + rows)
+                prod = U[r0:r1, k0:k1].to(torch.float32) @ Vf
+                acc = prod.to(torch.int32) if k0 == 0 else out[r0:r1].to(torch.int32) + prod.to(torch.int32)
+                out[r0:r1] = (acc % p).to(torch.uint8)
+            del Vf
     finally:
         if old is not None:
             torch.backends.cuda.matmul.allow_tf32 = old
-    return acc.to(torch.uint8)
+    return out
 
 
 def lowrank_u8(m: int, n: int, k: int, p: int, seed: int, device="cpu") -> torch.Tensor:
@@ -184,3 +203,43 @@ def matrix(p: int, m: int, n: int, seed: int, rank: int | None = None, device="c
     if rank is None:
         return uniform_u8(m, n, p, seed, 0, device)
     return lowrank_u8(m, n, rank, p, seed, device)
+
+
+PRIMES = [q for q in range(2, 252) if all(q % d for d in range(2, int(q ** 0.5) + 1))]
+
+
+def c4_specs(count: int, seed: int = 1) -> list:
+    """The batched workload's draw: (p, m, n, rank or None) per matrix, m and
+    n log-uniform in [64, 2048] with aspect ratio <= 4 (resampled), p uniform
+    in {2, 3, 5, 7}, every second matrix of rank 0.6 min(m, n).  Matrix i is
+    drawn with matrix(p, m, n, seed=5000 + i, rank=rank)."""
+    import numpy as np
+    rng = np.random.RandomState(seed)
+    out = []
+    while len(out) < count:
+        m, n = (int(round(64 * 32 ** rng.rand())) for _ in range(2))
+        if max(m, n) > 4 * min(m, n):
+            continue
+        p = [2, 3, 5, 7][rng.randint(4)]
+        rk = int(0.6 * min(m, n)) if len(out) % 2 else None
+        out.append((p, m, n, rk))
+    return out
+
+
+def c5_specs(count: int, seed: int = 1) -> list:
+    """The served workload's draw: (p, n, rank or None) per request, square n
+    ~ Pareto(1.5) on [256, 16384] (rejection), p uniform over the primes
+    <= 251, 30% of rank 0.6 n.  Request i is drawn with
+    matrix(p, n, n, seed=7000 + i, rank=rank)."""
+    import numpy as np
+    rng = np.random.RandomState(seed)
+    out = []
+    while len(out) < count:
+        n = 256 * (1 - rng.rand()) ** (-1 / 1.5)
+        if n > 16384:
+            continue
+        n = int(n)
+        p = PRIMES[rng.randint(len(PRIMES))]
+        rk = int(0.6 * n) if rng.rand() < 0.3 else None
+        out.append((p, n, rk))
+    return out

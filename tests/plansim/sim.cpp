@@ -104,6 +104,10 @@ cudaError_t cudaMemcpyAsync(void* d, const void* s, size_t n, cudaMemcpyKind k, 
     if (k != cudaMemcpyHostToDevice) chk(s, n, "memcpy src");
     if (k != cudaMemcpyDeviceToHost) chk(d, n, "memcpy dst", true);
     memcpy(d, s, n); race::cur = -1; return cudaSuccess; }
+cudaError_t cudaMemsetAsync(void* d, int v, size_t n, cudaStream_t st) {
+    race::op_begin(st, "memset");
+    chk(d, n, "memset dst", true);
+    memset(d, v, n); race::cur = -1; return cudaSuccess; }
 cudaError_t cudaHostAlloc(void** p, size_t n, unsigned int) { *p = malloc(n); std::lock_guard<std::mutex> g(g_rmu); g_regions.push_back({(const char*)*p, n}); return cudaSuccess; }
 cudaError_t cudaEventCreate(cudaEvent_t* e) { std::lock_guard<std::mutex> g(race::mu); *e = (cudaEvent_t)(g_handle++); return cudaSuccess; }
 cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t s) { std::lock_guard<std::mutex> g(race::mu); int i = race::id_of((uintptr_t)s); race::svc[i].join(race::host); race::evs[(uintptr_t)e] = race::svc[i]; return cudaSuccess; }
@@ -152,7 +156,13 @@ void mad(const Launch& L, int64_t m, int64_t n, int64_t k, const void* W, int64_
     if (m <= 0 || n <= 0) return;
     mad_plain(L, m, n, k, W, ldw, A, lda, B, ldb, C, ldc);
 }
-int tc_error_flag(bool) { return 0; }
+bool read_error_word(cudaStream_t st, const int* err, int* value) {
+    *value = 0;
+    if (!err) return true;
+    cudaMemcpyAsync(value, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    return true;
+}
 int wait_selftest(cudaStream_t, int64_t) { return 1; }
 int64_t tc_k_chunk(int) { return 1 << 20; }
 int ech_leaf_cols(int p) { return p == 2 ? ECH_LEAF_COLS_GF2 : ECH_LEAF_COLS; }

@@ -1,0 +1,132 @@
+"""The stated configurations at their full sizes, in the launch configuration
+the benchmark uses (GPU).
+
+* C2 GF(2) n = 8192, uniform and rank-6144 twin: element-wise against the
+  oracle.
+* The 6144-wide block policy the planner takes for GF(2) inputs with
+  max(m, n) >= 65536, on inputs the oracle still finishes: element-wise.
+* C2 GF(2) n = 100000, uniform and rank-75000 twin (the policy above),
+  through the batched entry point with two workers as in the benchmark:
+  the oracle's certificate (exact structure checks plus Freivalds' check of
+  T A = E, Eq. (echelon) of Section 3.1; the oracle itself is too slow here).
+* C3 GF(7) 32768^2 rank-19660 twin and GF(251) 20000 x 50000 uniform:
+  certificate.
+* C4, the full seeded draw of 4096 matrices through one batched call:
+  certificate for every matrix, element-wise oracle parity on a seeded
+  subset.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1806_04211_gb300 import gfe, synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def host(d):
+    return {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in d.items()}
+
+
+def gf2_host(d):
+    res = host(d)
+    for k in ("M", "K", "R"):
+        res[k] = np.ascontiguousarray(res[k]).view(np.uint64)
+    return res
+
+
+def compare_gf2(got, ref, m, n):
+    assert got["rank"] == ref["rank"]
+    r = ref["rank"]
+    for k in ("rho", "ups"):
+        assert np.array_equal(got[k].cpu().numpy(), ref[k]), k
+    for k, cols in (("R", n - r), ("M", r), ("K", r)):
+        g = O.unpack_bits(got[k].cpu().numpy(), cols) if got[k].numel() else np.zeros((0, cols), np.uint8)
+        e = O.unpack_bits(ref[k], cols) if ref[k].size else np.zeros((0, cols), np.uint8)
+        assert np.array_equal(g[:e.shape[0]], e), k
+
+
+@pytest.fixture(autouse=True)
+def _policy():
+    gfe.set_block_policy()
+    yield
+    gfe.set_block_policy()
+    torch.cuda.empty_cache()
+
+
+def test_c2_gf2_8192_vs_oracle():
+    n = 8192
+    mats = [synth.matrix(2, n, n, seed=1, rank=rk) for rk in (None, 6144)]
+    got = gfe.batch_echelon([(A.to(DEV), 2, n) for A in mats], workers=2)
+    for A, g in zip(mats, got):
+        compare_gf2(g, O.echelon_gf2(A.numpy(), n, n), n, n)
+    assert got[1]["rank"] == 6144
+
+
+@pytest.mark.parametrize("m,n,rank", [(7000, 13000, None), (13000, 7000, 5000)])
+def test_block_6144_policy_vs_oracle(m, n, rank):
+    """6144-square top-level blocks (the default above 65536), each ECH a
+    Chief over 1024 x 256 leaves, with ragged last blocks."""
+    gfe.set_block_policy(6144, 6144)
+    A = synth.matrix(2, m, n, seed=31, rank=rank)
+    ref = O.echelon_gf2(A.numpy(), m, n)
+    compare_gf2(gfe.echelon(A.to(DEV), 2, n=n), ref, m, n)
+
+
+def test_c2_gf2_100000_certificate():
+    n = 100000
+    assert gfe.lib().gfe_auto_block(2, n, n) == 6144
+    mats = [synth.matrix(2, n, n, seed=1, rank=rk, device=DEV) for rk in (None, 75000)]
+    got = gfe.batch_echelon([(A, 2, n) for A in mats], workers=2)
+    assert got[0]["rank"] >= n - 8
+    assert got[1]["rank"] == 75000
+    for A, g in zip(mats, got):
+        res = gf2_host(g)
+        assert O.certify_gf2(A.cpu().numpy(), n, n, res, seed=11) == 0
+    del mats, got
+
+
+def test_c3_gf7_32768_twin_certificate():
+    n, rk = 32768, int(0.6 * 32768)
+    A = synth.matrix(7, n, n, seed=11, rank=rk, device=DEV)
+    got = gfe.echelon(A, 7)
+    assert got["rank"] == rk
+    assert O.certify(A.cpu().numpy(), 7, host(got), nvec=4, seed=13) == 0
+
+
+def test_c3_gf251_rect_uniform_certificate():
+    m, n = 20000, 50000
+    A = synth.matrix(251, m, n, seed=11, device=DEV)
+    got = gfe.echelon(A, 251)
+    assert got["rank"] == m
+    assert O.certify(A.cpu().numpy(), 251, host(got), nvec=4, seed=17) == 0
+
+
+def test_c4_full_draw():
+    """All 4096 matrices of the seeded draw in one batched call (the one-launch
+    kernels plus the planner for the largest), as the benchmark runs it."""
+    specs = synth.c4_specs(4096)
+    mats = [synth.matrix(p, m, n, seed=5000 + i, rank=rk, device=DEV) for i, (p, m, n, rk) in enumerate(specs)]
+    got = gfe.batch_echelon([(A, p, n) for A, (p, m, n, rk) in zip(mats, specs)], workers=16)
+    rng = np.random.RandomState(4)
+    light = [i for i, (p, m, n, rk) in enumerate(specs) if p == 2 or m * n * min(m, n) <= 1e9]
+    subset = set(rng.choice(light, 40, replace=False).tolist())
+    for i, ((p, m, n, rk), A, g) in enumerate(zip(specs, mats, got)):
+        if rk is not None:
+            assert g["rank"] == rk, (i, p, m, n)
+        Ah = A.cpu().numpy()
+        if p == 2:
+            res = gf2_host(g)
+            assert O.certify_gf2(Ah, m, n, res, seed=i) == 0, (i, m, n)
+            if i in subset:
+                compare_gf2(g, O.echelon_gf2(Ah, m, n), m, n)
+        else:
+            res = host(g)
+            assert O.certify(Ah, p, res, nvec=2, seed=i) == 0, (i, p, m, n)
+            if i in subset:
+                ref = O.echelon(Ah, p)
+                assert res["rank"] == ref["rank"]
+                for k in ("rho", "ups", "R", "M", "K"):
+                    assert np.array_equal(res[k], ref[k]), (i, k)

@@ -1,4 +1,4 @@
-"""gfe_mad_noalloc, the multiply-add entry point for callers that must not
+"""gfe_mad_noalloc, the multiply-add entry point for callers that cannot
 allocate device memory (a fixed device budget owned by the caller, or a path
 where cudaMalloc / cudaFree could block or synchronise).  It is checked
 through the C ABI against gfe_mad, the entry point that takes a workspace,
@@ -45,11 +45,42 @@ def test_mad_noalloc_matches_mad_on_two_calls():
         assert np.array_equal(C.cpu().numpy(), exact % p)
 
 
+def test_mad_noalloc_second_call_allocates_nothing():
+    """The first call on a device loads the library's device code and with it
+    the 32 MiB array; a later call must leave free device memory unchanged,
+    on the default stream and on a non-blocking one."""
+    L = gfe.lib()
+    p, m, n, k = 5, 256, 384, 512
+    A = synth.uniform_u8(m, k, p, 30, 1).to(DEV)
+    B = synth.uniform_u8(k, n, p, 30, 2).to(DEV)
+    C = torch.empty((m, n), dtype=torch.uint8, device=DEV)
+    assert call_noalloc(L, p, None, A, B, C, torch.cuda.current_stream().cuda_stream) == 0, L.gfe_last_error()
+    torch.cuda.synchronize()
+    exact = (A.cpu().numpy().astype(np.int64) @ B.cpu().numpy().astype(np.int64)) % p
+    side = torch.cuda.Stream()  # non-blocking with respect to the legacy stream
+    free0 = torch.cuda.mem_get_info()[0]
+    for s in (torch.cuda.current_stream(), side):
+        C.fill_(255)
+        torch.cuda.synchronize()
+        assert call_noalloc(L, p, None, A, B, C, s.cuda_stream) == 0, L.gfe_last_error()
+        # the call returns once the product is complete on its stream
+        assert np.array_equal(C.cpu().numpy(), exact)
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_mad_noalloc_checks_p_first():
+    L = gfe.lib()
+    for p in (1, 4, 257):
+        assert L.gfe_mad_noalloc(p, 0, 0, 0, None, 0, None, 0, None, 0, None, 0, 0, None) == 1
+        assert b"prime" in L.gfe_last_error()
+
+
 def test_mad_noalloc_rejects_oversize():
     L = gfe.lib()
     cap = L.gfe_mad_noalloc_max_bytes()
     assert cap == 32 << 20
-    m = n = k = 4096  # 3 x 32 MiB of bf16 scratch: more than the array holds
+    m = n = k = 4096  # GF(3) is e4m3 inside: 3 x 16 MiB of scratch, more than the array holds
+    assert L.gfe_mad_workspace(3, m, n, k) > cap
     A = torch.zeros((m, k), dtype=torch.uint8, device=DEV)
     C = torch.zeros((m, n), dtype=torch.uint8, device=DEV)
     st = L.gfe_mad_noalloc(3, m, n, k, None, 0, A.data_ptr(), k, A.data_ptr(), n, C.data_ptr(), n, 0,
