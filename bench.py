@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--c4", type=int, default=4096, help="matrices of the batched leg")
     ap.add_argument("--c5", type=int, default=2000, help="measured requests of the serving leg")
     ap.add_argument("--c5-warmup", type=int, default=200, help="warm-up requests of the serving leg")
+    ap.add_argument("--gf2-mad", action="store_true",
+                    help="run only the GF(2) multiply-add comparison: bit-packed M4RM kernel vs the e4m3 tensor-core "
+                         "kernel per shape, with the measured LOP3 and shared-memory load peaks")
     ap.add_argument("--cpu-omp-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-c3", action="store_true", help="skip the C3 tensor-vs-plain leg")
     return ap.parse_args()
@@ -435,6 +438,71 @@ def bench_c3(dev):
     return out
 
 
+GF2_SHAPES = [  # (m, n, k): planner shapes (leaf-level, UpdateRow, ClearDown) and large squares
+    (1024, 2816, 256), (3072, 3072, 3072), (3072, 30720, 3072), (6144, 6144, 6144), (6144, 92160, 6144),
+    (8192, 16384, 2048), (16384, 16384, 16384)]
+
+
+def bench_gf2_mad(dev, reps=5):
+    """GF(2) job MAD on one shape at a time: the bit-packed kernel
+    (gfe_mad_gf2, CUDA events around the launch) against the tensor-core
+    kernel on e4m3 operands (the planner's representation; device-stamped
+    duration of k_mad_tc alone, without gfe_mad's conversions).  Median of
+    `reps` after one warm-up; inputs larger than L2 for all but the smallest."""
+    import torch
+    from paper_1806_04211_gb300 import gfe, synth
+    pk = gfe.gf2_peaks()
+    out = {"peaks": pk, "shapes": []}
+    for m, n, k in GF2_SHAPES:
+        Aw = synth.bernoulli_gf2(m, k, 3, 1, device=dev)
+        Bw = synth.bernoulli_gf2(k, n, 3, 2, device=dev)
+        C = torch.empty((m, synth.gf2_words_per_row(n)), dtype=torch.int64, device=dev)
+        gfe.mad_gf2(None, Aw, Bw, n, k, out=C)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gfe.mad_gf2(None, Aw, Bw, n, k, out=C)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        t_bits = statistics.median(ts)
+        ref_bits = C
+        A8 = synth.unpack_gf2(Aw, k)
+        B8 = synth.unpack_gf2(Bw, n)
+        del Aw, Bw
+        C8 = gfe.mad(None, A8, B8, 2)
+        ts = []
+        for _ in range(reps):
+            gfe.profile_enable(True, kinds=["mad_tensor"])
+            gfe.profile_read(True)
+            gfe.trace_enable(1 << 12)
+            gfe.mad(None, A8, B8, 2, out=C8)
+            torch.cuda.synchronize()
+            prof = gfe.profile_read(True)
+            gfe.trace_enable(0)
+            gfe.profile_enable(False)
+            ts.append(prof["ms"]["mad_tensor"])
+        t_tc = statistics.median(ts)
+        same = bool(torch.equal(synth.pack_gf2(C8), ref_bits))
+        madds = float(m) * n * k
+        nb = n / 8.0
+        lookups = m * ((k + 7) // 8) * nb                      # one n-bit entry per row and slice
+        builds = -(-m // 512) * ((k + 7) // 8) * 256 * nb      # 256 entries per slice and 512-row tile
+        out["shapes"].append({
+            "m": m, "n": n, "k": k, "equal": same,
+            "bits_m4rm": {"ms": t_bits, "madds_per_s": madds / (t_bits * 1e-3),
+                          "frac_of_alu_lop3": madds / (t_bits * 1e-3) / pk["gf2_madds_per_s_alu"],
+                          "smem_bytes": lookups + builds,
+                          "frac_of_lds": (lookups + builds) / (t_bits * 1e-3) / pk["lds_bytes_per_s"]},
+            "e4m3_tensor": {"ms": t_tc, "madds_per_s": madds / (t_tc * 1e-3)},
+            "faster": "bits_m4rm" if t_bits < t_tc else "e4m3_tensor"})
+        del A8, B8, C8, C, ref_bits
+        gfe.release_workspace()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -480,6 +548,11 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    if args.gf2_mad:
+        if rank == 0:
+            print(json.dumps({"gf2_mad": bench_gf2_mad(dev)}), flush=True)
+        barrier(ws)
+        return
 
     def make_insts(n):
         out = []

@@ -12,7 +12,7 @@
 // of the row-by-row product and reads operands from shared memory with
 // 128-bit loads.
 //
-// CTA tile: 1024 rows x 16 words (1024 columns) of C, 512 threads.  A thread
+// CTA tile: 512 rows x 16 words (1024 columns) of C, 256 threads.  A thread
 // owns 16 consecutive rows x 2 words (one uint4) in registers.  Per 64-bit
 // chunk of k: A's 64 bits of every tile row are stored transposed in shared
 // memory (byte s of each row contiguous over rows), the chunk's 64 rows of B
@@ -29,9 +29,9 @@
 namespace gfe {
 namespace {
 
-constexpr int G_BM = 1024;        // rows of a tile
+constexpr int G_BM = 512;         // rows of a tile
 constexpr int G_BW = 16;          // 64-bit words of a tile row
-constexpr int G_THREADS = 512;
+constexpr int G_THREADS = 256;
 constexpr int G_ROWS = 16;        // rows per thread
 constexpr int G_SMEM = 2 * 256 * G_BW * 8 + 64 * G_BW * 8 + 8 * G_BM;  // tables, B chunk, A bytes
 
@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     uint4 acc[G_ROWS];
 #pragma unroll
     for (int j = 0; j < G_ROWS; ++j) acc[j] = make_uint4(0, 0, 0, 0);
-    const int bw = tid & 15, bh = tid >> 4;  // table-build item: word column, high 5 bits
+    // table-build items: word column bw, high 5 bits bh and bh + 16
+    const int bw = tid & 15, bh = tid >> 4;
     for (int64_t ch = ch0; ch < ch1; ++ch) {
         __syncthreads();  // the previous chunk's readers are done with As, Bs and the tables
         const int64_t kc0 = ch * 64;
@@ -101,9 +102,13 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         }
         __syncthreads();
         build_entries(Tb, Bs, 0, bw, bh);
+        build_entries(Tb, Bs, 0, bw, bh + 16);
         for (int s = 0; s < 8; ++s) {
             __syncthreads();  // table s complete; table s+1's buffer free
-            if (s < 7) build_entries(Tb + ((s + 1) & 1) * 256 * G_BW, Bs, s + 1, bw, bh);
+            if (s < 7) {
+                build_entries(Tb + ((s + 1) & 1) * 256 * G_BW, Bs, s + 1, bw, bh);
+                build_entries(Tb + ((s + 1) & 1) * 256 * G_BW, Bs, s + 1, bw, bh + 16);
+            }
             const uint64_t *T = Tb + (s & 1) * 256 * G_BW;
             const uint4 ab = *(const uint4 *)(As + s * G_BM + rbase);
             const uint32_t aw[4] = {ab.x, ab.y, ab.z, ab.w};

@@ -423,11 +423,14 @@ def _result_struct(res, dev, bits: bool):
     es = 8 if bits else 1
     rk = torch.tensor([int(res["rank"])], dtype=torch.int64, device=dev)
 
+    def addr(t):
+        # the address of the view's first element, also for an empty view
+        # (the result tensors are views of buffers of at least one row)
+        return t.untyped_storage().data_ptr() + t.storage_offset() * t.element_size()
+
     def p_ld(key):
         t = res[key] if key in res else None
-        # the result tensors are views of buffers of at least one row: their
-        # address is valid even when the view is empty
-        return (None, 0) if t is None else (t.data_ptr(), t.stride(0) * es)
+        return (None, 0) if t is None else (addr(t), t.stride(0) * es)
 
     R, ldR = p_ld("R")
     M, ldM = p_ld("M")
@@ -435,7 +438,7 @@ def _result_struct(res, dev, bits: bool):
     ups = res["ups"]
     rho = res["rho"]
     keep = (rk, ups, rho)
-    st = GfeResult(rk.data_ptr(), ups.data_ptr(), rho.data_ptr(), R, ldR, M, ldM, K, ldK, None, 0, None, 0)
+    st = GfeResult(rk.data_ptr(), addr(ups), addr(rho), R, ldR, M, ldM, K, ldK, None, 0, None, 0)
     return st, keep
 
 
