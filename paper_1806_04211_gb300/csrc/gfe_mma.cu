@@ -277,17 +277,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const float pf = (float)p, invp = 1.0f / (float)p, halfp = (float)(p >> 1);
         const bool vec = ((ldc * G::ES) % 16 == 0) && (((uintptr_t)Cv & 15) == 0) &&
                          (!Wv || (((ldw * G::ES) % 16 == 0) && (((uintptr_t)Wv & 15) == 0)));
+        // W words of one 32-column chunk: 32 e4m3 bytes or 32 bf16
+        constexpr int WQ = F8 ? 2 : 4;
         int i = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
             const int b = i & 1;
             const uint32_t use = (uint32_t)(i >> 1);
+            const int m0 = (t % mt) * TBM, n0 = (t / mt) * TBN;
+            const int row = m0 + quarter * 32 + lane;
+            // this thread's W (its row, the warp's 128 columns) is loaded before
+            // the accumulator is waited for, so its latency overlaps the MMAs
+            uint4 wpre[4][WQ];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int cb = n0 + half * 128 + 32 * q;
+                const bool full = Wv && vec && row < M && cb + 32 <= N;
+#pragma unroll
+                for (int h = 0; h < WQ; ++h)
+                    wpre[q][h] = full ? ((const uint4 *)((const char *)Wv + ((int64_t)row * ldw + cb) * G::ES))[h]
+                                      : make_uint4(0, 0, 0, 0);
+            }
             const bool have = __all_sync(0xffffffffu, mbar_wait(&accf[b], use & 1u, err));
             if (!have) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int m0 = (t % mt) * TBM, n0 = (t / mt) * TBN;
-            const int row = m0 + quarter * 32 + lane;
-#pragma unroll 1
-            for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+#pragma unroll
+            for (int qc = 0; qc < 4; ++qc) {
+                const int c0 = half * 128 + 32 * qc;
                 uint32_t v[32];
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TBN + c0);
                 asm volatile(
@@ -303,18 +318,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (row >= M) continue;
                 const int cb = n0 + c0;
+                const bool full_chunk = vec && cb + 32 <= N;
+                if constexpr (F8) {
+                    if (p == 2 && full_chunk) {
+                        // GF(2): the codes are 0 and 1.0, so every partial sum is
+                        // an integer in [0, 2^22] (the k chunk) and adding 2^23
+                        // puts it in the mantissa: its parity is bit 0.  Bytes of
+                        // four results gather into one word, W's bit (bit 3 of a
+                        // code 0x38) is XORed in, and x 0x38 gives the e4m3 codes.
+                        uint32_t o[8];
+#pragma unroll
+                        for (int g4 = 0; g4 < 8; ++g4) {
+                            uint32_t u[4];
+#pragma unroll
+                            for (int h = 0; h < 4; ++h)
+                                u[h] = __float_as_uint(__uint_as_float(v[4 * g4 + h]) + 8388608.0f);
+                            const uint32_t lo = __byte_perm(u[0], u[1], 0x0040), hi = __byte_perm(u[2], u[3], 0x0040);
+                            uint32_t bits = __byte_perm(lo, hi, 0x5410) & 0x01010101u;
+                            if (Wv) {
+                                const uint4 &w4 = wpre[qc][g4 >> 2];
+                                const uint32_t ww = (g4 & 3) == 0 ? w4.x : (g4 & 3) == 1 ? w4.y : (g4 & 3) == 2 ? w4.z : w4.w;
+                                bits ^= (ww >> 3) & 0x01010101u;
+                            }
+                            o[g4] = bits * 0x38u;
+                        }
+                        uint4 *cp = (uint4 *)((uint8_t *)Cv + (int64_t)row * ldc + cb);
+                        cp[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                        cp[1] = make_uint4(o[4], o[5], o[6], o[7]);
+                        continue;
+                    }
+                }
                 float x[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) x[j] = fmodp(__uint_as_float(v[j]), pf, invp);
-                const bool full_chunk = vec && cb + 32 <= N;
                 // + W (centred, |w| <= (p-1)/2), back into [0, p), then centred
                 if (Wv) {
                     if (full_chunk) {
                         if constexpr (F8) {
-                            const uint4 *wp = (const uint4 *)((const uint8_t *)Wv + (int64_t)row * ldw + cb);
 #pragma unroll
                             for (int q = 0; q < 2; ++q) {
-                                const uint4 w4 = wp[q];
+                                const uint4 w4 = wpre[qc][q];
                                 const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                                 for (int h = 0; h < 4; ++h) {
@@ -328,10 +371,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 }
                             }
                         } else {
-                            const uint4 *wp = (const uint4 *)((const uint16_t *)Wv + (int64_t)row * ldw + cb);
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
-                                const uint4 w4 = wp[q];
+                                const uint4 w4 = wpre[qc][q];
                                 const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                                 for (int h = 0; h < 4; ++h) {
@@ -495,8 +537,11 @@ inline bool al16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 }  // namespace
 
 // largest K (multiple of 64) whose fp32 partial sums stay exact integers
+// GF(2) takes 2^22: its epilogue reads the parity of a partial sum below
+// 2^23 from the mantissa of (sum + 2^23)
 int64_t tc_k_chunk(int p) {
-    const int64_t cmax = p == 2 ? 1 : (p - 1) / 2;
+    if (p == 2) return ((int64_t)1 << 22) / TBK * TBK;
+    const int64_t cmax = (p - 1) / 2;
     const int64_t kc = (((int64_t)1 << 24) - 1) / (cmax * cmax);
     return kc / TBK * TBK;
 }

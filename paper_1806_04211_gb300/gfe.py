@@ -509,7 +509,7 @@ def mad_gf2(W, A: torch.Tensor, B: torch.Tensor, n: int, k: int, out=None, strea
     """gfe_mad_gf2: C := W + A B over GF(2) on bit-packed int64 rows (A m x k
     bits, B k x n bits, W and C m x n bits); W may be None or `out`."""
     m = A.shape[0]
-    C = out if out is not None else torch.empty((m, words_per_row(max(n, 1))), dtype=torch.int64, device=A.device)
+    C = out if out is not None else torch.zeros((m, words_per_row(max(n, 1))), dtype=torch.int64, device=A.device)
     _check(lib().gfe_mad_gf2(m, n, k, _ptr(W), 8 * W.stride(0) if W is not None else 0, _ptr(A), 8 * A.stride(0),
                              _ptr(B), 8 * B.stride(0), C.data_ptr(), 8 * C.stride(0), _stream(stream)))
     return C

@@ -211,7 +211,9 @@ def test_mad(p, m, n, k, impl):
 
 
 def _kchunk(p):
-    cmax = 1 if p == 2 else (p - 1) // 2
+    if p == 2:  # parity read from the mantissa of (sum + 2^23): sums stay below 2^22
+        return (1 << 22) // 64 * 64
+    cmax = (p - 1) // 2
     return ((1 << 24) - 1) // (cmax * cmax) // 64 * 64
 
 
@@ -222,7 +224,7 @@ def test_mad_tensor_exact_at_the_accumulation_bound(p):
     p <= 3): the fp32 partial sums come within one chunk of 2^24 (2^20).  The
     expected value is the closed form K * (+-cmax^2) + W mod p."""
     cmax = 1 if p == 2 else (p - 1) // 2
-    k = min(_kchunk(p) + 200, 1 << 20)
+    k = min(_kchunk(p) + 200, 1 << 20) if p != 2 else _kchunk(p) + 200
     m, n = 8, 40
     A = torch.full((m, k), cmax, dtype=torch.uint8, device=DEV)
     B = torch.full((k, n), cmax, dtype=torch.uint8, device=DEV)
