@@ -14,6 +14,8 @@ the benchmark uses (GPU).
 * C4, the full seeded draw of 4096 matrices through one batched call:
   certificate for every matrix, element-wise oracle parity on a seeded
   subset.
+* The paper's GF(193) experiment (Section 5) at half its side, 100000^2:
+  certificate.
 """
 import numpy as np
 import pytest
@@ -130,3 +132,20 @@ def test_c4_full_draw():
                 assert res["rank"] == ref["rank"]
                 for k in ("rho", "ups", "R", "M", "K"):
                     assert np.array_equal(res[k], ref[k]), (i, k)
+
+
+def test_paper_scale_gf193_100000_certificate():
+    """The paper's GF(193) experiment (Section 5) at half its side: 100000^2
+    uniform, echelon form with transformation, certified."""
+    gfe.release_workspace()
+    torch.cuda.empty_cache()
+    n = 100000
+    A = synth.matrix(193, n, n, seed=1, device=DEV)
+    got = gfe.echelon(A, 193)
+    assert got["rank"] == n
+    res = host(got)
+    Ah = A.cpu().numpy()
+    del got, A
+    gfe.release_workspace()
+    torch.cuda.empty_cache()
+    assert O.certify(Ah, 193, res, nvec=2, seed=19) == 0
