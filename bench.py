@@ -53,6 +53,17 @@ def parse():
     ap.add_argument("--gf2-mad", action="store_true",
                     help="run only the GF(2) multiply-add comparison: bit-packed M4RM kernel vs the e4m3 tensor-core "
                          "kernel per shape, with the measured LOP3 and shared-memory load peaks")
+    ap.add_argument("--single", type=int, default=0,
+                    help="profiling run: one GF(2) matrix of side N (uniform, or --twin), one untimed and one "
+                         "counted call; prints the library's launch counts and algorithmic work")
+    ap.add_argument("--twin", action="store_true", help="with --single: the rank-0.75n twin")
+    ap.add_argument("--block", type=int, default=0, help="with --single: top-level block side (0: the table)")
+    ap.add_argument("--side-tiles", type=int, default=-1,
+                    help="with --single: tiles per CTA of the planner's side-stream multiply-adds (-1: default)")
+    ap.add_argument("--trace", action="store_true", help="with --single: time every launch (events; the "
+                                                          "multiply-add stamps itself) and group by kind and shape")
+    ap.add_argument("--mad-shapes", action="store_true",
+                    help="profiling run: the tensor-core multiply-add alone on the planner's GF(2) shape classes")
     ap.add_argument("--cpu-omp-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-c3", action="store_true", help="skip the C3 tensor-vs-plain leg")
     ap.add_argument("--no-f2", action="store_true", help="skip the paper-scale 100000^2 GF(193) leg")
@@ -527,6 +538,115 @@ def bench_paper_scale(dev):
             "paper": "200000^2 GF(193): 445 min on 64 cores (Section 5), about 3.0e11 mul-adds/s"}
 
 
+def union_of(iv):
+    iv = sorted(iv)
+    tot, cs, ce = 0.0, None, None
+    for s0, e0 in iv:
+        if ce is None or s0 > ce:
+            if ce is not None:
+                tot += ce - cs
+            cs, ce = s0, e0
+        else:
+            ce = max(ce, e0)
+    return tot + (ce - cs if ce is not None else 0.0)
+
+
+def run_single(args, dev):
+    """One GF(2) matrix of the C2 family through the batched entry point (one
+    worker): an untimed call, then a counted one (and with --trace a traced
+    one: per-kind unions of launch intervals, multiply-add shape classes)."""
+    import collections
+    import torch
+    from paper_1806_04211_gb300 import gfe, synth
+    n = args.single
+    if args.block:
+        gfe.set_block_policy(args.block, args.block)
+    if args.side_tiles >= 0:
+        gfe._check(gfe.lib().gfe_set_side_tiles(args.side_tiles))
+    A = synth.matrix(2, n, n, seed=1, rank=(3 * n) // 4 if args.twin else None, device=dev)
+    gfe.batch_echelon([(A, 2, n)], workers=1)
+    torch.cuda.synchronize()
+    gfe.profile_enable(True, kinds=["other"])  # counts only: no kind is timed
+    gfe.profile_read(True)
+    t = time.perf_counter()
+    d = gfe.batch_echelon([(A, 2, n)], workers=1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    pr = gfe.profile_read(True)
+    gfe.profile_enable(False)
+    out = {"n": n, "rank": d[0]["rank"], "block": args.block or gfe.lib().gfe_auto_block(2, n, n), "seconds": dt,
+           "launches": pr["launches"], "madds": pr["madds"], "algorithmic_bytes": pr["bytes"],
+           "host_syncs": pr["host_syncs"]}
+    if args.trace:
+        gfe.profile_enable(True)
+        gfe.profile_read(True)
+        gfe.trace_enable(1 << 21)
+        gfe.batch_echelon([(A, 2, n)], workers=1)
+        torch.cuda.synchronize()
+        tr = gfe.trace_read(True)
+        gfe.trace_enable(0)
+        gfe.profile_enable(False)
+        by = collections.defaultdict(list)
+        for r in tr:
+            by[r["kind"]].append((r["start_ms"], r["start_ms"] + r["ms"]))
+        out["union_ms_by_kind"] = {k: union_of(v) for k, v in by.items()}
+        out["union_ms_all"] = union_of([x for v in by.values() for x in v])
+
+        def bucket(x):
+            for lim in (64, 256, 1024, 2048, 4096, 6144, 12288):
+                if x <= lim:
+                    return str(lim)
+            return "more"
+        cls = collections.defaultdict(lambda: [0, 0.0, 0.0])
+        for r in tr:
+            if r["kind"] == "mad_tensor":
+                c = cls["m<=%s n<=%s k<=%s" % (bucket(r["m"]), bucket(r["n"]), bucket(r["k"]))]
+                c[0] += 1
+                c[1] += r["ms"]
+                c[2] += 2.0 * r["m"] * r["n"] * r["k"]
+        out["mad_classes"] = sorted(({"shape": k, "launches": v[0], "ms": v[1],
+                                      "tflops": v[2] / (v[1] * 1e-3) / 1e12 if v[1] else 0.0}
+                                     for k, v in cls.items()), key=lambda x: -x["ms"])
+    gfe.set_block_policy()
+    gfe._check(gfe.lib().gfe_set_side_tiles(4))
+    return out
+
+
+MAD_SHAPES = [(1024, 256, 256), (1024, 1024, 256), (1024, 6144, 256), (256, 1024, 256), (6144, 6144, 64),
+              (6144, 6144, 8), (6144, 6144, 6144), (6144, 92160, 6144), (1024, 92160, 256), (128, 256, 64)]
+
+
+def run_mad_shapes(dev, reps=7):
+    """The tensor-core multiply-add alone (GF(2) e4m3 codes, W given) on the
+    planner's shape classes: median device-stamped duration of k_mad_tc."""
+    import torch
+    from paper_1806_04211_gb300 import gfe, synth
+    out = []
+    for m, n, k in MAD_SHAPES:
+        A = synth.uniform_u8(m, k, 2, 1, 1, device=dev)
+        B = synth.uniform_u8(k, n, 2, 1, 2, device=dev)
+        W = synth.uniform_u8(m, n, 2, 1, 3, device=dev)
+        C = torch.empty_like(W)
+        gfe.mad(W, A, B, 2, out=C)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            gfe.profile_enable(True, kinds=["mad_tensor"])
+            gfe.profile_read(True)
+            gfe.trace_enable(1 << 10)
+            gfe.mad(W, A, B, 2, out=C)
+            torch.cuda.synchronize()
+            pr = gfe.profile_read(True)
+            gfe.trace_enable(0)
+            gfe.profile_enable(False)
+            ts.append(pr["ms"]["mad_tensor"] * 1e3)
+        t = statistics.median(ts)
+        out.append({"m": m, "n": n, "k": k, "kernel_us": t, "tflops": 2.0 * m * n * k / (t * 1e-6) / 1e12})
+        del A, B, W, C
+    gfe.release_workspace()
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -572,9 +692,14 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    if args.gf2_mad:
+    if args.gf2_mad or args.single or args.mad_shapes:
         if rank == 0:
-            print(json.dumps({"gf2_mad": bench_gf2_mad(dev)}), flush=True)
+            if args.gf2_mad:
+                print(json.dumps({"gf2_mad": bench_gf2_mad(dev)}), flush=True)
+            if args.single:
+                print(json.dumps({"single": run_single(args, dev)}), flush=True)
+            if args.mad_shapes:
+                print(json.dumps({"mad_shapes": run_mad_shapes(dev)}), flush=True)
         barrier(ws)
         return
 

@@ -329,6 +329,12 @@ int64_t gfe_auto_block(int32_t p, int64_t m, int64_t n);
  * p <= 13, 256 for larger p); larger values are capped at that.  Process
  * wide.  Results never depend on it.  GFE_EINVAL outside [0, 1024]. */
 gfe_status gfe_set_leaf_rows(int64_t rows);
+/* Tiles per thread block of the multiply-adds the planner runs beside its
+ * critical path (the side streams): enough blocks are launched that none
+ * takes more, so SMs come free for the critical path every few tiles.
+ * 0 = one persistent block per SM.  Default 4.  Results never depend on it.
+ * GFE_EINVAL outside [0, 1024]. */
+gfe_status gfe_set_side_tiles(int32_t tiles);
 
 /* Kernel profile of the calls made since the last reset (all streams).
  * While enabled every launch is counted; launches of the kinds selected by

@@ -784,6 +784,12 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block) {
 
 int64_t gfe_auto_block(int32_t p, int64_t m, int64_t n) { return auto_block(p, m, n); }
 
+gfe_status gfe_set_side_tiles(int32_t tiles) {
+    if (tiles < 0 || tiles > 1024) return (set_error("side tiles must be in [0, 1024]"), GFE_EINVAL);
+    g_side_tiles = tiles;
+    return GFE_OK;
+}
+
 gfe_status gfe_set_leaf_rows(int64_t rows) {
     if (rows < 0 || rows > ECH_LEAF_ROWS) return (set_error("leaf rows must be in [0, 1024]"), GFE_EINVAL);
     g_leaf_rows = rows;

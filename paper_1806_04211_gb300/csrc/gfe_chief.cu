@@ -432,6 +432,8 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
 int64_t g_block_threshold = 0, g_block_big = 0;
 // rows of a leaf block in the leaf grid; 0: auto_leaf_rows
 int64_t g_leaf_rows = 0;
+// tiles per CTA of the side streams' multiply-adds (0: one persistent CTA per SM)
+int g_side_tiles = 4;
 
 thread_local cudaEvent_t g_wait_event = nullptr;
 
@@ -567,9 +569,9 @@ void chief(Ctx &X, const DMat &H, const std::vector<int64_t> &arows, const std::
     const Level lv = X.level(X.depth);
     const cudaStream_t s1 = lv.s1, s2 = lv.s2;
     ++X.depth;
-    // side-stream multiply-adds take at most SIDE_TILES tiles per CTA, so the
-    // ClearDown chain (on a higher-priority stream) gets SMs as tiles finish
-    constexpr int SIDE_TILES = 4;
+    // side-stream multiply-adds take at most g_side_tiles tiles per CTA, so
+    // the ClearDown chain (on a higher-priority stream) gets SMs as tiles finish
+    const int SIDE_TILES = g_side_tiles;
     auto on = [&](cudaStream_t s) {
         X.L.st = s;
         X.L.tiles_per_cta = s == s0 ? 0 : SIDE_TILES;

@@ -180,6 +180,7 @@ void run_chief(const Launch &L, char *ws, size_t ws_bytes, bool dry, const DMat 
                int64_t *syncs);
 
 extern int64_t g_block_threshold, g_block_big, g_leaf_rows;
+extern int g_side_tiles;
 // A host thread that set g_wait_event (a cudaEventBlockingSync event) sleeps
 // in its waits for the GPU instead of spinning: the batched form runs more
 // workers than the host has cores.  host_wait(s) waits for stream s either way.

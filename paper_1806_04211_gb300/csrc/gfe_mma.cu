@@ -147,11 +147,25 @@ __device__ __forceinline__ void unpack_e4m3x2(uint32_t two, float &lo, float &hi
 constexpr int TC_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int EPI_WARPS = 8;
 
-// Persistent: CTA c handles tiles c, c + gridDim.x, ...; tile t covers rows
-// (t % mt) * 128 and columns (t / mt) * 256 (M fastest, so CTAs resident at
-// the same time share B's columns).  The accumulator is double-buffered in
-// TMEM (2 x 256 fp32 columns) so the epilogue of one tile overlaps the MMAs
-// of the next.
+// Tile order: bands of TBAND columns of tiles; within a band, TBAND tiles
+// of one row of tiles after another.  The tiles resident at the same time
+// (about one per SM) then cover a block of about (SMs / TBAND) x TBAND
+// tiles, whose A rows and B columns both stay in L2.  (With the rows of
+// tiles fastest, A would be read from HBM once per 256 columns: for the
+// ClearUp products of Step 3, whose A has tens of thousands of rows, that
+// made the kernel HBM-bound.)
+constexpr int TBAND = 8;
+__device__ __forceinline__ void tile_of(int t, int mt, int nt, int &m0, int &n0) {
+    const int band = t / (mt * TBAND);
+    const int idx = t - band * mt * TBAND;
+    const int w = min(TBAND, nt - band * TBAND);
+    m0 = (idx / w) * TBM;
+    n0 = (band * TBAND + idx % w) * TBN;
+}
+
+// Persistent: CTA c handles tiles c, c + gridDim.x, ... in the order of
+// tile_of.  The accumulator is double-buffered in TMEM (2 x 256 fp32
+// columns) so the epilogue of one tile overlaps the MMAs of the next.
 template <bool F8>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_mad_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int p, int M,
@@ -202,7 +216,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int m0 = (t % mt) * TBM, n0 = (t / mt) * TBN;
+                int m0, n0;
+                tile_of(t, mt, nt, m0, n0);
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = it % TSTAGES;
                     const uint32_t ph = (uint32_t)(it / TSTAGES) & 1u;
@@ -283,7 +298,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
             const int b = i & 1;
             const uint32_t use = (uint32_t)(i >> 1);
-            const int m0 = (t % mt) * TBM, n0 = (t / mt) * TBN;
+            int m0, n0;
+            tile_of(t, mt, nt, m0, n0);
             const int row = m0 + quarter * 32 + lane;
             // this thread's W (its row, the warp's 128 columns) is loaded before
             // the accumulator is waited for, so its latency overlaps the MMAs

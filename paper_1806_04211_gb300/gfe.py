@@ -87,6 +87,7 @@ SIGNATURES = {
     "gfe_set_block_policy": (_i32, [_i64, _i64]),
     "gfe_auto_block": (_i64, [_i32, _i64, _i64]),
     "gfe_set_leaf_rows": (_i32, [_i64]),
+    "gfe_set_side_tiles": (_i32, [_i32]),
     "gfe_profile_enable": (_i32, [_i32]),
     "gfe_profile_read": (_i32, [ctypes.POINTER(GfeProfile), _i32]),
     "gfe_trace_enable": (_i32, [_i64]),
