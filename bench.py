@@ -191,6 +191,17 @@ def union_ms(recs):
     return tot + (ce - cs if ce is not None else 0.0)
 
 
+# DRAM bytes (read + write) of the tensor-core multiply-add per algorithmic
+# byte (A, B, W read, C written), from one ncu capture of every k_mad_tc
+# launch of one GF(2) 24576^2 matrix with the 6144-wide blocks of the
+# n = 100000 policy (dram__bytes_read.sum + dram__bytes_write.sum over 5816
+# launches: 38.64 GB; the library's algorithmic bytes for the same launches:
+# 40.47 GB), with the current kernel (banded tile order, GF(2) epilogue).
+# The full-size step is too large to capture; its launches are scaled by
+# their algorithmic bytes.
+MAD_TRAFFIC_PER_ALG_BYTE = 0.955
+
+
 def roofline(prof, codec_bytes, trace):
     """Roofline of the dominant kernel kind of the timed region.  The
     planner runs multiply-adds on several streams at once, so per-launch
@@ -212,9 +223,14 @@ def roofline(prof, codec_bytes, trace):
         ratio = 2.0 if codec_bytes == 1 else 1.0
         peak = pk["bf16_tflops_sustained"] * ratio
         achieved = 2.0 * madds / ((um if um else ms) * 1e-3) / 1e12
+        alg_bytes = prof["bytes"][k] / max(prof["launches"][k], 1)
         return {"kernel": "k_mad_tc<%s> (tcgen05)" % ("e4m3" if codec_bytes == 1 else "bf16"), "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": "%s bf16 sustained x %.0f" % (src, ratio),
+                "traffic": MAD_TRAFFIC_PER_ALG_BYTE * alg_bytes,
+                "traffic_source": "bytes per launch: %.3f x the algorithmic bytes per launch, the ratio from an ncu "
+                                  "capture of every multiply-add of one 24576^2 matrix with the same 6144 blocks"
+                                  % MAD_TRAFFIC_PER_ALG_BYTE,
+                "peak_source": "%s bf16 sustained x %.0f" % (src, ratio),
                 "denominator": ("union of the launches' intervals (%s clock)" % recs[0].get("clock", "event"))
                 if um else "sum of launch times",
                 "union_ms": um, "sum_of_launch_ms": ms,
