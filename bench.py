@@ -345,7 +345,8 @@ def bench_batched(dev, count, plain_count=512, clock_index=None):
     specs = c4_matrices(count)
     mats = [(synth.matrix(p, m, n, seed=5000 + i, rank=rk, device=dev), p, n) for i, (p, m, n, rk) in enumerate(specs)]
     units = float(sum(m * n * min(m, n) for p, m, n, rk in specs))
-    one_launch = sum(1 for p, m, n, rk in specs if m * n * min(m, n) / (16 if p == 2 else 1) <= 4e9)
+    one_launch = sum(1 for p, m, n, rk in specs
+                     if m * n * min(m, n) / (16 if p == 2 else (2.5 if p <= 13 else 1)) <= 4e9)
     gfe.batch_echelon(mats, workers=C4_WORKERS)
     torch.cuda.synchronize()
     times = []

@@ -136,8 +136,9 @@ gfe_status gfe_batch_echelon(const gfe_matrix *As, const gfe_result *outs, int32
                              uint32_t flags, void *ws, size_t ws_bytes, void *stream);
 /*
  * Matrices of a batch with at most `side` rows and columns (side <= 2048,
- * the default) and work m n min(m,n) (over GF(2): a 16th of it) at most
- * max_work (<= 0: the default 4e9), over GF(2) (GFE_BITS64) or any odd prime
+ * the default) and work m n min(m,n) at most max_work (<= 0: the default
+ * 4e9; the work of a GF(2) matrix counts a 16th, and that of a p <= 13 byte
+ * matrix 1/2.5, for their faster kernels), over GF(2) (GFE_BITS64) or any odd prime
  * p <= 251 (GFE_U8), with no
  * dense E / T asked for, are echelonised together by ONE kernel launch per
  * kind (p <= 13, larger p, GF(2)), one thread block per matrix, with no host

@@ -465,12 +465,14 @@ constexpr double SMALL_WORK_DEFAULT = 4e9;
 static int64_t g_batch_small_max = SMALL_MAX;
 static double g_batch_small_work = SMALL_WORK_DEFAULT;
 
-// GF(2) work counts 1/16: one CTA clears 64 columns of a row per word and
-// updates a row by table XORs, about 16x the byte kernels' rate
 static bool batch_small(const gfe_matrix &A, uint32_t flags) {
     if (flags & (GFE_WANT_DENSE_E | GFE_WANT_DENSE_T)) return false;
     if (A.m > g_batch_small_max || A.n > g_batch_small_max) return false;
-    const double work = (double)A.m * (double)A.n * (double)std::min(A.m, A.n) / (A.fmt == GFE_BITS64 ? 16 : 1);
+    // work in units of the wide kernel's rate: the GF(2) kernel is about 16x
+    // as fast and the byte kernel for p <= 13 (rest update on int8 tensor
+    // instructions) about 2.5x
+    const double rate = A.fmt == GFE_BITS64 ? 16.0 : (A.p <= SMALL_MAX_P ? 2.5 : 1.0);
+    const double work = (double)A.m * (double)A.n * (double)std::min(A.m, A.n) / rate;
     if (work > g_batch_small_work) return false;
     return small_eligible(A.p, A.fmt, A.m, A.n);
 }

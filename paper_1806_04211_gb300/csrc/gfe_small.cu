@@ -157,9 +157,13 @@ constexpr int BK = 32;             // panel width: two 16-byte vectors per row
 constexpr int U8_THREADS = 1024;   // one thread per row (two rows above 1024) in the panel
 constexpr int U8_WARPS = U8_THREADS / 32;
 
+constexpr int OT = 36;             // pitch (bytes) of a column of OLDT: 32 pivots + 4 (bank spread)
 struct U8Shared {
     uint8_t P[SMALL_MAX * BK];        // the panel, row j at BK j
-    uint8_t OLD[BK * SMALL_MAX];      // this panel's pivot rows before the update (ldw apart)
+    // this panel's pivot rows before the update, transposed: column k of the
+    // matrix at OT k holds pivot rows 0..31 (zero past kp and past ldw)
+    alignas(16) uint8_t OLDT[(SMALL_MAX + BK) * OT];
+    alignas(16) uint8_t stage[U8_WARPS][16 * BK];  // per warp: a 16 x 32 tile of products mod p
     int16_t piv_of_col[SMALL_MAX];    // pivot row of column c, -1: none
     int16_t col_of_row[SMALL_MAX];    // the column row j is the pivot of, -1: none
     int16_t ups[SMALL_MAX], upsbar[SMALL_MAX], rho[SMALL_MAX], rhobar[SMALL_MAX];
@@ -317,55 +321,83 @@ __device__ void small_u8(const SmallJob &J, U8Shared &S) {
         }
         const int kp = S.kp;  // written before the last barrier of the loop
         if (kp > 0) {
-            // the pivot rows as they were before this panel's operations
-            for (int v = tid; v < kp * vpr; v += U8_THREADS) {
-                const int q = v / vpr, k0 = (v - q * vpr) << 4;
-                *(uint4 *)(S.OLD + q * ldw + k0) = *(const uint4 *)(W + S.piv_row[q] * ldw + k0);
+            // the pivot rows as they were before this panel's operations,
+            // transposed (warp: 16 columns; lane q: pivot row q), zero past kp
+            // and past ldw up to a whole 32-column block
+            const int ncols = (ldw + BK - 1) / BK * BK;
+            for (int k0 = warp * 16; k0 < ncols; k0 += U8_WARPS * 16) {
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (lane < kp && k0 < ldw) v = *(const uint4 *)(W + S.piv_row[lane] * ldw + k0);
+                const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int t = 0; t < 16; ++t) S.OLDT[(k0 + t) * OT + lane] = (uint8_t)(vv[t >> 2] >> (8 * (t & 3)));
             }
             __syncthreads();
-            // every row: rest += sum_q coef_q * OLD_q, coef_q = P[j][pivot column q] - [j = pivot row q]
-            for (int j = warp; j < m; j += U8_WARPS) {
-                uint32_t cq = 0;
-                if (lane < kp) {
-                    cq = S.P[j * BK + S.piv_pc[lane]];
-                    if (S.piv_row[lane] == j) cq = cq ? cq - 1 : (uint32_t)(p - 1);
-                    S.coef[warp][lane] = (uint8_t)cq;
-                }
-                if (!__any_sync(0xffffffffu, cq != 0)) continue;
-                __syncwarp();
-                uint8_t *row = W + j * ldw;
-                for (int k0 = lane << 4; k0 < ldw; k0 += 512) {
-                    if (k0 >= c0 && k0 < c0 + BK) continue;  // the panel's own columns come from P
-                    const uint4 w = *(const uint4 *)(row + k0);
-                    uint32_t e[4] = {w.x & 0x00FF00FFu, w.y & 0x00FF00FFu, w.z & 0x00FF00FFu, w.w & 0x00FF00FFu};
-                    uint32_t o[4] = {(w.x >> 8) & 0x00FF00FFu, (w.y >> 8) & 0x00FF00FFu, (w.z >> 8) & 0x00FF00FFu,
-                                     (w.w >> 8) & 0x00FF00FFu};
-                    for (int q4 = 0; q4 < kp; q4 += 4) {
-                        const uint32_t c4 = *(const uint32_t *)(&S.coef[warp][q4]);
+            // every row: rest += sum_q coef_q * OLD_q, coef_q = P[j][pivot column q] - [j = pivot row q],
+            // as a product (rows x 32) (32 x columns) on the tensor cores: int8 mma.sync m16n8k32 with
+            // int32 accumulation (at most 32 * 12 * 12 < 2^13), then mod p, then + the row's entry mod p.
+            // A warp takes 16 rows and every 32-column block but the panel's own (those come from P).
+            const int gid = lane >> 2, tig = lane & 3;
+            const uint32_t pppp = (uint32_t)p * 0x01010101u;
+            uint8_t *st = S.stage[warp];
+            for (int r0 = warp * 16; r0 < m; r0 += U8_WARPS * 16) {
+                // A fragment: rows r0 + gid (a0, a2) and r0 + gid + 8 (a1, a3), coefficients
+                // q = 4 tig .. 4 tig + 3 (a0, a1) and 16 + 4 tig .. (a2, a3)
+                uint32_t a[4];
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const uint32_t c = (c4 >> (8 * t)) & 0xFFu;
-                            if (q4 + t < kp && c) {
-                                const uint4 v = *(const uint4 *)(S.OLD + (q4 + t) * ldw + k0);
-                                e[0] += c * (v.x & 0x00FF00FFu);
-                                e[1] += c * (v.y & 0x00FF00FFu);
-                                e[2] += c * (v.z & 0x00FF00FFu);
-                                e[3] += c * (v.w & 0x00FF00FFu);
-                                o[0] += c * ((v.x >> 8) & 0x00FF00FFu);
-                                o[1] += c * ((v.y >> 8) & 0x00FF00FFu);
-                                o[2] += c * ((v.z >> 8) & 0x00FF00FFu);
-                                o[3] += c * ((v.w >> 8) & 0x00FF00FFu);
-                            }
+                for (int h = 0; h < 4; ++h) {
+                    const int j = r0 + gid + ((h & 1) ? 8 : 0);
+                    const int qb = ((h & 2) ? 16 : 0) + 4 * tig;
+                    uint32_t w = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int q = qb + i;
+                        uint32_t cq = 0;
+                        if (j < m && q < kp) {
+                            cq = S.P[j * BK + S.piv_pc[q]];
+                            if (S.piv_row[q] == j) cq = cq ? cq - 1 : (uint32_t)(p - 1);
                         }
+                        w |= cq << (8 * i);
                     }
-                    uint4 out;
-                    out.x = mod_lanes(e[0], p, rcp) | (mod_lanes(o[0], p, rcp) << 8);
-                    out.y = mod_lanes(e[1], p, rcp) | (mod_lanes(o[1], p, rcp) << 8);
-                    out.z = mod_lanes(e[2], p, rcp) | (mod_lanes(o[2], p, rcp) << 8);
-                    out.w = mod_lanes(e[3], p, rcp) | (mod_lanes(o[3], p, rcp) << 8);
-                    *(uint4 *)(row + k0) = out;
+                    a[h] = w;
                 }
-                __syncwarp();
+                if (!__any_sync(0xffffffffu, (a[0] | a[1] | a[2] | a[3]) != 0u)) continue;
+                for (int cb = 0; cb < ncols; cb += BK) {
+                    if (cb == c0) continue;  // the panel's own columns
+                    // four n8 steps of the 16 x 32 tile; the products mod p staged as bytes
+#pragma unroll
+                    for (int s8 = 0; s8 < 4; ++s8) {
+                        const uint8_t *bcol = S.OLDT + (cb + 8 * s8 + gid) * OT + 4 * tig;
+                        const uint32_t b0 = *(const uint32_t *)bcol, b1 = *(const uint32_t *)(bcol + 16);
+                        int d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+                        asm volatile(
+                            "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                            "{%8,%9}, {%0,%1,%2,%3};"
+                            : "+r"(d0), "+r"(d1), "+r"(d2), "+r"(d3)
+                            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+                        // d0, d1: row gid, columns 8 s8 + 2 tig + {0, 1}; d2, d3: row gid + 8
+                        const uint32_t e0 = (uint32_t)d0 - (uint32_t)p * __umulhi((uint32_t)d0, rcp);
+                        const uint32_t e1 = (uint32_t)d1 - (uint32_t)p * __umulhi((uint32_t)d1, rcp);
+                        const uint32_t e2 = (uint32_t)d2 - (uint32_t)p * __umulhi((uint32_t)d2, rcp);
+                        const uint32_t e3 = (uint32_t)d3 - (uint32_t)p * __umulhi((uint32_t)d3, rcp);
+                        *(uint16_t *)(st + gid * BK + 8 * s8 + 2 * tig) = (uint16_t)(e0 | (e1 << 8));
+                        *(uint16_t *)(st + (gid + 8) * BK + 8 * s8 + 2 * tig) = (uint16_t)(e2 | (e3 << 8));
+                    }
+                    __syncwarp();
+                    // lane: row r0 + lane / 2, 16 columns from cb + 16 (lane & 1)
+                    const int j = r0 + (lane >> 1), k = cb + 16 * (lane & 1);
+                    if (j < m && k < ldw) {
+                        const uint4 pr = *(const uint4 *)(st + (lane >> 1) * BK + 16 * (lane & 1));
+                        uint4 *wp = (uint4 *)(W + j * ldw + k);
+                        uint4 w = *wp;
+                        // entries and products are below p: their sum is below 2p, one correction
+                        uint32_t x[4] = {w.x + pr.x, w.y + pr.y, w.z + pr.z, w.w + pr.w};
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) x[h] -= __vcmpgeu4(x[h], pppp) & pppp;
+                        *wp = make_uint4(x[0], x[1], x[2], x[3]);
+                    }
+                    __syncwarp();
+                }
             }
         }
         // the panel back into W
