@@ -665,8 +665,9 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
     __shared__ uint64_t orig[8][2 * W];    // the group's pivot rows at the group start
     __shared__ uint64_t tab[2][2 * W][16]; // XOR of every subset of pivots 0..3 / 4..7 (word-major)
     __shared__ uint32_t slc[32][8];        // bit q of slc[w][k]: column c0+k of row 32w+q
-    __shared__ uint32_t cms[32][8];        // bit q of cms[w][s]: pivot s in CM of row 32w+q
+    __shared__ __align__(16) uint32_t cms[32][8];  // bit q of cms[w][s]: pivot s in CM of row 32w+q
     __shared__ int16_t gpr[8], gpc[8];     // the group's pivots: row, column
+    __shared__ uint8_t gmark[1024];        // 1 + the group slot of a row that is a group pivot, else 0
     __shared__ int gnp;
     __shared__ uint8_t piv[1024];
     __shared__ int16_t slotOf[1024], pivpos[1024];
@@ -674,9 +675,34 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
     __shared__ int wsum[32];
     const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
 
-    // coalesced load: warp w reads its 32 rows one at a time, lane l the 8
-    // columns 8l..8l+7, stored as byte l of the row's 32-byte bitmask
-    {
+    // coalesced load into the rows' 32-byte bitmasks.  One-byte codes: warp w
+    // reads its 32 rows two at a time, lane l 16 columns 16 (l % 16) .. of
+    // row 2 i + l / 16 (16-byte loads; a byte is 1 iff it is not zero: four
+    // bytes at a time by a SIMD compare and a multiply that gathers their
+    // flags).  Two-byte codes: one row at a time, lane l columns 8l..8l+7.
+    if constexpr (sizeof(T) == 1) {
+        uint8_t *hb = (uint8_t *)hw;
+        const int half = lane >> 4, ch = lane & 15, c16 = 16 * ch;
+#pragma unroll 8
+        for (int rr = 0; rr < 16; ++rr) {
+            const int row = warp * 32 + 2 * rr + half;
+            uint32_t mask = 0;
+            if (row < alpha) {
+                const T *rp = H + (int64_t)row * ldh + c16;
+                if (c16 + 16 <= beta && ((uintptr_t)rp & 15) == 0) {
+                    const uint4 v = *(const uint4 *)rp;
+                    const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        mask |= (((__vcmpne4(vv[q], 0u) & 0x01010101u) * 0x01020408u) >> 24) << (4 * q);
+                } else {
+                    for (int q = 0; q < 16 && c16 + q < beta; ++q)
+                        if (rp[q]) mask |= 1u << q;
+                }
+            }
+            *(uint16_t *)(hb + row * 8 * W + 2 * ch) = (uint16_t)mask;
+        }
+    } else {
         uint8_t *hb = (uint8_t *)hw;
 #pragma unroll 8
         for (int rr = 0; rr < 32; ++rr) {
@@ -719,6 +745,7 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
     }
     piv[y] = 0;
     slotOf[y] = -1;
+    gmark[y] = 0;
     bool isp = false;
     __syncthreads();
 
@@ -753,16 +780,22 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
                 cmb[k] = 0u;
             }
             int np = 0;
+            // unrolled over the group's columns, so that each step touches only
+            // what can still change: the columns right of k and the group's
+            // pivots found so far (np <= k)
+#pragma unroll
             for (int k = 0; k < 8; ++k) {
                 // every lane takes its own first candidate row q and forms that
-                // row's byte and combination; the lowest lane with a candidate
+                // row's bits and combination; the lowest lane with a candidate
                 // holds the pivot and broadcasts them
                 const uint32_t cand = col[k] & cand_rows;
                 const int q = __ffs(cand) - 1;  // -1: none here
+                const int qq = q & 31;
                 uint32_t mine = 0;
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    mine |= (((col[u] >> (q & 31)) & 1u) << u) | (((cmb[u] >> (q & 31)) & 1u) << (8 + u));
+                for (int u = k + 1; u < 8; ++u) mine |= ((col[u] >> qq) & 1u) << u;
+#pragma unroll
+                for (int u = 0; u < k; ++u) mine |= ((cmb[u] >> qq) & 1u) << (8 + u);
                 const unsigned bal = __ballot_sync(0xffffffffu, cand != 0u);
                 if (bal == 0u) continue;  // uniform: no pivot in this column
                 const int owner = __ffs(bal) - 1;
@@ -771,14 +804,14 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
                 // rows with column c0+k set, other than the pivot
                 const uint32_t rows = col[k] & ~(lane == owner ? 1u << q : 0u);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    col[u] ^= rows & (0u - ((pb >> u) & 1u));
-                    cmb[u] ^= rows & (0u - ((pc >> u) & 1u));
-                }
+                for (int u = k + 1; u < 8; ++u) col[u] ^= rows & (0u - ((pb >> u) & 1u));
+#pragma unroll
+                for (int u = 0; u <= k; ++u) cmb[u] ^= rows & (0u - ((pc >> u) & 1u));
                 if (lane == owner) {
                     cand_rows &= ~(1u << q);
                     gpr[np] = (int16_t)(lane * 32 + q);
                     gpc[np] = (int16_t)(c0 + k);
+                    gmark[lane * 32 + q] = (uint8_t)(np + 1);
                 }
                 ++np;
             }
@@ -792,9 +825,8 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         const int np = gnp;
         if (np == 0) continue;  // uniform
         // (C) the group's pivot rows as they stand now, with their identity
-        int s_me = -1;
-        for (int u = 0; u < np; ++u)
-            if (gpr[u] == y) s_me = u;
+        const int s_me = (int)gmark[y] - 1;
+        if (s_me >= 0) gmark[y] = 0;
         if (s_me >= 0) {
             const int slot = ns + s_me;
 #pragma unroll
@@ -821,14 +853,22 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
         __syncthreads();
         // (E) add the rows of this row's combination; a pivot row also its identity
         int m = 0;
+        {
+            const uint4 ca = *(const uint4 *)&cms[warp][0], cb = *(const uint4 *)&cms[warp][4];
+            const uint32_t cw[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
 #pragma unroll
-        for (int u = 0; u < 8; ++u) m |= (int)((cms[warp][u] >> lane) & 1u) << u;
+            for (int u = 0; u < 8; ++u) m |= (int)((cw[u] >> lane) & 1u) << u;
+        }
         if (m) {
+            // the group's pivot rows are zero left of column c0 and in slot
+            // words past the group's last slot, and the second table is empty
+            // when the group has at most four pivots: those words are skipped
             const int lo = m & 15, hi = m >> 4;
+            const int hfirst = c0 >> 6, tlast = (ns + np - 1) >> 6;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                h[w] ^= tab[0][w][lo] ^ tab[1][w][hi];
-                t[w] ^= tab[0][W + w][lo] ^ tab[1][W + w][hi];
+                if (w >= hfirst) h[w] ^= tab[0][w][lo] ^ (np > 4 ? tab[1][w][hi] : 0ull);
+                if (w <= tlast) t[w] ^= tab[0][W + w][lo] ^ (np > 4 ? tab[1][W + w][hi] : 0ull);
             }
         }
         if (s_me >= 0) wxor<W>(t, (ns + s_me) >> 6, (uint64_t)1 << ((ns + s_me) & 63));
@@ -862,53 +902,61 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_gf2(int alpha, int beta, c
     // outputs: one row per warp; lane l writes the row's entries 8l .. 8l+7
     // (r <= 256), picking each from the row's 4 words by a fixed bit index
     // (the sorted slot for M and K, the non-pivot column for R)
+    // Each lane's 8 output columns read the same bit positions of every row
+    // (a sorted slot for M and K, a non-pivot column for R): their 32-bit
+    // word and shift are computed once, and a row costs 8 shared loads, 8
+    // bit extracts and one multiply per 4 entries (bits times the code of 1).
     const int e0 = 8 * lane;
-    auto emit = [&](const uint64_t *src, const int (&bit)[8], int count, T *out) {
-        const uint64_t w0 = src[0], w1 = src[1], w2 = src[2], w3 = src[3];
-        T v[8];
+    auto emit = [&](const uint64_t *src, const int (&qw)[8], const int (&qsh)[8], int count, T *out) {
+        const uint32_t *s32 = (const uint32_t *)src;
+        uint32_t b[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int q = bit[j] & 255;
-            const uint64_t w = (q & 128) ? ((q & 64) ? w3 : w2) : ((q & 64) ? w1 : w0);
-            v[j] = ((w >> (q & 63)) & 1) ? one : (T)0;
-        }
+        for (int j = 0; j < 8; ++j) b[j] = (s32[qw[j]] >> qsh[j]) & 1u;
         if (e0 + 8 <= count && ((uintptr_t)(out + e0) & (8 * sizeof(T) - 1)) == 0) {
             if constexpr (sizeof(T) == 1) {
                 uint2 pk;
-                pk.x = (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16) | ((uint32_t)v[3] << 24);
-                pk.y = (uint32_t)v[4] | ((uint32_t)v[5] << 8) | ((uint32_t)v[6] << 16) | ((uint32_t)v[7] << 24);
+                pk.x = (b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24)) * (uint32_t)one;
+                pk.y = (b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24)) * (uint32_t)one;
                 *(uint2 *)(out + e0) = pk;
             } else {
                 uint4 pk;
-                pk.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
-                pk.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
-                pk.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
-                pk.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
+                pk.x = (b[0] | (b[1] << 16)) * (uint32_t)one;
+                pk.y = (b[2] | (b[3] << 16)) * (uint32_t)one;
+                pk.z = (b[4] | (b[5] << 16)) * (uint32_t)one;
+                pk.w = (b[6] | (b[7] << 16)) * (uint32_t)one;
                 *(uint4 *)(out + e0) = pk;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                if (e0 + j < count) out[e0 + j] = v[j];
+                if (e0 + j < count) out[e0 + j] = b[j] ? one : (T)0;
         }
     };
     if (e0 < r) {
-        int q[8];
+        int qw[8], qsh[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) q[j] = e0 + j < r ? sortedSlot[e0 + j] : 0;
+        for (int j = 0; j < 8; ++j) {
+            const int q = e0 + j < r ? sortedSlot[e0 + j] : 0;
+            qw[j] = q >> 5;
+            qsh[j] = q & 31;
+        }
         // M[l][s] = coefficient of pivot row rho_s in echelon row l
-        for (int l = warp; l < r; l += nwarp) emit(tw + slotRow[l] * W, q, r, Mo + (int64_t)l * ldm);
+        for (int l = warp; l < r; l += nwarp) emit(tw + slotRow[l] * W, qw, qsh, r, Mo + (int64_t)l * ldm);
         // K[t][s] for the non-pivot rows t
         for (int row = warp; row < alpha; row += nwarp)
-            if (!piv[row]) emit(tw + row * W, q, r, Ko + (int64_t)pivpos[row] * ldk);
+            if (!piv[row]) emit(tw + row * W, qw, qsh, r, Ko + (int64_t)pivpos[row] * ldk);
     }
     // R[l][j] = entry of echelon row l in the j-th non-pivot column
     const int nr = beta - r;
     if (e0 < nr) {
-        int c[8];
+        int qw[8], qsh[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) c[j] = e0 + j < nr ? nonCol[e0 + j] : 0;
-        for (int l = warp; l < r; l += nwarp) emit(hw + slotRow[l] * W, c, nr, Ro + (int64_t)l * ldr);
+        for (int j = 0; j < 8; ++j) {
+            const int c = e0 + j < nr ? nonCol[e0 + j] : 0;
+            qw[j] = c >> 5;
+            qsh[j] = c & 31;
+        }
+        for (int l = warp; l < r; l += nwarp) emit(hw + slotRow[l] * W, qw, qsh, nr, Ro + (int64_t)l * ldr);
     }
 }
 
