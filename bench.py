@@ -54,9 +54,11 @@ def parse():
                     help="run only the GF(2) multiply-add comparison: bit-packed M4RM kernel vs the e4m3 tensor-core "
                          "kernel per shape, with the measured LOP3 and shared-memory load peaks")
     ap.add_argument("--single", type=int, default=0,
-                    help="profiling run: one GF(2) matrix of side N (uniform, or --twin), one untimed and one "
+                    help="profiling run: one matrix of N rows (GF(2) unless --p; uniform, or --twin), one untimed and one "
                          "counted call; prints the library's launch counts and algorithmic work")
     ap.add_argument("--twin", action="store_true", help="with --single: the rank-0.75n twin")
+    ap.add_argument("--p", type=int, default=2, help="with --single: the field (uint8 storage for p > 2)")
+    ap.add_argument("--cols", type=int, default=0, help="with --single: columns (0: square)")
     ap.add_argument("--block", type=int, default=0, help="with --single: top-level block side (0: the table)")
     ap.add_argument("--side-tiles", type=int, default=-1,
                     help="with --single: tiles per CTA of the planner's side-stream multiply-adds (-1: default)")
@@ -575,30 +577,33 @@ def run_single(args, dev):
     import collections
     import torch
     from paper_1806_04211_gb300 import gfe, synth
-    n = args.single
+    m, p = args.single, args.p
+    n = args.cols or m
     if args.block:
         gfe.set_block_policy(args.block, args.block)
     if args.side_tiles >= 0:
         gfe._check(gfe.lib().gfe_set_side_tiles(args.side_tiles))
-    A = synth.matrix(2, n, n, seed=1, rank=(3 * n) // 4 if args.twin else None, device=dev)
-    gfe.batch_echelon([(A, 2, n)], workers=1)
+    A = synth.matrix(p, m, n, seed=1, rank=(3 * min(m, n)) // 4 if args.twin else None, device=dev)
+    arg = (A, p, n) if p == 2 else (A, p)
+    gfe.batch_echelon([arg], workers=1)
     torch.cuda.synchronize()
     gfe.profile_enable(True, kinds=["other"])  # counts only: no kind is timed
     gfe.profile_read(True)
     t = time.perf_counter()
-    d = gfe.batch_echelon([(A, 2, n)], workers=1)
+    d = gfe.batch_echelon([arg], workers=1)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     pr = gfe.profile_read(True)
     gfe.profile_enable(False)
-    out = {"n": n, "rank": d[0]["rank"], "block": args.block or gfe.lib().gfe_auto_block(2, n, n), "seconds": dt,
+    out = {"p": p, "m": m, "n": n, "rank": d[0]["rank"], "block": args.block or gfe.lib().gfe_auto_block(p, m, n),
+           "seconds": dt, "madds_per_s": float(m) * n * d[0]["rank"] / dt,
            "launches": pr["launches"], "madds": pr["madds"], "algorithmic_bytes": pr["bytes"],
            "host_syncs": pr["host_syncs"]}
     if args.trace:
         gfe.profile_enable(True)
         gfe.profile_read(True)
         gfe.trace_enable(1 << 21)
-        gfe.batch_echelon([(A, 2, n)], workers=1)
+        gfe.batch_echelon([arg], workers=1)
         torch.cuda.synchronize()
         tr = gfe.trace_read(True)
         gfe.trace_enable(0)

@@ -399,92 +399,111 @@ __device__ __forceinline__ float fred(float x, float p, float invp) {
 // fp32 integers in registers, so an update is one exact fma.  Rows start as
 // residues below p and gain less than p^2 per pivot step, so after the at
 // most 64 steps of a leaf every value is below 64 p^2 + p < 2^24 and no row
-// is reduced before the end.  The published pivot row is reduced and scaled
-// by -1/pivot lane-parallel (lane l takes entries l, l+32, l+64, l+96) into
-// a warp-private buffer; rows then add v times it over the columns >= c and
-// the slots <= the new one only (jump tables into unrolled runs of 4).
-// 128 fp32 registers per row: at most F32_LEAF_ROWS rows.
+// is reduced before the end.
+// Two threads per row (adjacent lanes): thread half hf holds columns
+// 32 hf .. 32 hf + 31 and slots 32 hf .. 32 hf + 31, so a row's update is
+// split in two and twice as many warps hide each other's latency.  The half
+// that holds column c computes the row's entry there and passes it to its
+// partner by a shuffle.  The published candidate row is written by both
+// halves; the pivot row is reduced and scaled by -1/pivot lane-parallel
+// (lane l takes entries l, l+32, l+64, l+96) into a warp-private buffer;
+// rows then add v times it over the columns >= c and the slots <= the new
+// one only (jump tables into runs of 4).  At most F32_LEAF_ROWS rows.
 // ---------------------------------------------------------------------------
+#define GFE_CASE8(M) M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7)
+#define GFE_RCASE8(M) M(7) M(6) M(5) M(4) M(3) M(2) M(1) M(0)
+#define GFE_CASE32(M) GFE_CASE16(M) M(16) M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31)
+constexpr int F32_THREADS = 2 * F32_LEAF_ROWS;
 template <int C>
-__global__ void __launch_bounds__(F32_LEAF_ROWS, 1) k_ech_leaf_f32(int p, int alpha, int beta,
-                                                                const typename Cd<C>::T *H, int64_t ldh,
-                                                                int32_t *info, typename Cd<C>::T *Mo,
-                                                                int64_t ldm, typename Cd<C>::T *Ko,
-                                                                int64_t ldk, typename Cd<C>::T *Ro,
-                                                                int64_t ldr) {
+__global__ void __launch_bounds__(F32_THREADS, 1) k_ech_leaf_f32(int p, int alpha, int beta,
+                                                              const typename Cd<C>::T *H, int64_t ldh,
+                                                              int32_t *info, typename Cd<C>::T *Mo,
+                                                              int64_t ldm, typename Cd<C>::T *Ko,
+                                                              int64_t ldk, typename Cd<C>::T *Ro,
+                                                              int64_t ldr) {
     using D = Cd<C>;
     extern __shared__ uint8_t sm[];
-    uint8_t *S = sm;                           // [threads][LS]  residues of H (load / output)
-    uint8_t *Tt = sm + blockDim.x * LS;        // [threads][LS]  slot coefficients (output)
+    const int rows_cap = blockDim.x >> 1;
+    uint8_t *S = sm;                           // [rows_cap][LS]  residues of H (load / output)
+    uint8_t *Tt = sm + rows_cap * LS;          // [rows_cap][LS]  slot coefficients (output)
     __shared__ uint8_t inv[256];
     __shared__ uint8_t piv[F32_LEAF_ROWS];
     __shared__ int16_t slotOf[F32_LEAF_ROWS];
     __shared__ int16_t pivpos[F32_LEAF_ROWS];
     __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
-    __shared__ __align__(16) float wbuf[2][F32_LEAF_ROWS / 32][128];  // per warp: its first candidate row
-    __shared__ __align__(16) float prow[F32_LEAF_ROWS / 32][128];     // per warp: the reduced, scaled pivot row
+    __shared__ __align__(16) float wbuf[2][F32_THREADS / 32][128];  // per warp: its first candidate row
+    __shared__ __align__(16) float prow[F32_THREADS / 32][128];     // per warp: the reduced, scaled pivot row
     __shared__ int wmin[2][32];
     __shared__ int wsum[32];
-    const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int y = tid >> 1, hf = tid & 1;  // row, half
     const float fp = (float)p, invp = 1.0f / (float)p;
 
-    for (int q = y; q < p; q += blockDim.x) {
+    for (int q = tid; q < p; q += blockDim.x) {
         int v = 0;
         for (int x = 1; x < p; ++x)
             if ((q * x) % p == 1) v = x;
         inv[q] = (uint8_t)v;
     }
-    for (int q = y; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
-    piv[y] = 0;
-    slotOf[y] = -1;
+    for (int q = tid; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
+    if (hf == 0) {
+        piv[y] = 0;
+        slotOf[y] = -1;
+    }
+    // warp w loads rows 16 w .. 16 w + 15 (lane l: entries l and 32 + l)
 #pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) {
-        const int row = warp * 32 + rr;
+    for (int rr = 0; rr < 16; ++rr) {
+        const int row = warp * 16 + rr;
         const typename D::T *hr = H + (int64_t)row * ldh;
         const bool in = row < alpha;
         S[row * LS + lane] = in && lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
         S[row * LS + 32 + lane] = in && 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
     }
     __syncthreads();
-    float h[64], t[64];
+    float h[32], t[32];
 #pragma unroll
-    for (int k = 0; k < 64; ++k) {
-        h[k] = (float)S[y * LS + k];
+    for (int k = 0; k < 32; ++k) {
+        h[k] = (float)S[y * LS + 32 * hf + k];
         t[k] = 0.f;
     }
     bool isp = false;
     __syncthreads();
 
     int ns = 0;
+    const int mate = lane & ~1;  // lane of this row's half 0
     for (int c = 0; c < beta; ++c) {
-        const int b = c & 1;
+        const int b = c & 1, oc = c >> 5;
         float vraw = 0.f;
-        switch (c) {
+        if (hf == oc) {
+            switch (c & 31) {
 #define GFE_PICK(k) \
     case k:         \
         vraw = h[k];  \
         break;
-            GFE_CASE64(GFE_PICK)
+                GFE_CASE32(GFE_PICK)
 #undef GFE_PICK
-        default:
-            break;
+            default:
+                break;
+            }
         }
-        const float v = fred(vraw, fp, invp);
+        const float v = __shfl_sync(0xffffffffu, fred(vraw, fp, invp), mate | oc);
         const bool cand = (y < alpha) && !isp && v != 0.f;
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
-        if (lane == 0) wmin[b][warp] = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
-        if (bal && lane == __ffs(bal) - 1) {
-            float4 *dst = (float4 *)wbuf[b][warp];
+        const int first = __ffs(bal) - 1;  // an even lane (both halves agree)
+        if (lane == 0) wmin[b][warp] = bal ? warp * 16 + (first >> 1) : INT_MAX;
+        if (bal && (lane >> 1) == (first >> 1)) {
+            float4 *dh = (float4 *)(wbuf[b][warp] + 32 * hf);
+            float4 *dt = (float4 *)(wbuf[b][warp] + 64 + 32 * hf);
 #pragma unroll
-            for (int w = 0; w < 16; ++w) {
-                dst[w] = make_float4(h[4 * w], h[4 * w + 1], h[4 * w + 2], h[4 * w + 3]);
-                dst[16 + w] = make_float4(t[4 * w], t[4 * w + 1], t[4 * w + 2], t[4 * w + 3]);
+            for (int w = 0; w < 8; ++w) {
+                dh[w] = make_float4(h[4 * w], h[4 * w + 1], h[4 * w + 2], h[4 * w + 3]);
+                dt[w] = make_float4(t[4 * w], t[4 * w + 1], t[4 * w + 2], t[4 * w + 3]);
             }
         }
         __syncthreads();
         const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)wmin[b][lane]);
         if (x == INT_MAX) continue;  // uniform: column c has no pivot
-        const float *px = wbuf[b][x >> 5];
+        const float *px = wbuf[b][x >> 4];
         const float pv = fred(px[c], fp, invp);
         const int pvi = (int)pv;
         const float sc = (float)(pvi ? p - inv[pvi] : 0);  // makes the pivot -1
@@ -504,45 +523,53 @@ __global__ void __launch_bounds__(F32_LEAF_ROWS, 1) k_ech_leaf_f32(int p, int al
         const float g = me ? 1.f : v;
         if (me) {
 #pragma unroll
-            for (int k = 0; k < 64; ++k) h[k] = t[k] = 0.f;
+            for (int k = 0; k < 32; ++k) h[k] = t[k] = 0.f;
             isp = true;
-            piv[y] = 1;
-            slotOf[y] = (int16_t)ns;
-            slotRow[ns] = (int16_t)y;
-            slotCol[ns] = (int16_t)c;
+            if (hf == 0) {
+                piv[y] = 1;
+                slotOf[y] = (int16_t)ns;
+                slotRow[ns] = (int16_t)y;
+                slotCol[ns] = (int16_t)c;
+            }
         }
         const float4 *pr = (const float4 *)prow[warp];
-        // columns from c's group of four on (the pivot row is zero left of c)
-        switch (c >> 2) {
+        // this half's columns from c's group of four on (the pivot row is zero left of c)
+        const int hstart = c - 32 * hf;  // first local column that may change
+        if (hstart < 32) {
+            switch (hstart < 0 ? 0 : hstart >> 2) {
 #define GFE_HUPD(k)                                     \
     case k: {                                           \
-        const float4 q4 = pr[k];                        \
+        const float4 q4 = pr[8 * hf + k];               \
         h[4 * k] = fmaf(g, q4.x, h[4 * k]);             \
         h[4 * k + 1] = fmaf(g, q4.y, h[4 * k + 1]);     \
         h[4 * k + 2] = fmaf(g, q4.z, h[4 * k + 2]);     \
         h[4 * k + 3] = fmaf(g, q4.w, h[4 * k + 3]);     \
     }                                                   \
         [[fallthrough]];
-            GFE_CASE16(GFE_HUPD)
+                GFE_CASE8(GFE_HUPD)
 #undef GFE_HUPD
-        default:
-            break;
+            default:
+                break;
+            }
         }
-        // slots up to ns's group of four (the pivot row's later slots are zero)
-        switch (ns >> 2) {
+        // this half's slots up to ns's group of four (the pivot row's later slots are zero)
+        const int tlast = ns - 32 * hf;  // last local slot that may change
+        if (tlast >= 0) {
+            switch (tlast > 31 ? 7 : tlast >> 2) {
 #define GFE_TUPD(k)                                     \
     case k: {                                           \
-        const float4 q4 = pr[16 + k];                   \
+        const float4 q4 = pr[16 + 8 * hf + k];          \
         t[4 * k] = fmaf(g, q4.x, t[4 * k]);             \
         t[4 * k + 1] = fmaf(g, q4.y, t[4 * k + 1]);     \
         t[4 * k + 2] = fmaf(g, q4.z, t[4 * k + 2]);     \
         t[4 * k + 3] = fmaf(g, q4.w, t[4 * k + 3]);     \
     }                                                   \
         [[fallthrough]];
-            GFE_RCASE16(GFE_TUPD)
+                GFE_RCASE8(GFE_TUPD)
 #undef GFE_TUPD
-        default:
-            break;
+            default:
+                break;
+            }
         }
         __syncwarp();  // prow is rewritten at the next pivot
         ++ns;
@@ -550,19 +577,20 @@ __global__ void __launch_bounds__(F32_LEAF_ROWS, 1) k_ech_leaf_f32(int p, int al
     const int r = ns;
     // reduced rows back to shared memory for the (coalesced) output phase
 #pragma unroll
-    for (int k = 0; k < 64; ++k) {
-        S[y * LS + k] = (uint8_t)fred(h[k], fp, invp);
-        Tt[y * LS + k] = (uint8_t)fred(t[k], fp, invp);
+    for (int k = 0; k < 32; ++k) {
+        S[y * LS + 32 * hf + k] = (uint8_t)fred(h[k], fp, invp);
+        Tt[y * LS + 32 * hf + k] = (uint8_t)fred(t[k], fp, invp);
     }
     // rank of each row among pivot rows (ascending) and among non-pivot rows
-    const int isp_i = (y < alpha) && isp;
+    // (half 0 of each row counts)
+    const int isp_i = (y < alpha) && isp && hf == 0;
     unsigned bal = __ballot_sync(0xffffffffu, isp_i);
     if (lane == 0) wsum[warp] = __popc(bal);
     __syncthreads();
     int before = 0;
     for (int w = 0; w < warp; ++w) before += wsum[w];
     before += __popc(bal & ((1u << lane) - 1));
-    if (y < alpha) {
+    if (y < alpha && hf == 0) {
         if (isp_i) {
             pivpos[y] = (int16_t)before;
             sortedSlot[before] = slotOf[y];
@@ -571,9 +599,9 @@ __global__ void __launch_bounds__(F32_LEAF_ROWS, 1) k_ech_leaf_f32(int p, int al
             pivpos[y] = (int16_t)(y - before);
         }
     }
-    if (y == 0) info[0] = r;
-    for (int c = y; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
-    if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
+    if (tid == 0) info[0] = r;
+    for (int c = tid; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
+    if (tid < r) info[1 + ECH_LEAF_COLS + tid] = slotCol[tid];
     __syncthreads();
     for (int l = warp; l < r; l += nwarp)
         for (int s = lane; s < r; s += 32)
@@ -1007,8 +1035,9 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
             cudaFuncSetAttribute(k_ech_leaf_f32<CODEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
                                  2 * F32_LEAF_ROWS * LS);                                                         \
         });                                                                                                       \
-        k_ech_leaf_f32<CODEC><<<1, threads, smem, L.st>>>(L.p, (int)alpha, (int)beta, (const T *)H, ldh, info,    \
-                                                         (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);                  \
+        /* two threads per row: 2 x (rows rounded up to 32); shared rows = those rows */                         \
+        k_ech_leaf_f32<CODEC><<<1, 2 * threads, smem, L.st>>>(L.p, (int)alpha, (int)beta, (const T *)H, ldh,     \
+                                                             info, (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);        \
     } while (0)
     // pivot steps between full reductions: (p - 1) + k (p - 1)^2 <= 255
     const int lazy_k = small ? (255 - (L.p - 1)) / ((L.p - 1) * (L.p - 1)) : 0;
