@@ -12,6 +12,7 @@ import collections.abc
 import contextlib
 import ctypes
 import os
+import threading
 
 import torch
 
@@ -156,7 +157,9 @@ _ws_cache = {}
 
 
 def _workspace(nbytes: int, device) -> torch.Tensor:
-    key = (str(device),)
+    # one cached workspace per device and host thread: calls made at the same
+    # time from several threads must not share one
+    key = (str(device), threading.get_ident())
     t = _ws_cache.get(key)
     if t is None or t.numel() < nbytes:
         _ws_cache.pop(key, None)
@@ -166,7 +169,8 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
 
 
 def release_workspace() -> None:
-    """Drop the cached workspace tensors (the next call allocates afresh)."""
+    """Drop the cached workspace tensors of every thread (the next call
+    allocates afresh)."""
     _ws_cache.clear()
 
 

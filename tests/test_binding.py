@@ -47,3 +47,23 @@ def test_batch_result_shapes_follow_the_rank():
     bufs2, slots2, _ = gfe._alloc_results(args[:1], "cpu", False)
     c = gfe.BatchResult(bufs2, args[0], slots2[0], 4)
     assert "M" not in c and len(c) == 4
+
+
+def test_workspace_cache_is_per_thread():
+    """Concurrent calls from several host threads must not share a workspace."""
+    import threading
+    got = {}
+    together = threading.Barrier(3)
+
+    def grab(name):
+        got[name] = gfe._workspace(1024, "cpu")
+        together.wait()  # all three alive at once: three distinct threads
+
+    ts = [threading.Thread(target=grab, args=(i,)) for i in range(3)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    ptrs = {got[i].data_ptr() for i in range(3)}
+    assert len(ptrs) == 3
+    gfe.release_workspace()
