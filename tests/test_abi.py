@@ -117,3 +117,32 @@ def test_batch_small_policy_validation():
         gfe._check(gfe.lib().gfe_set_batch_small_max(-1, 0.0))
     gfe.set_batch_small_max(512, 1e8)
     gfe.set_batch_small_max()
+
+
+def test_solve_nullspace_and_gf2_mad_reject_bad_arguments():
+    """Argument checks that return before any CUDA call."""
+    L = gfe.lib()
+    mat = gfe.GfeMatrix(7, 10, 8, 0, None, 8)
+    rk = ctypes.c_int64(0)
+    res = gfe.GfeResult(ctypes.addressof(rk), 1, 1, 1, 8, 1, 8, 1, 8, None, 0, None, 0)
+    assert L.gfe_nullspace(ctypes.byref(mat), ctypes.byref(res), 5, 1, 16, None) == 1  # bad side
+    assert b"side" in L.gfe_last_error()
+    bad = gfe.GfeMatrix(4, 10, 8, 0, None, 8)  # 4 is not prime
+    assert L.gfe_nullspace(ctypes.byref(bad), ctypes.byref(res), 0, 1, 16, None) == 1
+    bits3 = gfe.GfeMatrix(3, 10, 8, 1, None, 8)  # GFE_BITS64 needs p = 2
+    assert L.gfe_nullspace(ctypes.byref(bits3), ctypes.byref(res), 0, 1, 16, None) == 1
+    assert L.gfe_nullspace(ctypes.byref(mat), ctypes.byref(res), 0, 1, 4, None) == 1  # ldn < m
+    assert L.gfe_solve_workspace(ctypes.byref(mat), -1) == 0
+    assert L.gfe_solve_workspace(ctypes.byref(mat), 3) > 0
+    assert L.gfe_solve(ctypes.byref(mat), ctypes.byref(res), 1, 8, -1, 1, 8, 1, 1, 1 << 20, None) == 1
+    assert L.gfe_solve(ctypes.byref(mat), ctypes.byref(res), 1, 8, 0, 1, 8, 1, 1, 1 << 20, None) == 0  # k = 0
+    assert L.gfe_solve(ctypes.byref(mat), ctypes.byref(res), 1, 8, 3, 1, 8, None, 1, 1 << 20, None) == 1
+    assert L.gfe_solve(ctypes.byref(mat), ctypes.byref(res), 1, 8, 3, 1, 8, 1, 1, 16, None) == 1  # small ws
+    assert b"workspace" in L.gfe_last_error()
+    # packed GF(2) multiply-add: pitches must be whole words covering a row
+    assert L.gfe_mad_gf2(4, 100, 70, None, 0, 1, 16, 1, 12, 1, 16, None) == 1
+    assert L.gfe_mad_gf2(4, 100, 70, None, 0, 1, 8, 1, 16, 1, 16, None) == 1
+    assert L.gfe_mad_gf2(-1, 100, 70, None, 0, 1, 16, 1, 16, 1, 16, None) == 1
+    assert L.gfe_mad_gf2(0, 100, 70, None, 0, 1, 16, 1, 16, 1, 16, None) == 0  # empty: nothing to do
+    assert L.gfe_set_side_tiles(-1) == 1 and L.gfe_set_side_tiles(2000) == 1
+    assert L.gfe_set_side_tiles(4) == 0
