@@ -384,68 +384,94 @@ __global__ void __launch_bounds__(1024, 1) k_ech_leaf_lazy(PackedMod pm, int laz
             Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
 }
 
-// x mod p for an integer-valued float 0 <= x < 2^24 (the float reciprocal
-// quotient is at most one off; the remainder is formed exactly by fma)
+// x mod p for an integer-valued float 0 <= x < 2^24 and a prime p >= 17.
+// The quotient x / p is rounded to the nearest integer by adding and
+// subtracting 1.5 * 2^23 (FMA-pipe arithmetic, no conversion instruction);
+// it is within one of the true quotient, so the remainder, formed exactly by
+// an fma, needs one correction.  Checked against integer x mod p for every
+// prime 17 <= p <= 251 and every x < 2^24, with and without the multiply and
+// add contracted into one fma.
 __device__ __forceinline__ float fred(float x, float p, float invp) {
-    const float q = floorf(x * invp);
-    float r = fmaf(-q, p, x);
-    r = r < 0.f ? r + p : r;
-    return r >= p ? r - p : r;
+    const float q = __fadd_rn(fmaf(x, invp, 12582912.0f), -12582912.0f);
+    const float r = fmaf(-q, p, x);
+    return r < 0.f ? r + p : r;
 }
 
 // ---------------------------------------------------------------------------
 // leaf ECH for 17 <= p <= 251: the same column-by-column Gauss-Jordan and
-// topmost-row rule, with a row's 64 entries and 64 slot coefficients held as
-// fp32 integers in registers, so an update is one exact fma.  Rows start as
-// residues below p and gain less than p^2 per pivot step, so after the at
-// most 64 steps of a leaf every value is below 64 p^2 + p < 2^24 and no row
-// is reduced before the end.
-// Two threads per row (adjacent lanes): thread half hf holds columns
-// 32 hf .. 32 hf + 31 and slots 32 hf .. 32 hf + 31, so a row's update is
-// split in two and twice as many warps hide each other's latency.  The half
-// that holds column c computes the row's entry there and passes it to its
-// partner by a shuffle.  The published candidate row is written by both
-// halves; the pivot row is reduced and scaled by -1/pivot lane-parallel
-// (lane l takes entries l, l+32, l+64, l+96) into a warp-private buffer;
-// rows then add v times it over the columns >= c and the slots <= the new
-// one only (jump tables into runs of 4).  At most F32_LEAF_ROWS rows.
+// topmost-row rule.  A row's 64 entries and 64 slot coefficients are fp32
+// integers in shared memory (row y at Rw[y], columns then slots); columns
+// are taken eight at a time:
+//  (A) the panel: every row's eight entries in the group's columns, reduced
+//      (written by the previous group's (D), else read from the rows);
+//  (B) the finder: the first half of the threads, one row per lane, runs the
+//      column-by-column elimination on the panel alone, one named barrier per
+//      column: each warp's topmost candidate publishes its reduced entries
+//      and the scale that makes its pivot -1, every row takes the new pivot
+//      row from the winner, and records the multiple G[y][s] of the new pivot
+//      row s added to it (one 64-bit word per row).  Then NP[s], the pivot
+//      row s as a combination of the rows Q_0 .. Q_s, Q_s being row x_s as
+//      it stood at the group start plus the identity of its slot;
+//  (C) warp s publishes Q_s, reduced, and row x_s restarts from zero; every
+//      row forms its coefficients CM_y = G[y] NP;
+//  (D) rows += CM Q, i.e. row y becomes [y is no pivot of the group] * y +
+//      sum_s CM_y[s] Q_s, on the tensor cores (mma.sync m16n8k8 with tf32
+//      operands), over the columns from the group on and the slots up to its
+//      last.
+// Rows are linear in the rows they were built from, so (D) reproduces the
+// column-by-column result; three block barriers per group.  Entries start
+// below p and grow by less than p^2 per pivot, so after the at most 64
+// pivots of a leaf they stay below 64 p^2 + p < 2^24: exact in fp32, and no
+// row is reduced before the end.  At most F32_LEAF_ROWS rows.
 // ---------------------------------------------------------------------------
-#define GFE_CASE8(M) M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7)
-#define GFE_RCASE8(M) M(7) M(6) M(5) M(4) M(3) M(2) M(1) M(0)
-#define GFE_CASE32(M) GFE_CASE16(M) M(16) M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31)
 constexpr int F32_THREADS = 2 * F32_LEAF_ROWS;
+constexpr int F32_RS = 136;  // row stride of Rw and Q (floats): the tensor-core fragments fall in distinct banks
+// dynamic shared memory of k_ech_leaf_f32 for rows_cap rows: the rows, then the byte
+// staging of the load phase
+inline int f32_leaf_smem(int rows_cap) { return rows_cap * F32_RS * 4 + rows_cap * LS; }
+
+struct InvTable {
+    uint8_t v[256];  // v[x] = x^-1 mod p (v[0] = 0)
+};
+
 template <int C>
-__global__ void __launch_bounds__(F32_THREADS, 1) k_ech_leaf_f32(int p, int alpha, int beta,
+__global__ void __launch_bounds__(F32_THREADS, 1) k_ech_leaf_f32(const __grid_constant__ InvTable it, int p,
+                                                              int alpha, int beta,
                                                               const typename Cd<C>::T *H, int64_t ldh,
                                                               int32_t *info, typename Cd<C>::T *Mo,
                                                               int64_t ldm, typename Cd<C>::T *Ko,
                                                               int64_t ldk, typename Cd<C>::T *Ro,
                                                               int64_t ldr) {
     using D = Cd<C>;
-    extern __shared__ uint8_t sm[];
-    const int rows_cap = blockDim.x >> 1;
-    uint8_t *S = sm;                           // [rows_cap][LS]  residues of H (load / output)
-    uint8_t *Tt = sm + rows_cap * LS;          // [rows_cap][LS]  slot coefficients (output)
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int rows_cap = blockDim.x >> 1;        // a multiple of 32
+    float *Rw = (float *)sm;                     // [rows_cap][F32_RS]  the rows
+    uint8_t *S = sm + rows_cap * F32_RS * 4;     // [rows_cap][LS]  residues of H (load)
     __shared__ uint8_t inv[256];
     __shared__ uint8_t piv[F32_LEAF_ROWS];
     __shared__ int16_t slotOf[F32_LEAF_ROWS];
     __shared__ int16_t pivpos[F32_LEAF_ROWS];
     __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
-    __shared__ __align__(16) float wbuf[2][F32_THREADS / 32][128];  // per warp: its first candidate row
-    __shared__ __align__(16) float prow[F32_THREADS / 32][128];     // per warp: the reduced, scaled pivot row
-    __shared__ int wmin[2][32];
+    __shared__ float panel[F32_LEAF_ROWS][9];    // the group's eight columns, reduced
+    __shared__ uint64_t Gm[F32_LEAF_ROWS];       // G[y][s] in byte s
+    __shared__ __align__(16) float NP[8][8];     // NP[s][s'] (zero for s' > s)
+    __shared__ __align__(16) float Q[8][F32_RS]; // Q_s: 64 columns, then 64 slots
+    __shared__ __align__(16) float CMs[F32_LEAF_ROWS][12];  // CM_y (stride 12: distinct banks)
+    __shared__ float cbuf[2][F32_LEAF_ROWS / 32][8];  // per warp: its topmost candidate's panel entries,
+    __shared__ uint64_t cgw[2][F32_LEAF_ROWS / 32];    // its multiples so far,
+    __shared__ float csc[2][F32_LEAF_ROWS / 32];       // the scale that makes its pivot -1
+    __shared__ uint64_t pgx[8];                        // per pivot s of the group: the multiples of x_s,
+    __shared__ float psc[8];                           // and its scale
+    __shared__ int wmin[2][F32_LEAF_ROWS / 32];        // and its row
+    __shared__ int gnp;                          // pivots in the group
     __shared__ int wsum[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    const int y = tid >> 1, hf = tid & 1;  // row, half
+    const int hf = tid >= rows_cap ? 1 : 0, y = tid - hf * rows_cap;  // half, row
     const float fp = (float)p, invp = 1.0f / (float)p;
+    float *row = Rw + y * F32_RS + 32 * hf;      // this thread's 32 columns; its slots at + 64
 
-    for (int q = tid; q < p; q += blockDim.x) {
-        int v = 0;
-        for (int x = 1; x < p; ++x)
-            if ((q * x) % p == 1) v = x;
-        inv[q] = (uint8_t)v;
-    }
-    for (int q = tid; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
+    for (int q = tid; q < 256; q += blockDim.x) inv[q] = it.v[q];
+    for (int q = tid; q < 8 * F32_RS; q += blockDim.x) Q[q / F32_RS][q % F32_RS] = 0.f;
     if (hf == 0) {
         piv[y] = 0;
         slotOf[y] = -1;
@@ -453,136 +479,206 @@ __global__ void __launch_bounds__(F32_THREADS, 1) k_ech_leaf_f32(int p, int alph
     // warp w loads rows 16 w .. 16 w + 15 (lane l: entries l and 32 + l)
 #pragma unroll 8
     for (int rr = 0; rr < 16; ++rr) {
-        const int row = warp * 16 + rr;
-        const typename D::T *hr = H + (int64_t)row * ldh;
-        const bool in = row < alpha;
-        S[row * LS + lane] = in && lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
-        S[row * LS + 32 + lane] = in && 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
+        const int r = warp * 16 + rr;
+        const typename D::T *hr = H + (int64_t)r * ldh;
+        const bool in = r < alpha;
+        S[r * LS + lane] = in && lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
+        S[r * LS + 32 + lane] = in && 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
     }
     __syncthreads();
-    float h[32], t[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        h[k] = (float)S[y * LS + 32 * hf + k];
-        t[k] = 0.f;
+    for (int k = 0; k < 32; k += 4) {
+        const uint32_t w = *(const uint32_t *)(S + y * LS + 32 * hf + k);
+        *(float4 *)(row + k) = make_float4((float)(w & 0xFF), (float)((w >> 8) & 0xFF), (float)((w >> 16) & 0xFF),
+                                           (float)(w >> 24));
+        *(float4 *)(row + 64 + k) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    bool isp = false;
     __syncthreads();
 
-    int ns = 0;
-    const int mate = lane & ~1;  // lane of this row's half 0
-    for (int c = 0; c < beta; ++c) {
-        const int b = c & 1, oc = c >> 5;
-        float vraw = 0.f;
-        if (hf == oc) {
-            switch (c & 31) {
-#define GFE_PICK(k) \
-    case k:         \
-        vraw = h[k];  \
-        break;
-                GFE_CASE32(GFE_PICK)
-#undef GFE_PICK
-            default:
-                break;
-            }
+    int ns = 0;          // pivots before the group
+    bool fresh = true;   // the panel is to be read from the rows
+    const int ngroups = (beta + 7) >> 3;
+    for (int g = 0; g < ngroups; ++g) {
+        const int c0 = 8 * g;
+        // (A) the panel: the half that holds columns c0 .. c0 + 7, unless the
+        // previous group's (D) has written it
+        if (fresh && hf == (c0 >> 5)) {
+            const float4 a = *(const float4 *)(row + (c0 & 31)), b = *(const float4 *)(row + (c0 & 31) + 4);
+            panel[y][0] = fred(a.x, fp, invp);
+            panel[y][1] = fred(a.y, fp, invp);
+            panel[y][2] = fred(a.z, fp, invp);
+            panel[y][3] = fred(a.w, fp, invp);
+            panel[y][4] = fred(b.x, fp, invp);
+            panel[y][5] = fred(b.y, fp, invp);
+            panel[y][6] = fred(b.z, fp, invp);
+            panel[y][7] = fred(b.w, fp, invp);
         }
-        const float v = __shfl_sync(0xffffffffu, fred(vraw, fp, invp), mate | oc);
-        const bool cand = (y < alpha) && !isp && v != 0.f;
-        const unsigned bal = __ballot_sync(0xffffffffu, cand);
-        const int first = __ffs(bal) - 1;  // an even lane (both halves agree)
-        if (lane == 0) wmin[b][warp] = bal ? warp * 16 + (first >> 1) : INT_MAX;
-        if (bal && (lane >> 1) == (first >> 1)) {
-            float4 *dh = (float4 *)(wbuf[b][warp] + 32 * hf);
-            float4 *dt = (float4 *)(wbuf[b][warp] + 64 + 32 * hf);
+        __syncthreads();
+        // (B) the finder: the half-0 warps, one row per lane, one named
+        // barrier per column.  Each warp's topmost candidate publishes its
+        // reduced entries and the scale that makes its pivot -1 before the
+        // barrier; after it every row takes the new pivot row from the winner.
+        if (hf == 0) {
+            float pan[8];
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                dh[w] = make_float4(h[4 * w], h[4 * w + 1], h[4 * w + 2], h[4 * w + 3]);
-                dt[w] = make_float4(t[4 * w], t[4 * w + 1], t[4 * w + 2], t[4 * w + 3]);
+            for (int k = 0; k < 8; ++k) pan[k] = panel[y][k];
+            bool cand = y < alpha && !piv[y];
+            uint64_t gw = 0;  // G[y][s] in byte s
+            int s = 0;
+            // one column per pass, the current one always in pan[0] (a short
+            // loop body: the finder runs once per group and its code is fetched
+            // each time)
+#pragma unroll 1
+            for (int k = 0; k < 8; ++k) {
+                const int b = k & 1;
+                const float v = fred(pan[0], fp, invp);
+                const bool c = c0 + k < beta && cand && v != 0.f;
+                const unsigned bal = __ballot_sync(0xffffffffu, c);
+                if (bal && lane == __ffs(bal) - 1) {  // this warp's topmost candidate
+#pragma unroll
+                    for (int j = 1; j < 8; ++j) cbuf[b][warp][j] = fred(pan[j], fp, invp);
+                    cgw[b][warp] = gw;
+                    csc[b][warp] = (float)(p - inv[(int)v]);
+                }
+                if (lane == 0) wmin[b][warp] = bal ? y + __ffs(bal) - 1 : INT_MAX;
+                asm volatile("bar.sync 1, %0;" ::"r"(rows_cap) : "memory");
+                const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)(lane < (rows_cap >> 5) ? wmin[b][lane]
+                                                                                                    : INT_MAX));
+                if (x != INT_MAX) {  // uniform: else column c0 + k has no pivot
+                    const int xw = x >> 5;
+                    const float sc = csc[b][xw];
+                    // the new pivot row's entries: lane j computes entry j & 7
+                    const float npl = fred(sc * cbuf[b][xw][lane & 7], fp, invp);
+                    // every other row adds its entry at column c0 + k times the new
+                    // pivot row; the pivot row's earlier multiples go into NP[s]
+                    const bool isx = y == x;
+#pragma unroll
+                    for (int j = 1; j < 8; ++j) {
+                        const float nj = __shfl_sync(0xffffffffu, npl, j);
+                        pan[j] = isx ? nj : fmaf(v, nj, pan[j]);
+                    }
+                    gw = isx ? 1ull << (8 * s) : (gw | ((uint64_t)(uint32_t)v << (8 * s)));
+                    cand = cand && !isx;
+                    if (tid == 0) {
+                        piv[x] = 1;
+                        slotOf[x] = (int16_t)(ns + s);
+                        slotRow[ns + s] = (int16_t)x;
+                        slotCol[ns + s] = (int16_t)(c0 + k);
+                        pgx[s] = cgw[b][xw];
+                        psc[s] = sc;
+                    }
+                    ++s;
+                }
+#pragma unroll
+                for (int j = 1; j < 8; ++j) pan[j - 1] = pan[j];
+            }
+            Gm[y] = gw;
+            if (tid == 0) gnp = s;
+            // NP[s] = sc_s (CM_(x_s) + e_s), CM_(x_s) = sum_{s' < s} G[x_s][s'] NP[s']:
+            // lane j < 8 of warp 0 forms column j
+            if (warp == 0) {
+                __syncwarp();
+                if (lane < 8) {
+                    float npc[8];
+#pragma unroll
+                    for (int s1 = 0; s1 < 8; ++s1) {
+                        float nv = 0.f;
+                        if (s1 < s) {
+                            const uint64_t gx = pgx[s1];
+                            float acc = 0.f;
+#pragma unroll
+                            for (int s2 = 0; s2 < s1; ++s2)
+                                acc = fmaf((float)(uint32_t)((gx >> (8 * s2)) & 0xFF), npc[s2], acc);
+                            acc = lane == s1 ? 1.f : (lane < s1 ? fred(acc, fp, invp) : 0.f);
+                            nv = fred(psc[s1] * acc, fp, invp);
+                        }
+                        npc[s1] = nv;
+                        NP[s1][lane] = nv;
+                    }
+                }
             }
         }
         __syncthreads();
-        const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)wmin[b][lane]);
-        if (x == INT_MAX) continue;  // uniform: column c has no pivot
-        const float *px = wbuf[b][x >> 4];
-        const float pv = fred(px[c], fp, invp);
-        const int pvi = (int)pv;
-        const float sc = (float)(pvi ? p - inv[pvi] : 0);  // makes the pivot -1
-        // lane l: entries l, l+32 (columns) and 64+l, 96+l (slots), with the
-        // pivot's own identity in slot ns, times sc
-        float e0 = fred(px[lane], fp, invp), e1 = fred(px[32 + lane], fp, invp);
-        float e2 = fred(px[64 + lane], fp, invp), e3 = fred(px[96 + lane], fp, invp);
-        if (lane == ns) e2 += 1.f;
-        if (lane + 32 == ns) e3 += 1.f;
-        prow[warp][lane] = fred(e0 * sc, fp, invp);
-        prow[warp][32 + lane] = fred(e1 * sc, fp, invp);
-        prow[warp][64 + lane] = fred(e2 * sc, fp, invp);
-        prow[warp][96 + lane] = fred(e3 * sc, fp, invp);
-        __syncwarp();
-        // the pivot row becomes that row; every other row adds v times it
-        const bool me = (y == x);
-        const float g = me ? 1.f : v;
-        if (me) {
+        const int nsg = gnp;
+        fresh = nsg == 0;
+        if (nsg == 0) continue;  // uniform
+        // (C) warp s publishes Q_s from pivot row x_s, which then restarts from
+        // zero; every row forms its coefficients
+        for (int sq = warp; sq < nsg; sq += nwarp) {
+            const int xs = slotRow[ns + sq], own = 64 + ns + sq;  // the identity of its slot
+            float *rx = Rw + xs * F32_RS + 4 * lane;
+            const float4 a = *(const float4 *)rx;
+            *(float4 *)(Q[sq] + 4 * lane) = make_float4(
+                fred(a.x, fp, invp) + (own == 4 * lane ? 1.f : 0.f), fred(a.y, fp, invp) + (own == 4 * lane + 1 ? 1.f : 0.f),
+                fred(a.z, fp, invp) + (own == 4 * lane + 2 ? 1.f : 0.f), fred(a.w, fp, invp) + (own == 4 * lane + 3 ? 1.f : 0.f));
+            *(float4 *)rx = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (hf == 0) {  // CM_y = G[y] NP, reduced
+            const uint64_t gy = Gm[y];
+            float acc[8];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) h[k] = t[k] = 0.f;
-            isp = true;
-            if (hf == 0) {
-                piv[y] = 1;
-                slotOf[y] = (int16_t)ns;
-                slotRow[ns] = (int16_t)y;
-                slotCol[ns] = (int16_t)c;
+            for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+#pragma unroll
+            for (int s2 = 0; s2 < 8; ++s2) {
+                if (s2 < nsg) {
+                    const float gv = (float)(uint32_t)((gy >> (8 * s2)) & 0xFF);
+                    const float4 a = *(const float4 *)NP[s2], b = *(const float4 *)(NP[s2] + 4);
+                    acc[0] = fmaf(gv, a.x, acc[0]);
+                    acc[1] = fmaf(gv, a.y, acc[1]);
+                    acc[2] = fmaf(gv, a.z, acc[2]);
+                    acc[3] = fmaf(gv, a.w, acc[3]);
+                    acc[4] = fmaf(gv, b.x, acc[4]);
+                    acc[5] = fmaf(gv, b.y, acc[5]);
+                    acc[6] = fmaf(gv, b.z, acc[6]);
+                    acc[7] = fmaf(gv, b.w, acc[7]);
+                }
+            }
+            *(float4 *)CMs[y] = make_float4(fred(acc[0], fp, invp), fred(acc[1], fp, invp), fred(acc[2], fp, invp),
+                                            fred(acc[3], fp, invp));
+            *(float4 *)(CMs[y] + 4) = make_float4(fred(acc[4], fp, invp), fred(acc[5], fp, invp), fred(acc[6], fp, invp),
+                                                  fred(acc[7], fp, invp));
+        }
+        __syncthreads();
+        // (D) rows += CM Q on the tensor cores (mma.sync m16n8k8, tf32 operands:
+        // CM and Q are residues below 2^8, exact in tf32; the rows stay below
+        // 2^24, exact in the fp32 accumulator), over the 8-column tiles from
+        // the group on and the 8-slot tiles up to its last slot.  Warp w takes
+        // rows 16 w .. 16 w + 15; its tile of columns c0 + 8 .. c0 + 15 also
+        // writes the next group's panel.
+        {
+            const int gid = lane >> 2, tig = lane & 3, r0 = 16 * warp;
+            const int nth = 8 - g, nt = nth + ((ns + nsg + 7) >> 3);  // column tiles, all tiles
+            const uint32_t a0 = __float_as_uint(CMs[r0 + gid][tig]), a1 = __float_as_uint(CMs[r0 + gid + 8][tig]),
+                           a2 = __float_as_uint(CMs[r0 + gid][tig + 4]), a3 = __float_as_uint(CMs[r0 + gid + 8][tig + 4]);
+#pragma unroll 4
+            for (int t2 = 0; t2 < nt; ++t2) {
+                const int off = t2 < nth ? 8 * (g + t2) : 64 + 8 * (t2 - nth);
+                const uint32_t b0 = __float_as_uint(Q[tig][off + gid]), b1 = __float_as_uint(Q[tig + 4][off + gid]);
+                float2 *c01 = (float2 *)(Rw + (r0 + gid) * F32_RS + off + 2 * tig);
+                float2 *c23 = (float2 *)(Rw + (r0 + gid + 8) * F32_RS + off + 2 * tig);
+                float2 u = *c01, w = *c23;
+                asm volatile(
+                    "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+                    "{%0, %1, %2, %3};"
+                    : "+f"(u.x), "+f"(u.y), "+f"(w.x), "+f"(w.y)
+                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                *c01 = u;
+                *c23 = w;
+                if (t2 == 1 && nth > 1) {
+                    panel[r0 + gid][2 * tig] = fred(u.x, fp, invp);
+                    panel[r0 + gid][2 * tig + 1] = fred(u.y, fp, invp);
+                    panel[r0 + gid + 8][2 * tig] = fred(w.x, fp, invp);
+                    panel[r0 + gid + 8][2 * tig + 1] = fred(w.y, fp, invp);
+                }
             }
         }
-        const float4 *pr = (const float4 *)prow[warp];
-        // this half's columns from c's group of four on (the pivot row is zero left of c)
-        const int hstart = c - 32 * hf;  // first local column that may change
-        if (hstart < 32) {
-            switch (hstart < 0 ? 0 : hstart >> 2) {
-#define GFE_HUPD(k)                                     \
-    case k: {                                           \
-        const float4 q4 = pr[8 * hf + k];               \
-        h[4 * k] = fmaf(g, q4.x, h[4 * k]);             \
-        h[4 * k + 1] = fmaf(g, q4.y, h[4 * k + 1]);     \
-        h[4 * k + 2] = fmaf(g, q4.z, h[4 * k + 2]);     \
-        h[4 * k + 3] = fmaf(g, q4.w, h[4 * k + 3]);     \
-    }                                                   \
-        [[fallthrough]];
-                GFE_CASE8(GFE_HUPD)
-#undef GFE_HUPD
-            default:
-                break;
-            }
-        }
-        // this half's slots up to ns's group of four (the pivot row's later slots are zero)
-        const int tlast = ns - 32 * hf;  // last local slot that may change
-        if (tlast >= 0) {
-            switch (tlast > 31 ? 7 : tlast >> 2) {
-#define GFE_TUPD(k)                                     \
-    case k: {                                           \
-        const float4 q4 = pr[16 + 8 * hf + k];          \
-        t[4 * k] = fmaf(g, q4.x, t[4 * k]);             \
-        t[4 * k + 1] = fmaf(g, q4.y, t[4 * k + 1]);     \
-        t[4 * k + 2] = fmaf(g, q4.z, t[4 * k + 2]);     \
-        t[4 * k + 3] = fmaf(g, q4.w, t[4 * k + 3]);     \
-    }                                                   \
-        [[fallthrough]];
-                GFE_RCASE8(GFE_TUPD)
-#undef GFE_TUPD
-            default:
-                break;
-            }
-        }
-        __syncwarp();  // prow is rewritten at the next pivot
-        ++ns;
+        ns += nsg;
     }
+    __syncthreads();  // rows were last written by the warps of their tiles
     const int r = ns;
-    // reduced rows back to shared memory for the (coalesced) output phase
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        S[y * LS + 32 * hf + k] = (uint8_t)fred(h[k], fp, invp);
-        Tt[y * LS + 32 * hf + k] = (uint8_t)fred(t[k], fp, invp);
-    }
+    const bool isp = piv[y] != 0;
     // rank of each row among pivot rows (ascending) and among non-pivot rows
-    // (half 0 of each row counts)
+    // (the half-0 warps count: warp w holds rows 32 w .. 32 w + 31)
     const int isp_i = (y < alpha) && isp && hf == 0;
     unsigned bal = __ballot_sync(0xffffffffu, isp_i);
     if (lane == 0) wsum[warp] = __popc(bal);
@@ -603,20 +699,28 @@ __global__ void __launch_bounds__(F32_THREADS, 1) k_ech_leaf_f32(int p, int alph
     for (int c = tid; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
     if (tid < r) info[1 + ECH_LEAF_COLS + tid] = slotCol[tid];
     __syncthreads();
-    for (int l = warp; l < r; l += nwarp)
-        for (int s = lane; s < r; s += 32)
-            Mo[(int64_t)l * ldm + s] = D::enc(cen(Tt[slotRow[l] * LS + sortedSlot[s]], p));
-    if (r > 0) {
-        for (int row = warp; row < alpha; row += nwarp) {
-            if (piv[row]) continue;
-            for (int s = lane; s < r; s += 32)
-                Ko[(int64_t)pivpos[row] * ldk + s] = D::enc(cen(Tt[row * LS + sortedSlot[s]], p));
-        }
-    }
+    // the outputs, reduced and centred, straight from the rows: lane l writes
+    // output columns l and l + 32 (their row entries found once)
+    using T = typename D::T;
     const int nr = beta - r;
-    for (int l = warp; l < r; l += nwarp)
-        for (int j = lane; j < nr; j += 32)
-            Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
+    const int sa = lane < r ? 64 + sortedSlot[lane] : -1, sb = lane + 32 < r ? 64 + sortedSlot[lane + 32] : -1;
+    const int ca = lane < nr ? nonCol[lane] : -1, cb = lane + 32 < nr ? nonCol[lane + 32] : -1;
+    auto put = [&](T *dst, const float *rw, int e) {
+        if (e >= 0) *dst = D::enc(cen((int)fred(rw[e], fp, invp), p));
+    };
+    for (int l = warp; l < r; l += nwarp) {  // M and R: the pivot rows in slot order
+        const float *rw = Rw + slotRow[l] * F32_RS;
+        put(Mo + (int64_t)l * ldm + lane, rw, sa);
+        put(Mo + (int64_t)l * ldm + lane + 32, rw, sb);
+        put(Ro + (int64_t)l * ldr + lane, rw, ca);
+        put(Ro + (int64_t)l * ldr + lane + 32, rw, cb);
+    }
+    for (int rw = warp; rw < alpha; rw += nwarp) {  // K: the other rows
+        if (piv[rw]) continue;
+        T *ko = Ko + (int64_t)pivpos[rw] * ldk;
+        put(ko + lane, Rw + rw * F32_RS, sa);
+        put(ko + lane + 32, Rw + rw * F32_RS, sb);
+    }
 }
 
 static PackedMod packed_mod(int p) {
@@ -1018,6 +1122,12 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
     const int smem_max = 2 * 1024 * LS, smem = 2 * threads * LS;
     const PackedMod pm = packed_mod(L.p);
     const bool small = L.p <= 13;
+    InvTable it{};
+    if (!small) {  // inverses mod p by x^-1 = -(p / x) * (p mod x)^-1
+        it.v[1] = 1;
+        for (int x = 2; x < L.p; ++x)
+            it.v[x] = (uint8_t)((L.p - (L.p / x) * it.v[L.p % x] % L.p) % L.p);
+    }
     static std::once_flag once2[4];
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
@@ -1033,11 +1143,11 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
     do {                                                                                                          \
         std::call_once(once2[IDX], [&] {                                                                          \
             cudaFuncSetAttribute(k_ech_leaf_f32<CODEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                                 2 * F32_LEAF_ROWS * LS);                                                         \
+                                 f32_leaf_smem(F32_LEAF_ROWS));                                                   \
         });                                                                                                       \
-        /* two threads per row: 2 x (rows rounded up to 32); shared rows = those rows */                         \
-        k_ech_leaf_f32<CODEC><<<1, 2 * threads, smem, L.st>>>(L.p, (int)alpha, (int)beta, (const T *)H, ldh,     \
-                                                             info, (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);        \
+        /* two threads per row: 2 x (rows rounded up to 32) */                                                    \
+        k_ech_leaf_f32<CODEC><<<1, 2 * threads, f32_leaf_smem(threads), L.st>>>(                                   \
+            it, L.p, (int)alpha, (int)beta, (const T *)H, ldh, info, (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);       \
     } while (0)
     // pivot steps between full reductions: (p - 1) + k (p - 1)^2 <= 255
     const int lazy_k = small ? (255 - (L.p - 1)) / ((L.p - 1) * (L.p - 1)) : 0;
