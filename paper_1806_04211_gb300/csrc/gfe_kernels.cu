@@ -8,6 +8,7 @@
 #include <type_traits>
 
 #include <climits>
+#include <cuda_fp16.h>
 #include <mutex>
 
 namespace gfe {
@@ -162,35 +163,6 @@ void mad(const Launch &L, int64_t m, int64_t n, int64_t k, const void *W, int64_
 // ---------------------------------------------------------------------------
 constexpr int LS = 68;  // smem row stride (bytes): 17 words -> conflict-free rows
 
-// Byte-wise arithmetic mod p (p <= 13) on four residues per 32-bit word:
-// the quotient of each byte (<= 255) comes from a Barrett step on the even
-// and odd bytes (two 16-bit lanes each), never too large and at most one too
-// small, fixed by one byte-wise compare (__vcmpgeu4).
-struct PackedMod {
-    uint32_t p, pp;     // p, and p in every byte
-    uint32_t M, S, QM;  // Barrett multiplier, shift, mask of the quotient bits
-    float invp;
-};
-
-// register-resident packed rows: word w of a 16-word array, static indices
-#define GFE_CASE16(M)                                                                                     \
-    M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15)
-#define GFE_RCASE16(M)                                                                                    \
-    M(15) M(14) M(13) M(12) M(11) M(10) M(9) M(8) M(7) M(6) M(5) M(4) M(3) M(2) M(1) M(0)
-#define GFE_CASE64(M) M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31) M(32) M(33) M(34) M(35) M(36) M(37) M(38) M(39) M(40) M(41) M(42) M(43) M(44) M(45) M(46) M(47) M(48) M(49) M(50) M(51) M(52) M(53) M(54) M(55) M(56) M(57) M(58) M(59) M(60) M(61) M(62) M(63)
-
-// word i of a register array: a select tree of depth 4 (not a chain of 15)
-__device__ __forceinline__ uint32_t pick16(const uint32_t (&a)[16], int i) {
-    uint32_t l1[8], l2[4], l3[2];
-#pragma unroll
-    for (int w = 0; w < 8; ++w) l1[w] = (i & 1) ? a[2 * w + 1] : a[2 * w];
-#pragma unroll
-    for (int w = 0; w < 4; ++w) l2[w] = (i & 2) ? l1[2 * w + 1] : l1[2 * w];
-#pragma unroll
-    for (int w = 0; w < 2; ++w) l3[w] = (i & 4) ? l2[2 * w + 1] : l2[2 * w];
-    return (i & 8) ? l3[1] : l3[0];
-}
-
 // column c's place among the non-pivot columns: slotCol holds the r pivot
 // columns in ascending order (pivots are found column by column)
 __device__ __forceinline__ void place_non_pivot(const int16_t *slotCol, int r, int c, int16_t *nonCol) {
@@ -203,194 +175,14 @@ __device__ __forceinline__ void place_non_pivot(const int16_t *slotCol, int r, i
     if (lo >= r || slotCol[lo] != c) nonCol[c - lo] = (int16_t)c;
 }
 
-// Byte-wise reduction mod p of four packed values <= 255 (p <= 13).
-__device__ __forceinline__ uint32_t preduce(uint32_t x, const PackedMod &q) {
-    const uint32_t lo = x & 0x00FF00FFu, hi = (x >> 8) & 0x00FF00FFu;
-    const uint32_t qq = (((lo * q.M) >> q.S) & q.QM) | ((((hi * q.M) >> q.S) & q.QM) << 8);
-    const uint32_t r = x - qq * q.p;
-    return r - (__vcmpgeu4(r, q.pp) & q.pp);
-}
-
-// ---------------------------------------------------------------------------
-// leaf ECH for small p (3 <= p <= 13) with lazy reduction: the same
-// column-by-column Gauss-Jordan and topmost-row rule as k_ech_leaf, but a
-// row update is one integer multiply-add per packed word, a += v * s with
-// v < p and s < p in every byte, and rows are reduced mod p only every
-// `lazy_k` pivot steps, lazy_k = floor((255 - (p - 1)) / (p - 1)^2), so no
-// byte ever exceeds 255.  The pivot row is published unreduced; every warp
-// reduces it and scales it by -1/pivot lane-parallel (lane w takes word w)
-// and passes the words to its lanes through a warp-private buffer.
-// ---------------------------------------------------------------------------
-template <int C>
-__global__ void __launch_bounds__(1024, 1) k_ech_leaf_lazy(PackedMod pm, int lazy_k, int alpha, int beta,
-                                                           const typename Cd<C>::T *H, int64_t ldh,
-                                                           int32_t *info, typename Cd<C>::T *Mo,
-                                                           int64_t ldm, typename Cd<C>::T *Ko,
-                                                           int64_t ldk, typename Cd<C>::T *Ro,
-                                                           int64_t ldr) {
-    using D = Cd<C>;
-    extern __shared__ uint8_t sm[];
-    uint8_t *S = sm;                           // [threads][LS]  residues of H (load / output)
-    uint8_t *Tt = sm + blockDim.x * LS;        // [threads][LS]  slot coefficients (output)
-    __shared__ uint8_t inv[16];
-    __shared__ uint8_t piv[1024];
-    __shared__ int16_t slotOf[1024];
-    __shared__ int16_t pivpos[1024];
-    __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
-    __shared__ __align__(16) uint32_t wbuf[2][32][32];
-    __shared__ __align__(16) uint32_t prow[32][32];  // per warp: the reduced, scaled pivot row
-    __shared__ int wmin[2][32];
-    __shared__ int wsum[32];
-    const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
-    const int p = (int)pm.p;
-    const uint32_t mv = (65536u + (uint32_t)p - 1) / (uint32_t)p;  // v mod p = v - ((v * mv) >> 16) * p, v <= 255
-
-    for (int q = y; q < p; q += blockDim.x) {
-        int v = 0;
-        for (int x = 1; x < p; ++x)
-            if ((q * x) % p == 1) v = x;
-        inv[q] = (uint8_t)v;
-    }
-    for (int q = y; q < 64; q += blockDim.x) wmin[q >> 5][q & 31] = INT_MAX;  // warps not launched
-    piv[y] = 0;
-    slotOf[y] = -1;
-#pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) {
-        const int row = warp * 32 + rr;
-        const typename D::T *hr = H + (int64_t)row * ldh;
-        const bool in = row < alpha;
-        S[row * LS + lane] = in && lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
-        S[row * LS + 32 + lane] = in && 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
-    }
-    __syncthreads();
-    uint32_t h[16], t[16];
-#pragma unroll
-    for (int w = 0; w < 16; ++w) {
-        h[w] = *(const uint32_t *)(S + y * LS + 4 * w);
-        t[w] = 0;
-    }
-    bool isp = false;
-    __syncthreads();
-
-    int ns = 0, since = 0;  // pivots so far; pivot steps since the last full reduction
-    for (int c = 0; c < beta; ++c) {
-        const int b = c & 1, wc = c >> 2, bc = 8 * (c & 3);
-        const uint32_t vraw = (pick16(h, wc) >> bc) & 0xFF;
-        const uint32_t v = vraw - ((vraw * mv) >> 16) * (uint32_t)p;
-        const bool cand = (y < alpha) && !isp && v != 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, cand);
-        if (lane == 0) wmin[b][warp] = bal ? warp * 32 + __ffs(bal) - 1 : INT_MAX;
-        if (bal && lane == __ffs(bal) - 1) {
-            uint4 *dst = (uint4 *)wbuf[b][warp];
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                dst[w] = make_uint4(h[4 * w], h[4 * w + 1], h[4 * w + 2], h[4 * w + 3]);
-                dst[4 + w] = make_uint4(t[4 * w], t[4 * w + 1], t[4 * w + 2], t[4 * w + 3]);
-            }
-        }
-        __syncthreads();
-        const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)wmin[b][lane]);
-        if (x == INT_MAX) continue;  // uniform: column c has no pivot
-        // lane w: word w of the pivot row (h words 0..15, then t words),
-        // reduced, with the pivot's own identity in slot ns, times -1/pivot
-        const uint32_t *px = wbuf[b][x >> 5];
-        const uint32_t praw = (px[wc] >> bc) & 0xFF;
-        const uint32_t pv = praw - ((praw * mv) >> 16) * (uint32_t)p;
-        const uint32_t sc = pv ? (uint32_t)p - inv[pv] : 0u;
-        uint32_t wv = preduce(px[lane], pm);
-        if (lane == 16 + (ns >> 2)) wv += 1u << (8 * (ns & 3));
-        wv = preduce(wv * sc, pm);
-        // the pivot row becomes that row; every other row adds v times it
-        const bool me = (y == x);
-        const uint32_t g = me ? 1u : v;
-        if (me) {
-#pragma unroll
-            for (int w = 0; w < 16; ++w) h[w] = t[w] = 0;
-            isp = true;
-            piv[y] = 1;
-            slotOf[y] = (int16_t)ns;
-            slotRow[ns] = (int16_t)y;
-            slotCol[ns] = (int16_t)c;
-        }
-        // through this warp's own buffer: one store per lane, eight
-        // broadcast 16-byte loads
-        prow[warp][lane] = wv;
-        __syncwarp();
-        const uint4 *pr = (const uint4 *)prow[warp];
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const uint4 hv = pr[w], tv = pr[4 + w];
-            h[4 * w] += g * hv.x;
-            h[4 * w + 1] += g * hv.y;
-            h[4 * w + 2] += g * hv.z;
-            h[4 * w + 3] += g * hv.w;
-            t[4 * w] += g * tv.x;
-            t[4 * w + 1] += g * tv.y;
-            t[4 * w + 2] += g * tv.z;
-            t[4 * w + 3] += g * tv.w;
-        }
-        __syncwarp();  // the buffer is rewritten at the next pivot
-        ++ns;
-        if (++since == lazy_k) {
-            since = 0;
-#pragma unroll
-            for (int w = 0; w < 16; ++w) {
-                h[w] = preduce(h[w], pm);
-                t[w] = preduce(t[w], pm);
-            }
-        }
-    }
-    const int r = ns;
-    // fully reduced rows back to shared memory for the (coalesced) output phase
-#pragma unroll
-    for (int w = 0; w < 16; ++w) {
-        *(uint32_t *)(S + y * LS + 4 * w) = preduce(h[w], pm);
-        *(uint32_t *)(Tt + y * LS + 4 * w) = preduce(t[w], pm);
-    }
-    // rank of each row among pivot rows (ascending) and among non-pivot rows
-    const int isp_i = (y < alpha) && isp;
-    unsigned bal = __ballot_sync(0xffffffffu, isp_i);
-    if (lane == 0) wsum[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0;
-    for (int w = 0; w < warp; ++w) before += wsum[w];
-    before += __popc(bal & ((1u << lane) - 1));
-    if (y < alpha) {
-        if (isp_i) {
-            pivpos[y] = (int16_t)before;
-            sortedSlot[before] = slotOf[y];
-            info[1 + before] = y;
-        } else {
-            pivpos[y] = (int16_t)(y - before);
-        }
-    }
-    if (y == 0) info[0] = r;
-    for (int c = y; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
-    if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
-    __syncthreads();
-    for (int l = warp; l < r; l += nwarp)
-        for (int s = lane; s < r; s += 32)
-            Mo[(int64_t)l * ldm + s] = D::enc(cen(Tt[slotRow[l] * LS + sortedSlot[s]], p));
-    if (r > 0) {
-        for (int row = warp; row < alpha; row += nwarp) {
-            if (piv[row]) continue;
-            for (int s = lane; s < r; s += 32)
-                Ko[(int64_t)pivpos[row] * ldk + s] = D::enc(cen(Tt[row * LS + sortedSlot[s]], p));
-        }
-    }
-    const int nr = beta - r;
-    for (int l = warp; l < r; l += nwarp)
-        for (int j = lane; j < nr; j += 32)
-            Ro[(int64_t)l * ldr + j] = D::enc(cen(S[slotRow[l] * LS + nonCol[j]], p));
-}
-
-// x mod p for an integer-valued float 0 <= x < 2^24 and a prime p >= 17.
+// x mod p for an integer-valued float 0 <= x < 2^24 with x / p < 2^20.
 // The quotient x / p is rounded to the nearest integer by adding and
 // subtracting 1.5 * 2^23 (FMA-pipe arithmetic, no conversion instruction);
 // it is within one of the true quotient, so the remainder, formed exactly by
 // an fma, needs one correction.  Checked against integer x mod p for every
-// prime 17 <= p <= 251 and every x < 2^24, with and without the multiply and
-// add contracted into one fma.
+// prime 17 <= p <= 251 and every x < 2^24, and for p <= 13 over the values a
+// leaf reaches (below 64 p^2 + p), with and without the multiply and add
+// contracted into one fma.
 __device__ __forceinline__ float fred(float x, float p, float invp) {
     const float q = __fadd_rn(fmaf(x, invp, 12582912.0f), -12582912.0f);
     const float r = fmaf(-q, p, x);
@@ -723,25 +515,281 @@ __global__ void __launch_bounds__(F32_THREADS, 1) k_ech_leaf_f32(const __grid_co
     }
 }
 
-static PackedMod packed_mod(int p) {
-    PackedMod q;
-    q.p = (uint32_t)p;
-    q.pp = (uint32_t)p * 0x01010101u;
-    q.invp = 1.0f / (float)p;
-    q.M = q.S = q.QM = 0;
-    if (p <= 13) {
-        // largest S with 255 * floor(2^S / p) < 2^16 and 255 / p < 2^(16 - S)
-        for (uint32_t S = 8; S < 16; ++S) {
-            const uint32_t M = (1u << S) / (uint32_t)p;
-            if (255u * M >= 65536u || (255u / (uint32_t)p) >= (1u << (16 - S))) break;
-            q.S = S;
-            q.M = M;
-        }
-        const uint32_t qm = (1u << (16 - q.S)) - 1;
-        q.QM = qm | (qm << 16);
+// ---------------------------------------------------------------------------
+// leaf ECH for 3 <= p <= 13, up to 1024 rows x 64 columns: the same
+// column-by-column Gauss-Jordan and topmost-row rule, and the same eight-
+// column groups as the fp32 leaf below, with the rows as residue bytes in
+// shared memory (row y at Rb[y]: 64 columns, then 64 slots), reduced after
+// every group:
+//  (B) the finder: one row per thread, one barrier per column; each warp's
+//      topmost candidate publishes its entries and the scale that makes its
+//      pivot -1, every row takes the new pivot row from the winner and
+//      records the multiple G[y][s] of the new pivot row s added to it.
+//      Then NP[s], pivot row s as a combination of the rows Q_0 .. Q_s, Q_s
+//      being row x_s as it stood at the group start plus the identity of its
+//      slot;
+//  (C) warp s publishes Q_s (transposed, for the tensor-core operand) and
+//      row x_s restarts from zero; every row forms CM_y = G[y] NP, reduced;
+//  (D) rows += CM Q on the tensor cores (mma.sync m16n8k8, fp16 operands
+//      below 13, fp32 sums below 2^11: exact), reduced to bytes again, over
+//      the columns from the group on and the slots up to its last.
+// A group's panel is read from the rows, which are reduced: the finder's
+// values stay below 8 p^2 + p during a group.  Three barriers per group plus
+// one per column.
+// ---------------------------------------------------------------------------
+constexpr int U8_RB = 132;  // row stride of Rb (bytes): 33 words, so 32 rows fall in 32 banks
+
+template <int C>
+__global__ void __launch_bounds__(1024, 1) k_ech_leaf_u8(const __grid_constant__ InvTable it, int p, int alpha,
+                                                         int beta, const typename Cd<C>::T *H, int64_t ldh,
+                                                         int32_t *info, typename Cd<C>::T *Mo, int64_t ldm,
+                                                         typename Cd<C>::T *Ko, int64_t ldk,
+                                                         typename Cd<C>::T *Ro, int64_t ldr) {
+    using D = Cd<C>;
+    using T = typename D::T;
+    extern __shared__ __align__(16) uint8_t sm[];
+    uint8_t *Rb = sm;                             // [rows][U8_RB]  the rows
+    __shared__ uint8_t inv[256];
+    __shared__ uint8_t piv[1024];
+    __shared__ int16_t slotOf[1024];
+    __shared__ int16_t pivpos[1024];
+    __shared__ int16_t slotRow[64], slotCol[64], sortedSlot[64], nonCol[64];
+    __shared__ uint64_t Gm[1024];                 // G[y][s] in byte s
+    __shared__ __align__(16) __half2 CMh[1024][4];    // CM_y: (CM_y[2 t], CM_y[2 t + 1]) at [y][t]
+    __shared__ __align__(16) __half QT[128][8];       // Q_s[e] at [e][s]
+    __shared__ __align__(16) float NP[8][8];      // NP[s][s'] (zero for s' > s)
+    __shared__ float cbuf[2][32][8];              // per warp: its topmost candidate's entries,
+    __shared__ uint64_t cgw[2][32];               // its multiples so far,
+    __shared__ float csc[2][32];                  // the scale that makes its pivot -1
+    __shared__ int wmin[2][32];                   // and its row
+    __shared__ uint64_t pgx[8];                   // per pivot s of the group: the multiples of x_s,
+    __shared__ float psc[8];                      // and its scale
+    __shared__ int gnp;                           // pivots in the group
+    __shared__ int wsum[32];
+    const int y = threadIdx.x, lane = y & 31, warp = y >> 5, nwarp = blockDim.x >> 5;
+    const float fp = (float)p, invp = 1.0f / (float)p;
+    uint8_t *row = Rb + y * U8_RB;
+
+    for (int q = y; q < 256; q += blockDim.x) inv[q] = it.v[q];
+    for (int q = y; q < 128 * 8; q += blockDim.x) QT[q >> 3][q & 7] = __float2half_rn(0.f);
+    piv[y] = 0;
+    slotOf[y] = -1;
+    // warp w loads rows 32 w .. 32 w + 31 (lane l: entries l and 32 + l); every
+    // thread clears its own row's slots
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+        const int r = warp * 32 + rr;
+        const T *hr = H + (int64_t)r * ldh;
+        const bool in = r < alpha;
+        Rb[r * U8_RB + lane] = in && lane < beta ? (uint8_t)res(D::dec(hr[lane]), p) : 0;
+        Rb[r * U8_RB + 32 + lane] = in && 32 + lane < beta ? (uint8_t)res(D::dec(hr[32 + lane]), p) : 0;
     }
-    return q;
+#pragma unroll
+    for (int k = 64; k < 128; k += 4) *(uint32_t *)(row + k) = 0u;
+    __syncthreads();
+
+    int ns = 0;  // pivots before the group
+    const int ngroups = (beta + 7) >> 3;
+    for (int g = 0; g < ngroups; ++g) {
+        const int c0 = 8 * g;
+        // (B) the finder
+        float pan[8];
+        {
+            const uint32_t w0 = *(const uint32_t *)(row + c0), w1 = *(const uint32_t *)(row + c0 + 4);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                pan[j] = (float)((w0 >> (8 * j)) & 0xFF);
+                pan[4 + j] = (float)((w1 >> (8 * j)) & 0xFF);
+            }
+        }
+        bool cand = y < alpha && !piv[y];
+        uint64_t gw = 0;  // G[y][s] in byte s
+        int s = 0;
+        // one column per pass, the current one always in pan[0]
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+            const int b = k & 1;
+            const float v = fred(pan[0], fp, invp);
+            const bool c = c0 + k < beta && cand && v != 0.f;
+            const unsigned bal = __ballot_sync(0xffffffffu, c);
+            if (bal && lane == __ffs(bal) - 1) {  // this warp's topmost candidate
+#pragma unroll
+                for (int j = 1; j < 8; ++j) cbuf[b][warp][j] = fred(pan[j], fp, invp);
+                cgw[b][warp] = gw;
+                csc[b][warp] = (float)(p - inv[(int)v]);
+            }
+            if (lane == 0) wmin[b][warp] = bal ? y + __ffs(bal) - 1 : INT_MAX;
+            __syncthreads();
+            const int x = (int)__reduce_min_sync(0xffffffffu, (unsigned)(lane < nwarp ? wmin[b][lane] : INT_MAX));
+            if (x != INT_MAX) {  // uniform: else column c0 + k has no pivot
+                const int xw = x >> 5;
+                const float sc = csc[b][xw];
+                // the new pivot row's entries: lane j computes entry j & 7
+                const float npl = fred(sc * cbuf[b][xw][lane & 7], fp, invp);
+                // every other row adds its entry at column c0 + k times the new
+                // pivot row; the pivot row's earlier multiples go into NP[s]
+                const bool isx = y == x;
+#pragma unroll
+                for (int j = 1; j < 8; ++j) {
+                    const float nj = __shfl_sync(0xffffffffu, npl, j);
+                    pan[j] = isx ? nj : fmaf(v, nj, pan[j]);
+                }
+                gw = isx ? 1ull << (8 * s) : (gw | ((uint64_t)(uint32_t)v << (8 * s)));
+                cand = cand && !isx;
+                if (y == 0) {
+                    piv[x] = 1;
+                    slotOf[x] = (int16_t)(ns + s);
+                    slotRow[ns + s] = (int16_t)x;
+                    slotCol[ns + s] = (int16_t)(c0 + k);
+                    pgx[s] = cgw[b][xw];
+                    psc[s] = sc;
+                }
+                ++s;
+            }
+#pragma unroll
+            for (int j = 1; j < 8; ++j) pan[j - 1] = pan[j];
+        }
+        Gm[y] = gw;
+        if (y == 0) gnp = s;
+        // NP[s] = sc_s (CM_(x_s) + e_s), CM_(x_s) = sum_{s' < s} G[x_s][s'] NP[s']:
+        // lane j < 8 of warp 0 forms column j
+        if (warp == 0) {
+            __syncwarp();
+            if (lane < 8) {
+                float npc[8];
+#pragma unroll
+                for (int s1 = 0; s1 < 8; ++s1) {
+                    float nv = 0.f;
+                    if (s1 < s) {
+                        const uint64_t gx = pgx[s1];
+                        float acc = 0.f;
+#pragma unroll
+                        for (int s2 = 0; s2 < s1; ++s2)
+                            acc = fmaf((float)(uint32_t)((gx >> (8 * s2)) & 0xFF), npc[s2], acc);
+                        acc = lane == s1 ? 1.f : (lane < s1 ? fred(acc, fp, invp) : 0.f);
+                        nv = fred(psc[s1] * acc, fp, invp);
+                    }
+                    npc[s1] = nv;
+                    NP[s1][lane] = nv;
+                }
+            }
+        }
+        __syncthreads();
+        const int nsg = gnp;
+        if (nsg == 0) continue;  // uniform
+        // (C) warp s publishes Q_s (transposed) from pivot row x_s, which then
+        // restarts from zero; every row forms its coefficients
+        for (int sq = warp; sq < nsg; sq += nwarp) {
+            const int xs = slotRow[ns + sq], own = 64 + ns + sq;  // the identity of its slot
+            uint32_t *rx = (uint32_t *)(Rb + xs * U8_RB) + lane;
+            uint32_t w = *rx;
+            if ((own >> 2) == lane) w += 1u << (8 * (own & 3));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) QT[4 * lane + i][sq] = __uint2half_rn((w >> (8 * i)) & 0xFF);
+            *rx = 0u;
+        }
+        {
+            const uint64_t gy = Gm[y];
+            float acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+#pragma unroll
+            for (int s2 = 0; s2 < 8; ++s2) {
+                if (s2 < nsg) {
+                    const float gv = (float)(uint32_t)((gy >> (8 * s2)) & 0xFF);
+                    const float4 a = *(const float4 *)NP[s2], b = *(const float4 *)(NP[s2] + 4);
+                    acc[0] = fmaf(gv, a.x, acc[0]);
+                    acc[1] = fmaf(gv, a.y, acc[1]);
+                    acc[2] = fmaf(gv, a.z, acc[2]);
+                    acc[3] = fmaf(gv, a.w, acc[3]);
+                    acc[4] = fmaf(gv, b.x, acc[4]);
+                    acc[5] = fmaf(gv, b.y, acc[5]);
+                    acc[6] = fmaf(gv, b.z, acc[6]);
+                    acc[7] = fmaf(gv, b.w, acc[7]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                CMh[y][t] = __floats2half2_rn(fred(acc[2 * t], fp, invp), fred(acc[2 * t + 1], fp, invp));
+        }
+        __syncthreads();
+        // (D) rows += CM Q, reduced, on the tensor cores over the 8-column
+        // tiles from the group on and the 8-slot tiles up to its last slot;
+        // warp w takes the 16-row tiles w, w + nwarp, ...
+        {
+            const int gid = lane >> 2, tig = lane & 3;
+            const int nth = 8 - g, nt = nth + ((ns + nsg + 7) >> 3);  // column tiles, all tiles
+            const int mtiles = (blockDim.x + 15) >> 4;
+            for (int mt = warp; mt < mtiles; mt += nwarp) {
+                const int r0 = 16 * mt;
+                const uint32_t a0 = *(const uint32_t *)&CMh[r0 + gid][tig];
+                const uint32_t a1 = *(const uint32_t *)&CMh[r0 + gid + 8][tig];
+                uint8_t *ra = Rb + (r0 + gid) * U8_RB, *rb = Rb + (r0 + gid + 8) * U8_RB;
+#pragma unroll 2
+                for (int t2 = 0; t2 < nt; ++t2) {
+                    const int off = t2 < nth ? 8 * (g + t2) : 64 + 8 * (t2 - nth);
+                    const uint32_t b0 = *(const uint32_t *)&QT[off + gid][2 * tig];
+                    const int e = off + 2 * tig;
+                    const uint32_t ua = *(const uint16_t *)(ra + e), ub = *(const uint16_t *)(rb + e);
+                    float d0 = (float)(ua & 0xFF), d1 = (float)(ua >> 8), d2 = (float)(ub & 0xFF), d3 = (float)(ub >> 8);
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5}, {%6}, "
+                        "{%0, %1, %2, %3};"
+                        : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+                        : "r"(a0), "r"(a1), "r"(b0));
+                    *(uint16_t *)(ra + e) = (uint16_t)((uint32_t)fred(d0, fp, invp) | ((uint32_t)fred(d1, fp, invp) << 8));
+                    *(uint16_t *)(rb + e) = (uint16_t)((uint32_t)fred(d2, fp, invp) | ((uint32_t)fred(d3, fp, invp) << 8));
+                }
+            }
+        }
+        __syncthreads();
+        ns += nsg;
+    }
+    const int r = ns;
+    // rank of each row among pivot rows (ascending) and among non-pivot rows
+    const int isp_i = (y < alpha) && piv[y];
+    unsigned bal = __ballot_sync(0xffffffffu, isp_i);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    before += __popc(bal & ((1u << lane) - 1));
+    if (y < alpha) {
+        if (isp_i) {
+            pivpos[y] = (int16_t)before;
+            sortedSlot[before] = slotOf[y];
+            info[1 + before] = y;
+        } else {
+            pivpos[y] = (int16_t)(y - before);
+        }
+    }
+    if (y == 0) info[0] = r;
+    for (int c = y; c < beta; c += blockDim.x) place_non_pivot(slotCol, r, c, nonCol);
+    if (y < r) info[1 + ECH_LEAF_COLS + y] = slotCol[y];
+    __syncthreads();
+    // the outputs, centred, straight from the (reduced) rows: lane l writes
+    // output columns l and l + 32
+    const int nr = beta - r;
+    const int sa = lane < r ? 64 + sortedSlot[lane] : -1, sb = lane + 32 < r ? 64 + sortedSlot[lane + 32] : -1;
+    const int ca = lane < nr ? nonCol[lane] : -1, cb = lane + 32 < nr ? nonCol[lane + 32] : -1;
+    auto put = [&](T *dst, const uint8_t *rw, int e) {
+        if (e >= 0) *dst = D::enc(cen(rw[e], p));
+    };
+    for (int l = warp; l < r; l += nwarp) {  // M and R: the pivot rows in slot order
+        const uint8_t *rw = Rb + slotRow[l] * U8_RB;
+        put(Mo + (int64_t)l * ldm + lane, rw, sa);
+        put(Mo + (int64_t)l * ldm + lane + 32, rw, sb);
+        put(Ro + (int64_t)l * ldr + lane, rw, ca);
+        put(Ro + (int64_t)l * ldr + lane + 32, rw, cb);
+    }
+    for (int rw = warp; rw < alpha; rw += nwarp) {  // K: the other rows
+        if (piv[rw]) continue;
+        T *ko = Ko + (int64_t)pivpos[rw] * ldk;
+        put(ko + lane, Rb + rw * U8_RB, sa);
+        put(ko + lane + 32, Rb + rw * U8_RB, sb);
+    }
 }
+
 
 // ---------------------------------------------------------------------------
 // leaf echelonisation over GF(2): the same Gauss-Jordan with the topmost-row
@@ -1119,25 +1167,21 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
         prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta), 0, alpha, beta);
         return;
     }
-    const int smem_max = 2 * 1024 * LS, smem = 2 * threads * LS;
-    const PackedMod pm = packed_mod(L.p);
-    const bool small = L.p <= 13;
-    InvTable it{};
-    if (!small) {  // inverses mod p by x^-1 = -(p / x) * (p mod x)^-1
-        it.v[1] = 1;
-        for (int x = 2; x < L.p; ++x)
-            it.v[x] = (uint8_t)((L.p - (L.p / x) * it.v[L.p % x] % L.p) % L.p);
-    }
+    // the byte leaf for small p and more rows than the fp32 leaf takes
+    const bool small = L.p <= 13 && alpha > F32_LEAF_ROWS;
+    InvTable it{};  // inverses mod p by x^-1 = -(p / x) * (p mod x)^-1
+    it.v[1] = 1;
+    for (int x = 2; x < L.p; ++x) it.v[x] = (uint8_t)((L.p - (L.p / x) * it.v[L.p % x] % L.p) % L.p);
     static std::once_flag once2[4];
     cudaEvent_t ev;
     prof_begin(L, K_ECH, &ev);
-#define GFE_LAZY(CODEC, T, IDX)                                                                                  \
+#define GFE_U8(CODEC, T, IDX)                                                                                    \
     do {                                                                                                          \
         std::call_once(once2[IDX], [&] {                                                                          \
-            cudaFuncSetAttribute(k_ech_leaf_lazy<CODEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);  \
+            cudaFuncSetAttribute(k_ech_leaf_u8<CODEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 * U8_RB); \
         });                                                                                                       \
-        k_ech_leaf_lazy<CODEC><<<1, threads, smem, L.st>>>(pm, lazy_k, (int)alpha, (int)beta, (const T *)H, ldh,  \
-                                                          info, (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);           \
+        k_ech_leaf_u8<CODEC><<<1, threads, threads * U8_RB, L.st>>>(it, L.p, (int)alpha, (int)beta, (const T *)H, \
+                                                                 ldh, info, (T *)M, ldm, (T *)K, ldk, (T *)R, ldr); \
     } while (0)
 #define GFE_F32(CODEC, T, IDX)                                                                                   \
     do {                                                                                                          \
@@ -1149,16 +1193,14 @@ void ech_leaf(const Launch &L, int64_t alpha, int64_t beta, const void *H, int64
         k_ech_leaf_f32<CODEC><<<1, 2 * threads, f32_leaf_smem(threads), L.st>>>(                                   \
             it, L.p, (int)alpha, (int)beta, (const T *)H, ldh, info, (T *)M, ldm, (T *)K, ldk, (T *)R, ldr);       \
     } while (0)
-    // pivot steps between full reductions: (p - 1) + k (p - 1)^2 <= 255
-    const int lazy_k = small ? (255 - (L.p - 1)) / ((L.p - 1) * (L.p - 1)) : 0;
     if (L.codec == CODEC_F8) {
-        if (small) GFE_LAZY(CODEC_F8, uint8_t, 0);
+        if (small) GFE_U8(CODEC_F8, uint8_t, 0);
         else GFE_F32(CODEC_F8, uint8_t, 1);
     } else {
-        if (small) GFE_LAZY(CODEC_BF16, uint16_t, 2);
+        if (small) GFE_U8(CODEC_BF16, uint16_t, 2);
         else GFE_F32(CODEC_BF16, uint16_t, 3);
     }
-#undef GFE_LAZY
+#undef GFE_U8
 #undef GFE_F32
     prof_end(L, K_ECH, ev, (double)alpha * (double)beta * (double)(alpha < beta ? alpha : beta), 0, alpha, beta);
 }
