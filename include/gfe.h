@@ -326,9 +326,10 @@ gfe_status gfe_set_block_policy(int64_t threshold, int64_t block);
 int64_t gfe_auto_block(int32_t p, int64_t m, int64_t n);
 
 /* Rows of a leaf block in the planner's leaf grid: 1..1024, or 0 for the
- * default, which is the most the field's leaf kernel takes (1024 for
- * p <= 13, 256 for larger p); larger values are capped at that.  Process
- * wide.  Results never depend on it.  GFE_EINVAL outside [0, 1024]. */
+ * default, which is the most the field's leaf kernels take (1024 for
+ * p <= 13, 256 for larger p); larger values are capped at that.  Leaves of
+ * at most 256 rows run the fp32 leaf kernel for every p > 2.  Process wide.
+ * Results never depend on it.  GFE_EINVAL outside [0, 1024]. */
 gfe_status gfe_set_leaf_rows(int64_t rows);
 /* Tiles per thread block of the multiply-adds the planner runs beside its
  * critical path (the side streams): enough blocks are launched that none
