@@ -98,6 +98,18 @@ typedef struct {
  * Depends only on (p, m, n, flags). */
 gfe_status gfe_query_workspace(const gfe_matrix *A, uint32_t flags, size_t *ws_bytes);
 
+/* Bytes of the gfe_result buffers gfe_echelon writes for A and flags (the
+ * outputs of Eq. (echelon), Section 3.1), each sized for the worst case
+ * r = k = min(m, n) with rows packed tight and every buffer rounded up to 256
+ * bytes: rank (8 bytes), pivot_cols and pivot_rows (k int64 each), R (k rows
+ * of n entries); with GFE_WANT_TRANSFORM or GFE_WANT_DENSE_T also M (k x k)
+ * and K (m x k); E (m x n) with GFE_WANT_DENSE_E, T (m x m) with
+ * GFE_WANT_DENSE_T.  A row of c entries takes c bytes (GFE_U8) or
+ * ceil(c / 64) 8-byte words (GFE_BITS64).  Host only: no device call, and
+ * A->data is checked as for gfe_echelon but never read.  GFE_EINVAL for a
+ * bad matrix or a NULL out_bytes. */
+gfe_status gfe_query_result_bytes(const gfe_matrix *A, uint32_t flags, size_t *out_bytes);
+
 /*
  * gfe_echelon -- the whole method: Step 1 (Tasks ClearDown, Extend,
  * UpdateRow, UpdateRowTrafo), Step 2 (Task RowLengthen) and Step 3 (Tasks

@@ -420,6 +420,21 @@ gfe_status gfe_query_workspace(const gfe_matrix *A, uint32_t flags, size_t *ws_b
     return query(A, trafo, true, ws_bytes);
 }
 
+gfe_status gfe_query_result_bytes(const gfe_matrix *A, uint32_t flags, size_t *out_bytes) {
+    gfe_status st = check_matrix(A);
+    if (st) return st;
+    if (!out_bytes) return (set_error("out_bytes is NULL"), GFE_EINVAL);
+    const bool bits = A->fmt == GFE_BITS64;
+    const int64_t m = A->m, n = A->n, k = std::min(m, n);
+    auto row = [&](int64_t c) -> size_t { return bits ? (size_t)((c + 63) / 64) * 8 : (size_t)c; };
+    size_t total = al256(8) + 2 * al256((size_t)k * 8) + al256((size_t)k * row(n));
+    if (flags & (GFE_WANT_TRANSFORM | GFE_WANT_DENSE_T)) total += al256((size_t)k * row(k)) + al256((size_t)m * row(k));
+    if (flags & GFE_WANT_DENSE_E) total += al256((size_t)m * row(n));
+    if (flags & GFE_WANT_DENSE_T) total += al256((size_t)m * row(m));
+    *out_bytes = total;
+    return GFE_OK;
+}
+
 gfe_status gfe_echelon(const gfe_matrix *A, const gfe_result *out, uint32_t flags, void *ws, size_t ws_bytes,
                        void *stream) {
     if (!out || !out->rank) return (set_error("out->rank is required"), GFE_EINVAL);

@@ -55,6 +55,7 @@ KINDS = ["mad_tensor", "mad_plain", "ech_leaf", "rows", "cols", "copy", "convert
 # every symbol declared in include/gfe.h, with its ctypes signature
 SIGNATURES = {
     "gfe_query_workspace": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]),
+    "gfe_query_result_bytes": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]),
     "gfe_echelon": (_i32, [ctypes.POINTER(GfeMatrix), ctypes.POINTER(GfeResult), ctypes.c_uint32, _vp,
                            ctypes.c_size_t, _vp]),
     "gfe_rank": (_i32, [ctypes.POINTER(GfeMatrix), _vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_size_t, _vp]),
@@ -178,6 +179,14 @@ def query_workspace(A: torch.Tensor, p: int, n: int | None = None, flags: int = 
     mat = matrix_arg(A, p, n)
     out = ctypes.c_size_t(0)
     _check(lib().gfe_query_workspace(ctypes.byref(mat), flags, ctypes.byref(out)))
+    return out.value
+
+
+def query_result_bytes(A: torch.Tensor, p: int, n: int | None = None, flags: int = WANT_TRANSFORM) -> int:
+    """Bytes of the result buffers gfe_echelon writes (gfe_query_result_bytes)."""
+    mat = matrix_arg(A, p, n)
+    out = ctypes.c_size_t(0)
+    _check(lib().gfe_query_result_bytes(ctypes.byref(mat), flags, ctypes.byref(out)))
     return out.value
 
 

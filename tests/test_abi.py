@@ -146,3 +146,32 @@ def test_solve_nullspace_and_gf2_mad_reject_bad_arguments():
     assert L.gfe_mad_gf2(0, 100, 70, None, 0, 1, 16, 1, 16, 1, 16, None) == 0  # empty: nothing to do
     assert L.gfe_set_side_tiles(-1) == 1 and L.gfe_set_side_tiles(2000) == 1
     assert L.gfe_set_side_tiles(4) == 0
+
+
+def test_query_result_bytes():
+    """gfe_query_result_bytes: the worst-case result buffers, 256-byte rounded,
+    computed on the host."""
+    L = gfe.lib()
+
+    def q(p, m, n, flags, fmt=0, ld=None):
+        mat = gfe.GfeMatrix(p, m, n, fmt, 64, ld if ld is not None else (((n + 63) // 64) * 8 if fmt else n))
+        out = ctypes.c_size_t(0)
+        assert L.gfe_query_result_bytes(ctypes.byref(mat), flags, ctypes.byref(out)) == 0, L.gfe_last_error()
+        return out.value
+
+    a = lambda x: (x + 255) // 256 * 256
+    m, n, k = 300, 200, 200
+    base = a(8) + 2 * a(8 * k) + a(k * n)
+    assert q(7, m, n, 0) == base
+    assert q(7, m, n, 1) == base + a(k * k) + a(m * k)
+    assert q(7, m, n, 1 | 2 | 4) == base + a(k * k) + a(m * k) + a(m * n) + a(m * m)
+    assert q(7, m, n, 4) == base + a(k * k) + a(m * k) + a(m * m)  # dense T needs M and K
+    words = lambda c: (c + 63) // 64 * 8
+    assert q(2, m, n, 1, fmt=1) == a(8) + 2 * a(8 * k) + a(k * words(n)) + a(k * words(k)) + a(m * words(k))
+    assert q(3, 0, 5, 1) == a(8) + 2 * a(0) + a(0) + a(0) + a(0)
+    # bad arguments: rejected before anything else
+    mat = gfe.GfeMatrix(4, 3, 3, 0, 64, 3)
+    out = ctypes.c_size_t(0)
+    assert L.gfe_query_result_bytes(ctypes.byref(mat), 1, ctypes.byref(out)) == 1
+    mat = gfe.GfeMatrix(7, 3, 3, 0, 64, 3)
+    assert L.gfe_query_result_bytes(ctypes.byref(mat), 1, None) == 1
