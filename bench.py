@@ -86,8 +86,15 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl" if os.environ.get("GFE_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        backend = "nccl" if os.environ.get("GFE_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        if backend == "nccl":
+            # each rank on its own GPU before NCCL starts: a barrier issued
+            # before any device is chosen (the reference arm's) would put
+            # every rank on GPU 0
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return ws, rank, local
 
 
