@@ -190,10 +190,11 @@ __device__ __forceinline__ float fred(float x, float p, float invp) {
 }
 
 // ---------------------------------------------------------------------------
-// leaf ECH for 17 <= p <= 251: the same column-by-column Gauss-Jordan and
-// topmost-row rule.  A row's 64 entries and 64 slot coefficients are fp32
-// integers in shared memory (row y at Rw[y], columns then slots); columns
-// are taken eight at a time:
+// leaf ECH of at most 256 rows for p > 2 (every leaf of 17 <= p <= 251; the
+// byte leaf below takes the larger ones of p <= 13): the same
+// column-by-column Gauss-Jordan and topmost-row rule.  A row's 64 entries
+// and 64 slot coefficients are fp32 integers in shared memory (row y at
+// Rw[y], columns then slots); columns are taken eight at a time:
 //  (A) the panel: every row's eight entries in the group's columns, reduced
 //      (written by the previous group's (D), else read from the rows);
 //  (B) the finder: the first half of the threads, one row per lane, runs the
@@ -516,9 +517,10 @@ __global__ void __launch_bounds__(F32_THREADS, 1) k_ech_leaf_f32(const __grid_co
 }
 
 // ---------------------------------------------------------------------------
-// leaf ECH for 3 <= p <= 13, up to 1024 rows x 64 columns: the same
-// column-by-column Gauss-Jordan and topmost-row rule, and the same eight-
-// column groups as the fp32 leaf below, with the rows as residue bytes in
+// leaf ECH for 3 <= p <= 13, 257 to 1024 rows x 64 columns (smaller leaves
+// take the fp32 leaf above): the same column-by-column Gauss-Jordan and
+// topmost-row rule, and the same eight-column groups as the fp32 leaf, with
+// the rows as residue bytes in
 // shared memory (row y at Rb[y]: 64 columns, then 64 slots), reduced after
 // every group:
 //  (B) the finder: one row per thread, one barrier per column; each warp's
